@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Benchmark of the density-fitted PNOF7 energy+gradient evaluation on one GB300.
+
+Workload: H50 linear chain (spacing 1.8 bohr + U(-0.1, 0.1) seeded jitter per bond), 3
+even-tempered s functions per H (alpha = 0.2 * 4^k) and 10 aux s per H (alpha = 0.1 * 3^k):
+nbf = 150, naux = 500, 50 active orbitals, PNOF7 with 25 pairs and N_g = 1. One step is one
+energy+gradient evaluation (transforms, J, K, energy, Lagrangian, orbital and occupation
+gradients) at fixed (C, gamma), with C = S^{-1/2} Q for a seeded random orthogonal Q and
+gamma ~ U(0.1, 1.2). L2 is flushed (a 256 MiB write) before every timed step; the step itself
+is bracketed by CUDA events on the library's stream.
+
+Under torchrun (N > 1) every rank evaluates its own independent geometry (seed 2 + rank):
+the path has no exchange step, so the ranks are replicas and `value` sums their work.
+
+`--impl reference` times the CPU FP64 oracle (test infrastructure) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NOF energy+gradient evals/sec vs FP64 plain GPU path at |ΔE|≤1e-6 Ha"
+WORKLOAD = ("H50 chain, spacing 1.8+U(-0.1,0.1) bohr, 3 s/H (0.2*4^k) + 10 aux s/H (0.1*3^k): "
+            "nbf=150, naux=500, nact=50, PNOF7, 25 pairs, N_g=1")
+ACC_GATE = 1e-6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--precision", choices=["auto", "split", "fp64"], default="auto")
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(seed=2):
+    from paper_2512_13550_gb300 import inputs
+    orb, aux = inputs.basis_3s_10aux()
+    xyz = inputs.jittered_chain(50, seed)
+    return xyz, orb, aux
+
+
+# ---------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+def oracle_setup(seed=2):
+    """The oracle's one-time set-up for the H50 workload (integrals, RI fit, orbitals)."""
+    from oracle import integrals, pnof, reference, ri
+    from paper_2512_13550_gb300 import inputs
+    xyz, orb, aux = workload(seed)
+    S, T, V = integrals.one_electron(orb, xyz)
+    B = ri.fitted_B(orb, aux, xyz)
+    vnn = integrals.nuclear_repulsion(xyz)
+    n = S.shape[0]
+    pm = pnof.PairMap(50, 1, n)
+    C = reference.orthonormal_orbitals(S, inputs.random_orthogonal(n, 0))
+    gam = inputs.random_gamma(pm.ngamma, 1)
+    return (B, T + V, C, gam, pm, vnn)
+
+
+def oracle_eval(system):
+    from oracle import pnof
+    return pnof.energy_and_gradients(*system)
+
+
+def _cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def cpu_baseline(budget_s: float):
+    """Time the FP64 oracle (as it stands) on a bounded sample of H50 evaluations."""
+    system = oracle_setup()
+    oracle_eval(system)
+    t0 = time.perf_counter()
+    count = 0
+    while True:
+        oracle_eval(system)
+        count += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or count >= 1000:
+            break
+    return {"value": count / el, "unit": "evals/s", "cores": _cores(), "kind": "oracle",
+            "sample": f"{count} H50 energy+gradient evaluations of the numpy FP64 oracle in "
+                      f"{el:.1f} s (set-up excluded; BLAS threads as configured)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    system = oracle_setup()
+    for _ in range(args.warmup):
+        oracle_eval(system)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_eval(system)
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": _cores(), "kind": "oracle",
+                             "sample": f"{args.steps} timed H50 energy+gradient evaluations of the "
+                                       f"numpy FP64 oracle (set-up excluded)"},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_2512_13550_gb300 as nof
+    from paper_2512_13550_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prec = {"auto": nof.PREC_SPLIT_BF16, "split": nof.PREC_SPLIT_BF16, "fp64": nof.PREC_FP64}[args.precision]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    xyz, orb, aux = workload(2 + rank)
+
+    def make_ctx(p):
+        ctx = nof.Context(precision=p, stream=stream)
+        ctx.build_B(xyz, orb, aux)
+        return ctx
+
+    try:
+        ctx = make_ctx(prec)
+    except nof.NofError as e:
+        if args.precision != "auto":
+            raise
+        print(f"# split path unavailable ({e}); timing the FP64 path", file=sys.stderr)
+        prec = nof.PREC_FP64
+        ctx = make_ctx(prec)
+    s = ctx.sizes
+    n = s["nbf"]
+    Q = torch.tensor(inputs.random_orthogonal(n, 0), dtype=torch.float64, device="cuda")
+    C = ctx.lowdin(Q)
+    gam = torch.tensor(inputs.random_gamma(s["ngamma"], 1), dtype=torch.float64, device="cuda")
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    gg = torch.empty(s["ngamma"], dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed_loop(c, steps, warmup, profile=False):
+        for _ in range(warmup):
+            c.energy_grad(C, gam, E, g, gg)
+        torch.cuda.synchronize()
+        if profile:
+            c.profile(True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        l0 = nof.kernel_launches()
+        for i in range(steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            c.energy_grad(C, gam, E, g, gg)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        launches = nof.kernel_launches() - l0
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        prof = c.profile_read() if profile else None
+        if profile:
+            c.profile(False)
+        return ms, launches, prof
+
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms, launches, prof = timed_loop(ctx, args.steps, args.warmup, profile=True)
+    torch.cuda.synchronize()
+    t_max = ms
+    if dist is not None:
+        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        dist.barrier()
+    E_fast = float(E.item())
+    g_fast = g.clone()
+
+    # accuracy and throughput of the plain FP64 path on the same inputs
+    if prec == nof.PREC_FP64:
+        ctx64, E64, dE, dg = ctx, E_fast, 0.0, 0.0
+        ms64, steps64 = ms, args.steps
+    else:
+        ctx64 = make_ctx(nof.PREC_FP64)
+        ms64, _, _ = timed_loop(ctx64, args.fp64_steps, 1)
+        steps64 = args.fp64_steps
+        E64 = float(E.item())
+        dE = abs(E_fast - E64)
+        dg = float((g_fast - g).abs().max().item())
+
+    # end-to-end through the public API from pinned host buffers
+    hC = C.cpu().pin_memory()
+    hgam = gam.cpu().pin_memory()
+    hE = torch.empty(1, dtype=torch.float64).pin_memory()
+    hg = torch.empty(n, n, dtype=torch.float64).pin_memory()
+    dC, dgam = torch.empty_like(C), torch.empty_like(gam)
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        dC.copy_(hC, non_blocking=True)
+        dgam.copy_(hgam, non_blocking=True)
+        ctx.energy_grad(dC, dgam, E, g, gg)
+        hE.copy_(E, non_blocking=True)
+        hg.copy_(g, non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = hC.numel() * 8 + hgam.numel() * 8
+    d2h = hE.numel() * 8 + hg.numel() * 8
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    value = world * args.steps / (t_max / 1e3)
+    dom_ms, dom_launches, dom_name = prof
+    roof = roofline(prec, s, dom_ms / max(dom_launches, 1), dom_name)
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if prec == nof.PREC_SPLIT_BF16 else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "path": "split-bf16 tcgen05" if prec else "plain fp64",
+                   "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "accuracy": {"max_abs_dE_vs_fp64_gpu": dE, "max_abs_dg_vs_fp64_gpu": dg,
+                     "gate": ACC_GATE, "pass": bool(dE <= ACC_GATE and dg <= ACC_GATE)},
+        "fp64_plain_evals_per_s": steps64 / (ms64 / 1e3),
+        "speedup_vs_fp64_plain": value / world / (steps64 / (ms64 / 1e3)),
+        "roofline": roof,
+        "e2e": {"value": world * e2e_steps / e2e_s, "unit": "evals/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 roofline of the plain path: 2 FP64 FMA per clock per SM (the rate an FMA-throughput probe
+# measured on GB300: 1.19 TFLOP/s), x 152 SMs x 2.07 GHz x 2 FLOP = 1.26 TFLOP/s.
+FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
+
+
+def roofline(prec, s, ms_per_launch, name):
+    n, X, a = s["nbf"], s["naux"], s["nact"]
+    peaks, src = _peaks()
+    if prec == 0:
+        flops = 2.0 * X * n * n * a  # half transform T = B C_a
+        achieved = flops / (ms_per_launch / 1e3) / 1e12
+        peak = FP64_PEAK_TFLOPS
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None, "traffic": None,
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe-measured rate)"}
+    return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None,
+            "frac": None, "traffic": None, "peak_source": src}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,150 @@
+/*
+ * nof.h - C ABI of the GB300 library for the density-fitted PNOF JK step.
+ *
+ * The operation follows DoNOF 2.0 (Lew-Yee, Mitxelena, del Campo, Piris, arXiv 2512.13550):
+ * a closed-shell natural-orbital-functional energy E[{n_p, phi_p}] (Theory section, Eq. ENOF)
+ * in its JKL-only form (Eq. PNOF) over the electron-pairing structure of Eq. OmegaG / Fig. 1,
+ * with occupations from the trigonometric gamma mapping (Occupation Number Optimization
+ * subsection), the Lagrangian and orbital gradient g = 4(lambda - lambda^T) and the orbital
+ * rotation C <- C exp(y) (Natural Orbital Optimization subsection), with the two-electron
+ * integrals approximated by the resolution of the identity (ERITYP='RI', Single Point
+ * Energy section).
+ *
+ * Conventions for every entry point:
+ *  - Return value: NOF_OK (0) or a negative NOF_E* code. Nothing aborts or throws across the
+ *    ABI; nof_last_error() returns a thread-local message for the last failure.
+ *  - Array arguments are DEVICE pointers owned by the caller, FP64, row-major, unless the
+ *    comment says "host". Calls are asynchronous on the stream given to nof_create; the
+ *    caller synchronises (or calls nof_sync) before reading results.
+ *  - Orbital coefficients: C is nbf x nbf, C[mu * nbf + p] = C_mu,p, so
+ *    phi_p = sum_mu C_mu,p chi_mu. Columns are orbitals and must be S-orthonormal for the
+ *    energy to be the functional's.
+ *  - Orbitals 0 .. nact-1 are active (nonzero occupation); nact = (N/2)(ncwo + 1).
+ *  - gamma has ngamma = (N/2) ncwo entries stored slot-major: gamma[i * (N/2) + g] is the
+ *    angle of slot i of subspace g (slot 0 = the strong orbital's gamma_g).
+ *  - The library owns only its workspaces (allocated by nof_build_B, freed by nof_destroy).
+ */
+#ifndef NOF_H
+#define NOF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NOF_OK 0
+#define NOF_EINVAL -1      /* bad argument: null pointer, size, option, unsupported system */
+#define NOF_ENOMEM -2      /* device allocation failed */
+#define NOF_ECUDA -3       /* a CUDA runtime call failed (message has the CUDA error) */
+#define NOF_ETIMEOUT -4    /* a bounded device-side wait gave up */
+#define NOF_ENONFINITE -5  /* NaN or Inf found in an input or a result */
+#define NOF_EILLCOND -6    /* the aux Coulomb metric is numerically singular */
+#define NOF_ENOTCONV -7    /* an iteration did not converge */
+#define NOF_ESTATE -8      /* call out of order (e.g. nof_jk before nof_build_B) */
+
+/* Arithmetic of the JK / Lagrangian contractions. */
+#define NOF_PREC_FP64 0       /* plain FP64 SIMT kernels */
+#define NOF_PREC_SPLIT_BF16 1 /* tcgen05 tensor cores on exact BF16 digit planes (4 digits,
+                                 FP32 exact partial sums, about 32 significant bits) */
+
+typedef struct nof_ctx nof_ctx;
+
+/* Functional and optimiser options. Field names follow the paper's input keywords where one
+ * exists (IPNOF, ISOFTMAX, NCWO = N_g of Eq. OmegaG). */
+typedef struct {
+    int ipnof;        /* 7 = PNOF7 (default), 5 = PNOF5 */
+    int isoftmax;     /* 0 = trigonometric mapping (the only mapping implemented) */
+    int ncwo;         /* N_g, weak orbitals per subspace (>= 1) */
+    int precision;    /* NOF_PREC_FP64 or NOF_PREC_SPLIT_BF16 */
+    int on_iters;     /* steepest-descent ON steps per nof_step (default 20) */
+    double on_lr;     /* ON step length (default 0.3) */
+    double lr;        /* ADAM learning rate for the orbital rotation (default 0.02) */
+    double b1, b2;    /* ADAM moment decays (default 0.9, 0.999) */
+    double eps;       /* ADAM epsilon (default 1e-8) */
+} nof_options;
+
+/* s-only contracted basis repeated on every atom (host arrays). Shell s has nprim[s]
+ * primitives; exponents and contraction coefficients are concatenated over shells.
+ * Primitives are normalised, then each contraction is renormalised. For an auxiliary
+ * basis every primitive is its own (uncontracted) function and coefs are ignored. */
+typedef struct {
+    int nshell;
+    const int* nprim;      /* host [nshell] */
+    const double* exps;    /* host [sum nprim] */
+    const double* coefs;   /* host [sum nprim] */
+} nof_basis;
+
+/* Fill opt with the defaults listed above. */
+void nof_default_options(nof_options* opt);
+
+/* Create a context on the current CUDA device. stream is a cudaStream_t (NULL = legacy
+ * default stream); every kernel of this context runs on it. */
+int nof_create(nof_ctx** out, const nof_options* opt, void* stream);
+
+/* Free the context and all of its device workspaces. Safe on NULL. */
+int nof_destroy(nof_ctx* ctx);
+
+/* Set-up for one geometry (the integral / RI stage of the Single Point Energy section,
+ * ERITYP='RI'): computes on the device S, H = T + V, V_nn, the three-centre integrals
+ * (P|mu nu), the Coulomb metric (P|Q) and its Cholesky factor L, and stores
+ * B^P_{mu nu} = sum_Q (L^{-1})_{PQ} (Q|mu nu) in the format the precision option needs.
+ * xyz: host [natom][3] bohr; Z: host [natom] nuclear charges (NULL = all 1).
+ * Only closed-shell singlets: mult must be 1 and sum(Z) - charge even and positive.
+ * Returns NOF_EILLCOND if a pivot of the metric falls below 1e-14 of its largest diagonal. */
+int nof_build_B(nof_ctx* ctx, int natom, const double* xyz, const double* Z, int charge,
+                int mult, const nof_basis* orb, const nof_basis* aux);
+
+/* Sizes of the built system (any pointer may be NULL). vnn is copied to the host
+ * (synchronises the stream). */
+int nof_query(nof_ctx* ctx, int* nbf, int* naux, int* nact, int* ngamma, double* vnn);
+
+/* Copy S and H (nbf x nbf) into caller device buffers. */
+int nof_get_SH(nof_ctx* ctx, double* S, double* H);
+
+/* Copy the fitted tensor B as FP64 [naux][nbf][nbf] (reconstructed from the stored digit
+ * planes under NOF_PREC_SPLIT_BF16). Used to check sum_P B^P B^P against exact ERIs. */
+int nof_get_B(nof_ctx* ctx, double* B);
+
+/* C = S^{-1/2} Q (Loewdin orthonormalisation, S^{-1/2} by a Newton-Schulz iteration on the
+ * device). Q: nbf x nbf orthogonal. Gives S-orthonormal orbitals for any orthogonal Q. */
+int nof_lowdin(nof_ctx* ctx, const double* Q, double* C);
+
+/* J_pq = sum_P b^P_pp b^P_qq and K_pq = sum_P (b^P_pq)^2 over the active orbitals, with
+ * b^P = C_a^T B^P C_a (the orbital transformation of the RI tensor; Eq. PNOF uses J and K,
+ * and L = K for real orbitals). J, K: nact x nact. */
+int nof_jk(nof_ctx* ctx, const double* C, double* J, double* K);
+
+/* One energy+gradient evaluation at fixed (C, gamma):
+ *   E       (1 double)      the PNOF energy of Eq. PNOF plus V_nn;
+ *   g_orb   (nbf x nbf)     g_pq = dE/dy_pq = 4 (lambda_pq - lambda_qp) for C' = C exp(y);
+ *   g_gamma (ngamma)        dE/dgamma through the trigonometric mapping.
+ * Any output pointer may be NULL to skip copying it (E is always computed). */
+int nof_energy_grad(nof_ctx* ctx, const double* C, const double* gamma, double* E,
+                    double* g_orb, double* g_gamma);
+
+/* One alternating optimisation step, in place:
+ *   1. J, K, h_pp at C;  2. on_iters ON steps gamma -= on_lr dE/dgamma with J, K fixed;
+ *   3. E, lambda, g at (C, gamma);  4. ADAM on g (moments m, v: nbf x nbf, step counter *t
+ *   on the host, incremented);  5. C <- C exp(y) (Taylor-12 scaling and squaring).
+ * out (device, 3 doubles): E at (C_old, gamma_new), ||g||_F, max |lambda - lambda^T|. */
+int nof_step(nof_ctx* ctx, double* C, double* gamma, double* m, double* v, int* t, double* out);
+
+/* Wait for the context's stream and report any device-side status word. */
+int nof_sync(nof_ctx* ctx);
+
+/* Measurement hooks (no paper counterpart; used by the benchmark):
+ * nof_kernel_launches: number of kernels this library has launched in the process so far.
+ * nof_profile: enable (1) / disable (0) CUDA-event timing of the dominant kernel of each
+ *   evaluation on the context's stream; enabling clears the accumulated record.
+ * nof_profile_read: synchronise and return the accumulated device time (ms) and launch count
+ *   of the dominant kernel, and its name (static string; may be NULL). */
+long long nof_kernel_launches(void);
+int nof_profile(nof_ctx* ctx, int enable);
+int nof_profile_read(nof_ctx* ctx, double* ms, int* launches, const char** name);
+
+/* Thread-local description of the last error (never NULL). */
+const char* nof_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NOF_H */

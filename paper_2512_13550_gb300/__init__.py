@@ -1,0 +1,223 @@
+"""GB300 library for the density-fitted PNOF JK step (DoNOF 2.0, arXiv 2512.13550).
+
+This module is a thin ctypes binding over the C ABI in include/nof.h: it marshals torch CUDA
+tensors (device memory and the current stream) into plain pointers and turns status codes into
+exceptions. Every step of the computation runs in the library's own CUDA kernels; there is no
+CPU fallback, and importing this package fails loudly if libnof.so has not been built
+(python -m paper_2512_13550_gb300.build).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs  # noqa: F401  (re-exported: seeded synthetic inputs)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnof.so")
+
+PREC_FP64 = 0
+PREC_SPLIT_BF16 = 1
+
+NOF_OK, NOF_EINVAL, NOF_ENOMEM, NOF_ECUDA = 0, -1, -2, -3
+NOF_ETIMEOUT, NOF_ENONFINITE, NOF_EILLCOND, NOF_ENOTCONV, NOF_ESTATE = -4, -5, -6, -7, -8
+ERROR_NAMES = {
+    -1: "NOF_EINVAL", -2: "NOF_ENOMEM", -3: "NOF_ECUDA", -4: "NOF_ETIMEOUT",
+    -5: "NOF_ENONFINITE", -6: "NOF_EILLCOND", -7: "NOF_ENOTCONV", -8: "NOF_ESTATE",
+}
+
+
+class NofError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("ipnof", ctypes.c_int), ("isoftmax", ctypes.c_int), ("ncwo", ctypes.c_int),
+                ("precision", ctypes.c_int), ("on_iters", ctypes.c_int), ("on_lr", ctypes.c_double),
+                ("lr", ctypes.c_double), ("b1", ctypes.c_double), ("b2", ctypes.c_double),
+                ("eps", ctypes.c_double)]
+
+
+class CBasis(ctypes.Structure):
+    _fields_ = [("nshell", ctypes.c_int), ("nprim", ctypes.POINTER(ctypes.c_int)),
+                ("exps", ctypes.POINTER(ctypes.c_double)), ("coefs", ctypes.POINTER(ctypes.c_double))]
+
+
+_lib = None
+
+# name -> (restype, argtypes); mirrors include/nof.h
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "nof_default_options": (None, [ctypes.POINTER(Options)]),
+    "nof_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(Options), _P]),
+    "nof_destroy": (ctypes.c_int, [_P]),
+    "nof_build_B": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(CBasis), ctypes.POINTER(CBasis)]),
+    "nof_query": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "nof_get_SH": (ctypes.c_int, [_P, _P, _P]),
+    "nof_get_B": (ctypes.c_int, [_P, _P]),
+    "nof_lowdin": (ctypes.c_int, [_P, _P, _P]),
+    "nof_jk": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nof_energy_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "nof_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "nof_sync": (ctypes.c_int, [_P]),
+    "nof_kernel_launches": (ctypes.c_longlong, []),
+    "nof_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "nof_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nof_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load_library():
+    """Load libnof.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2512_13550_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libnof so far in this process (counted at every launch site)."""
+    return int(load_library().nof_kernel_launches())
+
+
+def _check(rc: int):
+    if rc != NOF_OK:
+        raise NofError(rc, load_library().nof_last_error().decode())
+
+
+def _basis_struct(b: "inputs.Basis"):
+    nprim = np.array([len(e) for e, _ in b.shells], np.int32)
+    exps = np.array([x for e, _ in b.shells for x in e], np.float64)
+    coefs = np.array([x for _, c in b.shells for x in c], np.float64)
+    st = CBasis(len(b.shells), nprim.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                exps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                coefs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return st, (nprim, exps, coefs)
+
+
+def _dptr(t):
+    import torch
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One system (geometry + basis) on the current CUDA device and stream."""
+
+    def __init__(self, precision: int = PREC_FP64, ipnof: int = 7, ncwo: int = 1, stream=None,
+                 **opts):
+        import torch
+        lib = load_library()
+        o = Options()
+        lib.nof_default_options(ctypes.byref(o))
+        o.precision, o.ipnof, o.ncwo = precision, ipnof, ncwo
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._h = ctypes.c_void_p()
+        _check(lib.nof_create(ctypes.byref(self._h), ctypes.byref(o), ctypes.c_void_p(self.stream.cuda_stream)))
+        self.opts = o
+        self.t = ctypes.c_int(0)
+        self.sizes = None
+
+    def close(self):
+        if self._h:
+            load_library().nof_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_B(self, xyz, orb, aux, Z=None, charge: int = 0, mult: int = 1):
+        xyz = np.ascontiguousarray(xyz, np.float64)
+        zarr = None if Z is None else np.ascontiguousarray(Z, np.float64)
+        ob, keep1 = _basis_struct(orb)
+        ab, keep2 = _basis_struct(aux)
+        _check(load_library().nof_build_B(self._h, xyz.shape[0], xyz.ctypes.data_as(ctypes.c_void_p),
+                                          None if zarr is None else zarr.ctypes.data_as(ctypes.c_void_p),
+                                          charge, mult, ctypes.byref(ob), ctypes.byref(ab)))
+        self.sizes = self.query()
+        self.t = ctypes.c_int(0)
+        return self.sizes
+
+    def query(self):
+        nbf, naux, nact, ng = (ctypes.c_int() for _ in range(4))
+        vnn = ctypes.c_double()
+        _check(load_library().nof_query(self._h, ctypes.byref(nbf), ctypes.byref(naux), ctypes.byref(nact),
+                                        ctypes.byref(ng), ctypes.byref(vnn)))
+        return dict(nbf=nbf.value, naux=naux.value, nact=nact.value, ngamma=ng.value, vnn=vnn.value)
+
+    def _empty(self, *shape):
+        import torch
+        return torch.empty(*shape, dtype=torch.float64, device="cuda")
+
+    def get_SH(self):
+        n = self.sizes["nbf"]
+        S, H = self._empty(n, n), self._empty(n, n)
+        _check(load_library().nof_get_SH(self._h, _dptr(S), _dptr(H)))
+        return S, H
+
+    def get_B(self):
+        s = self.sizes
+        B = self._empty(s["naux"], s["nbf"], s["nbf"])
+        _check(load_library().nof_get_B(self._h, _dptr(B)))
+        return B
+
+    def lowdin(self, Q):
+        n = self.sizes["nbf"]
+        C = self._empty(n, n)
+        _check(load_library().nof_lowdin(self._h, _dptr(Q), _dptr(C)))
+        return C
+
+    def jk(self, C, J=None, K=None):
+        a = self.sizes["nact"]
+        J = self._empty(a, a) if J is None else J
+        K = self._empty(a, a) if K is None else K
+        _check(load_library().nof_jk(self._h, _dptr(C), _dptr(J), _dptr(K)))
+        return J, K
+
+    def energy_grad(self, C, gamma, E=None, g=None, gg=None, grad: bool = True):
+        s = self.sizes
+        E = self._empty(1) if E is None else E
+        if grad:
+            g = self._empty(s["nbf"], s["nbf"]) if g is None else g
+            gg = self._empty(s["ngamma"]) if gg is None else gg
+        _check(load_library().nof_energy_grad(self._h, _dptr(C), _dptr(gamma), _dptr(E),
+                                              _dptr(g) if grad else None, _dptr(gg) if grad else None))
+        return E, g, gg
+
+    def step(self, C, gamma, m, v, out=None):
+        out = self._empty(3) if out is None else out
+        _check(load_library().nof_step(self._h, _dptr(C), _dptr(gamma), _dptr(m), _dptr(v),
+                                       ctypes.byref(self.t), _dptr(out)))
+        return out
+
+    def profile(self, enable: bool = True):
+        _check(load_library().nof_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        ms, cnt, name = ctypes.c_double(), ctypes.c_int(), ctypes.c_char_p()
+        _check(load_library().nof_profile_read(self._h, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(name)))
+        return ms.value, cnt.value, (name.value or b"").decode()
+
+    def sync(self):
+        _check(load_library().nof_sync(self._h))

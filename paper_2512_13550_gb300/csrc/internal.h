@@ -1,0 +1,124 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/nof.h"
+
+// ---------------------------------------------------------------------------------------
+// Error handling: every entry point returns an int status; the message is thread-local.
+// ---------------------------------------------------------------------------------------
+void nof_set_error(const std::string& msg);
+int nof_cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define NOF_CUDA(call)                                                            \
+    do {                                                                          \
+        cudaError_t e__ = (call);                                                 \
+        if (e__ != cudaSuccess) return nof_cuda_fail(e__, #call, __FILE__, __LINE__); \
+    } while (0)
+// Every kernel launch site is followed by NOF_LAUNCH_CHECK, which also counts the launch.
+void nof_count_launch();
+#define NOF_LAUNCH_CHECK()       \
+    do {                         \
+        nof_count_launch();      \
+        NOF_CUDA(cudaGetLastError()); \
+    } while (0)
+#define NOF_TRY(expr)              \
+    do {                           \
+        int r__ = (expr);          \
+        if (r__ != NOF_OK) return r__; \
+    } while (0)
+
+// Device status word bits (written by kernels, read by nof_sync).
+enum { NOF_DEV_NONFINITE = 1, NOF_DEV_TIMEOUT = 2, NOF_DEV_ILLCOND = 4 };
+
+// ---------------------------------------------------------------------------------------
+// Split-precision (exact BF16 digit) storage of the RI tensor; defined in fast.cu.
+// ---------------------------------------------------------------------------------------
+struct FastState;
+
+struct nof_ctx {
+    nof_options opt;
+    cudaStream_t stream;
+    int built;
+    int natom, nbf, naux, nact, ngamma, nelec, npair;
+    // basis description on the device
+    int *fn_atom, *fn_first, *fn_nprim;   // per orbital function
+    double *pexp, *pcoef;                  // orbital primitives (coef normalised in place)
+    int *ax_atom;                          // per aux function
+    double *axexp;
+    double *xyz, *Z;
+    // one-electron and RI data
+    double *S, *H, *vnn;
+    double *B;        // FP64 [X][n][n] (plain path; also the source of the digit planes)
+    // pairing structure
+    int *pair, *slot;
+    // workspaces for an evaluation (plain path)
+    double *T, *b, *d, *J, *K, *D, *W, *HC, *Lam, *lam, *hpp, *A, *Bc;
+    double *s, *t, *ds, *dt, *occ, *E, *part, *ggam, *gorb;
+    size_t part_elems;
+    // step workspaces
+    double *y, *U, *U2, *tmpn;
+    int* status;
+    FastState* fast;
+    // dominant-kernel timing (nof_profile)
+    int prof_on;
+    const char* prof_name;
+    void* prof_events;  // std::vector<std::pair<cudaEvent_t, cudaEvent_t>>*
+};
+
+// Bracket the dominant kernel of an evaluation with timing events when profiling is on.
+int prof_begin(nof_ctx* c, const char* name);
+int prof_end(nof_ctx* c);
+
+// ---------------------------------------------------------------------------------------
+// FP64 building blocks (linalg.cu)
+// ---------------------------------------------------------------------------------------
+// Generic strided FP64 GEMM: C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n).
+// The contraction index may be two-level: k = k1 * K0 + k0 with element offsets
+// k0 * s?k0 + k1 * s?k1 (lets one GEMM run over a composite (P, r) index).
+// Batched over grid z with element strides bA, bB, bC.
+struct Gemm64 {
+    int M = 0, N = 0, K = 0, K0 = 1 << 30, batch = 1;
+    const double* A = nullptr;
+    long long sAm = 0, sAk0 = 0, sAk1 = 0, bA = 0;
+    const double* B = nullptr;
+    long long sBn = 0, sBk0 = 0, sBk1 = 0, bB = 0;
+    double* C = nullptr;
+    long long sCm = 0, sCn = 1, bC = 0;
+    double alpha = 1.0, beta = 0.0;
+};
+int gemm64(const Gemm64& g, cudaStream_t st);
+// Same contraction with the K range split over `splits` CTAs; partial results are written
+// to work[split][M][N] then summed in a fixed order into C (deterministic).
+int gemm64_splitk(const Gemm64& g, int splits, double* work, cudaStream_t st);
+
+int cholesky_inverse(double* V, double* Linv, int X, int* status, cudaStream_t st);
+int newton_schulz_invsqrt(const double* S, double* Xout, double* w1, double* w2, double* w3,
+                          double* w4, int n, int iters, cudaStream_t st);
+int expm_antisym_device(const double* y, double* U, double* w1, double* w2, int n,
+                        cudaStream_t st);
+
+// Integrals (integrals.cu)
+int build_integrals(nof_ctx* c, double* M3 /* [X][n][n] */, double* V2 /* [X][X] */);
+
+// PNOF kernels (pnof.cu)
+int plain_jk(nof_ctx* c, const double* C);
+int plain_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad);
+int pnof_occupations(nof_ctx* c, const double* gamma);
+int pnof_energy(nof_ctx* c);
+int pnof_gamma_grad(nof_ctx* c, double* out);
+int pnof_hpp(nof_ctx* c, const double* C);
+int pnof_lambda_and_g(nof_ctx* c, const double* C, double* g_out);
+int pnof_jk_from_b(nof_ctx* c);
+int pnof_build_W(nof_ctx* c);
+int pnof_on_update(nof_ctx* c, double* gamma);
+int pnof_adam_rotate(nof_ctx* c, double* C, double* m, double* v, int* t, double* out);
+
+// Split-precision path (fast.cu)
+int fast_prepare(nof_ctx* c);
+int fast_release(nof_ctx* c);
+int fast_jk(nof_ctx* c, const double* C);
+int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad);
+int fast_get_B(nof_ctx* c, double* B);

@@ -1,0 +1,461 @@
+// PNOF pairing-coefficient, energy, Lagrangian and gradient kernels (FP64) and the plain FP64
+// evaluation path.
+//
+// Occupations: trigonometric mapping (Occupation Number Optimization subsection):
+//   n_g = (1 + cos^2 gamma_g)/2, h_g = 1 - n_g,
+//   n_{p_i} = h_g cos^2 gamma_{p_1} ... cos^2 gamma_{p_{i-1}} sin^2 gamma_{p_i} (i < N_g),
+//   n_{p_{N_g}} = h_g cos^2 gamma_{p_1} ... cos^2 gamma_{p_{N_g - 1}},
+// which keeps the sum rule of Eq. sum1. sqrt(n) and sqrt(1 - n) are formed from |sin|, |cos|
+// so their gamma-derivatives never divide by a vanishing occupation (one-sided at gamma = 0).
+// Energy: Eq. PNOF, E = 2 sum n_p h_pp + sum A_pq J_pq - sum B_pq K_pq + V_nn, with the
+// spin-restricted PNOF7 coefficients: A_pp = n_p, A_pq = 2 n_p n_q (different subspaces);
+// B_pq = -c_p c_q (same subspace, p != q; c = +sqrt n strong, -sqrt n weak),
+// B_pq = n_p n_q + Phi_p Phi_q (different subspaces; PNOF5 drops Phi), Phi = sqrt(n(1-n)).
+// Lagrangian (Natural Orbital Optimization subsection): lambda = C^T Lambda,
+//   Lambda_mu,p = n_p (HC)_mu,p + sum_P sum_r T^P_mu,r W^P_rp,
+//   W^P_rp = delta_rp D^P_p - B_pr b^P_rp,  D^P = A d^P,
+// and g = 4 (lambda - lambda^T).
+#include <cmath>
+
+#include "internal.h"
+
+namespace {
+
+inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+__device__ __forceinline__ double sgn1(double x) { return x >= 0.0 ? 1.0 : -1.0; }
+
+// One thread per subspace g: s = sqrt(n), t = sqrt(1-n) and their derivatives with respect to
+// the N_g angles of the subspace (ds[p * ncwo + slot]).
+__global__ void k_occupations(const double* gamma, int npair, int ncwo, double* s, double* t,
+                              double* ds, double* dt) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npair) return;
+    const double rt2 = 1.4142135623730950488;
+    double th0 = gamma[g];
+    double s0 = sin(th0), c0 = cos(th0);
+    double sg = sqrt(0.5 * (1.0 + c0 * c0));
+    double tg = fabs(s0) / rt2;
+    double dsg = (-s0 * c0) / (2.0 * sg);
+    double dtg = sgn1(s0) * c0 / rt2;
+    s[g] = sg;
+    t[g] = tg;
+    for (int k = 0; k < ncwo; ++k) {
+        ds[g * ncwo + k] = (k == 0) ? dsg : 0.0;
+        dt[g * ncwo + k] = (k == 0) ? dtg : 0.0;
+    }
+    for (int i = 1; i <= ncwo; ++i) {
+        int p = npair + (i - 1) * npair + (npair - 1 - g);
+        // factors: slot 0 -> tg; slots 1..i-1 -> |cos|; slot i (if i < ncwo) -> |sin|
+        double val = tg;
+        for (int j = 1; j < i; ++j) val *= fabs(cos(gamma[j * npair + g]));
+        if (i < ncwo) val *= fabs(sin(gamma[i * npair + g]));
+        for (int k = 0; k < ncwo; ++k) {
+            double d = 0.0;
+            // derivative of factor k times the product of the others
+            bool has = (k == 0) || (k < i) || (k == i && i < ncwo);
+            if (has) {
+                double dk, prod = 1.0;
+                if (k == 0) dk = dtg; else prod = tg;
+                for (int j = 1; j < i; ++j) {
+                    double th = gamma[j * npair + g];
+                    if (j == k) dk = -sgn1(cos(th)) * sin(th);
+                    else prod *= fabs(cos(th));
+                }
+                if (i < ncwo) {
+                    double th = gamma[i * npair + g];
+                    if (k == i) dk = sgn1(sin(th)) * cos(th);
+                    else prod *= fabs(sin(th));
+                }
+                d = dk * prod;
+            }
+            ds[p * ncwo + k] = d;
+        }
+        double tp = sqrt(1.0 - val * val);
+        s[p] = val;
+        t[p] = tp;
+        for (int k = 0; k < ncwo; ++k) dt[p * ncwo + k] = -val * ds[p * ncwo + k] / tp;
+    }
+}
+
+__global__ void k_coefficients(const double* s, const double* t, const int* pair, const int* slot,
+                               int a, int ipnof, double* occ, double* A, double* Bc) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)a * a) return;
+    int p = (int)(idx / a), q = (int)(idx % a);
+    double np = s[p] * s[p], nq = s[q] * s[q];
+    if (q == 0) occ[p] = np;
+    double av, bv;
+    if (p == q) {
+        av = np;
+        bv = 0.0;
+    } else if (pair[p] == pair[q]) {
+        double cp = slot[p] == 0 ? s[p] : -s[p];
+        double cq = slot[q] == 0 ? s[q] : -s[q];
+        av = 0.0;
+        bv = -cp * cq;
+    } else {
+        av = 2.0 * np * nq;
+        bv = np * nq;
+        if (ipnof == 7) bv += (s[p] * t[p]) * (s[q] * t[q]);
+    }
+    A[idx] = av;
+    Bc[idx] = bv;
+}
+
+// hpp_p = sum_mu C_mu,p (H C)_mu,p
+__global__ void k_hpp(const double* C, const double* HC, int n, int a, double* hpp) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a) return;
+    double s = 0.0;
+    for (int mu = 0; mu < n; ++mu) s = fma(C[(long long)mu * n + p], HC[(long long)mu * a + p], s);
+    hpp[p] = s;
+}
+
+// Single-block energy reduction in a fixed order.
+__global__ void k_energy(const double* occ, const double* hpp, const double* A, const double* Bc,
+                         const double* J, const double* K, const double* vnn, int a, double* E) {
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int p = threadIdx.x; p < a; p += blockDim.x) s += 2.0 * occ[p] * hpp[p];
+    for (long long i = threadIdx.x; i < (long long)a * a; i += blockDim.x) s += A[i] * J[i] - Bc[i] * K[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *E = red[0] + *vnn;
+}
+
+// d^P_p = b^P_pp
+__global__ void k_diag(const double* b, int X, int a, double* d) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)X * a) return;
+    long long P = idx / a;
+    int p = (int)(idx % a);
+    d[idx] = b[P * a * a + (long long)p * a + p];
+}
+
+// K_pq = sum_P (b^P_pq)^2
+__global__ void k_ksum(const double* b, int X, int a, double* K) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long aa = (long long)a * a;
+    if (idx >= aa) return;
+    double s = 0.0;
+    for (int P = 0; P < X; ++P) {
+        double v = b[P * aa + idx];
+        s = fma(v, v, s);
+    }
+    K[idx] = s;
+}
+
+// W^P_rp = delta_rp D^P_p - B_pr b^P_rp
+__global__ void k_build_W(const double* b, const double* D, const double* Bc, int X, int a,
+                          double* W) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long aa = (long long)a * a;
+    if (idx >= (long long)X * aa) return;
+    long long P = idx / aa;
+    long long rp = idx - P * aa;
+    int r = (int)(rp / a), p = (int)(rp % a);
+    double w = -Bc[(long long)p * a + r] * b[idx];
+    if (r == p) w += D[P * a + p];
+    W[idx] = w;
+}
+
+// Lambda = n_p HC + Lam' (in place in Lam)
+__global__ void k_lambda_assemble(const double* HC, const double* occ, int n, int a, double* Lam) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * a) return;
+    int p = (int)(idx % a);
+    Lam[idx] += occ[p] * HC[idx];
+}
+
+__global__ void k_orbital_gradient(const double* lam, int n, double* g) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * n) return;
+    int p = (int)(idx / n), q = (int)(idx % n);
+    g[idx] = 4.0 * (lam[idx] - lam[(long long)q * n + p]);
+}
+
+__global__ void k_zero(double* x, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = 0.0;
+}
+
+// Partial derivatives of E with respect to n_p, c_p and Phi_p (one warp per active orbital p).
+__global__ void k_dE_parts(const double* s, const double* t, const int* pair, const int* slot,
+                           const double* hpp, const double* J, const double* K, int a, int ipnof,
+                           double* out /* [3][a] */) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= a) return;
+    int p = warp;
+    double sn = 0.0, sc = 0.0, sf = 0.0;
+    for (int q = lane; q < a; q += 32) {
+        double Jpq = J[(long long)p * a + q], Kpq = K[(long long)p * a + q];
+        if (pair[q] != pair[p]) {
+            double nq = s[q] * s[q];
+            sn += nq * (2.0 * Jpq - Kpq);
+            sf += (s[q] * t[q]) * Kpq;
+        } else if (q != p) {
+            double cq = slot[q] == 0 ? s[q] : -s[q];
+            sc += cq * Kpq;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        sn += __shfl_xor_sync(0xffffffffu, sn, o);
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        sf += __shfl_xor_sync(0xffffffffu, sf, o);
+    }
+    if (lane == 0) {
+        out[p] = 2.0 * hpp[p] + J[(long long)p * a + p] + 2.0 * sn;
+        out[a + p] = 2.0 * sc;
+        out[2 * a + p] = (ipnof == 7) ? -2.0 * sf : 0.0;
+    }
+}
+
+// dE/dgamma for gamma index k = i * npair + g: sum over the orbitals of subspace g.
+__global__ void k_gamma_chain(const double* s, const double* t, const double* ds, const double* dt,
+                              const int* slot, const double* parts, int npair, int ncwo, int a,
+                              double* out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npair * ncwo) return;
+    int i = k / npair, g = k % npair;
+    double acc = 0.0;
+    for (int m = 0; m <= ncwo; ++m) {
+        int p = (m == 0) ? g : npair + (m - 1) * npair + (npair - 1 - g);
+        double dsk = ds[p * ncwo + i], dtk = dt[p * ncwo + i];
+        double sign = slot[p] == 0 ? 1.0 : -1.0;
+        acc += parts[p] * 2.0 * s[p] * dsk + parts[a + p] * sign * dsk +
+               parts[2 * a + p] * (dsk * t[p] + s[p] * dtk);
+    }
+    out[k] = acc;
+}
+
+__global__ void k_gamma_descent(double* gamma, const double* grad, double lr, int ng) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < ng) gamma[k] -= lr * grad[k];
+}
+
+// ADAM moments and rotation generator y = -lr mhat / (sqrt(vhat) + eps)
+__global__ void k_adam(const double* g, double* m, double* v, double* y, long long nn, double b1,
+                       double b2, double c1, double c2, double lr, double eps) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    double gi = g[i];
+    double mi = b1 * m[i] + (1.0 - b1) * gi;
+    double vi = b2 * v[i] + (1.0 - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    y[i] = -lr * (mi / c1) / (sqrt(vi / c2) + eps);
+}
+
+// out[0] = E, out[1] = ||g||_F, out[2] = max |lambda - lambda^T|
+__global__ void k_step_stats(const double* E, const double* g, const double* lam, int n,
+                             double* out) {
+    __shared__ double r1[256], r2[256];
+    double s = 0.0, mx = 0.0;
+    for (long long i = threadIdx.x; i < (long long)n * n; i += blockDim.x) {
+        s = fma(g[i], g[i], s);
+        int p = (int)(i / n), q = (int)(i % n);
+        mx = fmax(mx, fabs(lam[i] - lam[(long long)q * n + p]));
+    }
+    r1[threadIdx.x] = s;
+    r2[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (threadIdx.x < o) {
+            r1[threadIdx.x] += r1[threadIdx.x + o];
+            r2[threadIdx.x] = fmax(r2[threadIdx.x], r2[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = *E;
+        out[1] = sqrt(r1[0]);
+        out[2] = r2[0];
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+int pnof_occupations(nof_ctx* c, const double* gamma) {
+    k_occupations<<<nblk(c->npair, 128), 128, 0, c->stream>>>(gamma, c->npair, c->opt.ncwo, c->s,
+                                                               c->t, c->ds, c->dt);
+    NOF_LAUNCH_CHECK();
+    long long aa = (long long)c->nact * c->nact;
+    k_coefficients<<<nblk(aa), 256, 0, c->stream>>>(c->s, c->t, c->pair, c->slot, c->nact,
+                                                    c->opt.ipnof, c->occ, c->A, c->Bc);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+int pnof_hpp(nof_ctx* c, const double* C) {
+    const int n = c->nbf, a = c->nact;
+    Gemm64 g;  // HC = H C_a
+    g.M = n; g.N = a; g.K = n;
+    g.A = c->H; g.sAm = n; g.sAk0 = 1;
+    g.B = C; g.sBn = 1; g.sBk0 = n;
+    g.C = c->HC; g.sCm = a; g.sCn = 1;
+    NOF_TRY(gemm64(g, c->stream));
+    k_hpp<<<nblk(a, 128), 128, 0, c->stream>>>(C, c->HC, n, a, c->hpp);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+int pnof_energy(nof_ctx* c) {
+    k_energy<<<1, 1024, 0, c->stream>>>(c->occ, c->hpp, c->A, c->Bc, c->J, c->K, c->vnn, c->nact, c->E);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+int pnof_gamma_grad(nof_ctx* c, double* out) {
+    const int a = c->nact;
+    k_dE_parts<<<nblk((long long)a * 32), 256, 0, c->stream>>>(c->s, c->t, c->pair, c->slot, c->hpp,
+                                                               c->J, c->K, a, c->opt.ipnof, c->part);
+    NOF_LAUNCH_CHECK();
+    k_gamma_chain<<<nblk(c->ngamma, 128), 128, 0, c->stream>>>(c->s, c->t, c->ds, c->dt, c->slot,
+                                                                c->part, c->npair, c->opt.ncwo, a, out);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+int pnof_jk_from_b(nof_ctx* c) {
+    const int X = c->naux, a = c->nact;
+    k_diag<<<nblk((long long)X * a), 256, 0, c->stream>>>(c->b, X, a, c->d);
+    NOF_LAUNCH_CHECK();
+    Gemm64 g;  // J = d^T d
+    g.M = a; g.N = a; g.K = X;
+    g.A = c->d; g.sAm = 1; g.sAk0 = a;
+    g.B = c->d; g.sBn = 1; g.sBk0 = a;
+    g.C = c->J; g.sCm = a; g.sCn = 1;
+    NOF_TRY(gemm64(g, c->stream));
+    k_ksum<<<nblk((long long)a * a), 256, 0, c->stream>>>(c->b, X, a, c->K);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+int pnof_build_W(nof_ctx* c) {
+    const int X = c->naux, a = c->nact;
+    Gemm64 g;  // D[P][p] = sum_r d[P][r] A[p][r]
+    g.M = X; g.N = a; g.K = a;
+    g.A = c->d; g.sAm = a; g.sAk0 = 1;
+    g.B = c->A; g.sBn = a; g.sBk0 = 1;
+    g.C = c->D; g.sCm = a; g.sCn = 1;
+    NOF_TRY(gemm64(g, c->stream));
+    k_build_W<<<nblk((long long)X * a * a), 256, 0, c->stream>>>(c->b, c->D, c->Bc, X, a, c->W);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+// Lam currently holds sum_P T^P W^P; finish Lambda, lambda = C^T Lambda and g.
+int pnof_lambda_and_g(nof_ctx* c, const double* C, double* g_out) {
+    const int n = c->nbf, a = c->nact;
+    k_lambda_assemble<<<nblk((long long)n * a), 256, 0, c->stream>>>(c->HC, c->occ, n, a, c->Lam);
+    NOF_LAUNCH_CHECK();
+    k_zero<<<nblk((long long)n * n), 256, 0, c->stream>>>(c->lam, (long long)n * n);
+    NOF_LAUNCH_CHECK();
+    Gemm64 g;  // lam[q][p] = sum_mu C[mu][q] Lam[mu][p], p < a
+    g.M = n; g.N = a; g.K = n;
+    g.A = C; g.sAm = 1; g.sAk0 = n;
+    g.B = c->Lam; g.sBn = 1; g.sBk0 = a;
+    g.C = c->lam; g.sCm = n; g.sCn = 1;
+    NOF_TRY(gemm64(g, c->stream));
+    k_orbital_gradient<<<nblk((long long)n * n), 256, 0, c->stream>>>(c->lam, n, g_out);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+// Plain FP64 JK stage: T = B C_a, b^P = C_a^T T^P, d, J, K, HC and h_pp.
+int plain_jk(nof_ctx* c, const double* C) {
+    const int n = c->nbf, X = c->naux, a = c->nact;
+    cudaStream_t st = c->stream;
+    {   // T[P][mu][p] = sum_nu B[P][mu][nu] C[nu][p]
+        Gemm64 g;
+        g.M = X * n; g.N = a; g.K = n;
+        g.A = c->B; g.sAm = n; g.sAk0 = 1;
+        g.B = C; g.sBn = 1; g.sBk0 = n;
+        g.C = c->T; g.sCm = a; g.sCn = 1;
+        NOF_TRY(prof_begin(c, "k_gemm64 (half transform T = B C)"));
+        NOF_TRY(gemm64(g, st));
+        NOF_TRY(prof_end(c));
+    }
+    {   // b[P][q][p] = sum_mu C[mu][q] T[P][mu][p]
+        Gemm64 g;
+        g.M = a; g.N = a; g.K = n; g.batch = X;
+        g.A = C; g.sAm = 1; g.sAk0 = n; g.bA = 0;
+        g.B = c->T; g.sBn = 1; g.sBk0 = a; g.bB = (long long)n * a;
+        g.C = c->b; g.sCm = a; g.sCn = 1; g.bC = (long long)a * a;
+        NOF_TRY(gemm64(g, st));
+    }
+    NOF_TRY(pnof_jk_from_b(c));
+    NOF_TRY(pnof_hpp(c, C));
+    return NOF_OK;
+}
+
+// Plain FP64 energy/gradient stage after plain_jk: occupations, coefficients and E at gamma;
+// with want_grad also Lambda, lambda, g (into c->gorb) and dE/dgamma (into c->ggam).
+int plain_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad) {
+    const int n = c->nbf, X = c->naux, a = c->nact;
+    cudaStream_t st = c->stream;
+    NOF_TRY(pnof_occupations(c, gamma));
+    NOF_TRY(pnof_energy(c));
+    if (!want_grad) return NOF_OK;
+    NOF_TRY(pnof_build_W(c));
+    {   // Lam[mu][p] = sum_{P,r} T[P][mu][r] W[P][r][p]  (composite contraction index)
+        Gemm64 g;
+        g.M = n; g.N = a; g.K = X * a; g.K0 = a;
+        g.A = c->T; g.sAm = a; g.sAk0 = 1; g.sAk1 = (long long)n * a;
+        g.B = c->W; g.sBn = 1; g.sBk0 = a; g.sBk1 = (long long)a * a;
+        g.C = c->Lam; g.sCm = a; g.sCn = 1;
+        int tiles = ((n + 63) / 64) * ((a + 63) / 64);
+        int splits = 304 / tiles;
+        if (splits < 1) splits = 1;
+        int maxs = (X * a + 63) / 64;
+        if (splits > maxs) splits = maxs;
+        if ((size_t)splits * n * a > c->part_elems) splits = (int)(c->part_elems / ((size_t)n * a));
+        if (splits < 1) splits = 1;
+        NOF_TRY(gemm64_splitk(g, splits, c->W + (long long)X * a * a, st));
+    }
+    NOF_TRY(pnof_lambda_and_g(c, C, c->gorb));
+    NOF_TRY(pnof_gamma_grad(c, c->ggam));
+    return NOF_OK;
+}
+
+// ON update of an alternating step (see nof.h): on_iters steepest-descent steps on gamma with
+// J, K and h_pp of the current orbitals held fixed.
+int pnof_on_update(nof_ctx* c, double* gamma) {
+    cudaStream_t st = c->stream;
+    for (int it = 0; it < c->opt.on_iters; ++it) {
+        NOF_TRY(pnof_occupations(c, gamma));
+        NOF_TRY(pnof_gamma_grad(c, c->ggam));
+        k_gamma_descent<<<nblk(c->ngamma, 128), 128, 0, st>>>(gamma, c->ggam, c->opt.on_lr, c->ngamma);
+        NOF_LAUNCH_CHECK();
+    }
+    return NOF_OK;
+}
+
+// ADAM update, rotation and statistics (called after the gradient at gamma_new is ready).
+int pnof_adam_rotate(nof_ctx* c, double* C, double* m, double* v, int* t, double* out) {
+    const int n = c->nbf;
+    cudaStream_t st = c->stream;
+    long long nn = (long long)n * n;
+    *t += 1;
+    double c1 = 1.0 - std::pow(c->opt.b1, *t), c2 = 1.0 - std::pow(c->opt.b2, *t);
+    k_adam<<<nblk(nn), 256, 0, st>>>(c->gorb, m, v, c->y, nn, c->opt.b1, c->opt.b2, c1, c2,
+                                     c->opt.lr, c->opt.eps);
+    NOF_LAUNCH_CHECK();
+    k_step_stats<<<1, 256, 0, st>>>(c->E, c->gorb, c->lam, n, out);
+    NOF_LAUNCH_CHECK();
+    NOF_TRY(expm_antisym_device(c->y, c->U, c->U2, c->tmpn, n, st));
+    Gemm64 g;  // tmp = C U
+    g.M = n; g.N = n; g.K = n;
+    g.A = C; g.sAm = n; g.sAk0 = 1;
+    g.B = c->U; g.sBn = 1; g.sBk0 = n;
+    g.C = c->tmpn; g.sCm = n; g.sCn = 1;
+    NOF_TRY(gemm64(g, st));
+    NOF_CUDA(cudaMemcpyAsync(C, c->tmpn, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return NOF_OK;
+}
