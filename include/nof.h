@@ -141,6 +141,14 @@ long long nof_kernel_launches(void);
 int nof_profile(nof_ctx* ctx, int enable);
 int nof_profile_read(nof_ctx* ctx, double* ms, int* launches, const char** name);
 
+/* Self-test of the exact BF16 digit-plane tensor-core GEMM (no paper counterpart): random
+ * digit planes (M x K and N x K, K = 16 katoms) multiplied on tcgen05 with `splits` K chunks
+ * (integer atomics when splits > 1) and by a SIMT integer reference; *max_abs_diff (host)
+ * receives the largest difference of the exact fixed-point results (0 when correct).
+ * Allocates and frees its own buffers; synchronises the device. */
+int nof_selftest_digit_gemm(int M, int N, int katoms, int splits, unsigned int seed,
+                            long long* max_abs_diff);
+
 /* Thread-local description of the last error (never NULL). */
 const char* nof_last_error(void);
 

@@ -68,6 +68,8 @@ SIGNATURES = {
     "nof_kernel_launches": (ctypes.c_longlong, []),
     "nof_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "nof_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nof_selftest_digit_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_uint, _P]),
     "nof_last_error": (ctypes.c_char_p, []),
 }
 
@@ -91,6 +93,13 @@ def load_library():
 def kernel_launches() -> int:
     """Kernels launched by libnof so far in this process (counted at every launch site)."""
     return int(load_library().nof_kernel_launches())
+
+
+def selftest_digit_gemm(M: int, N: int, katoms: int, splits: int = 1, seed: int = 1) -> int:
+    """Largest |difference| between the tcgen05 digit GEMM and a SIMT integer reference."""
+    out = ctypes.c_longlong(-1)
+    _check(load_library().nof_selftest_digit_gemm(M, N, katoms, splits, seed, ctypes.byref(out)))
+    return out.value
 
 
 def _check(rc: int):
