@@ -288,36 +288,47 @@ size_t digit_gemm_smem(int N) {
     return (size_t)kStages * 4 * kStageAtoms * 32 * (kBM + N) + 8 * (2 * kStages + 1) + 16 + 1024;
 }
 
-// A: atom-major planes with rowsA rows (>= M), B: atom-major planes with N rows (padded N),
-// both with katoms_total K atoms. K range per CTA: katoms (split-K chunks = katoms_total/katoms).
-int digit_gemm(const uint16_t* A, int rowsA, const uint16_t* B, int N, int katoms_total, int katoms,
-               int M, int Nvalid, long long* out, long long ldo, bool atomic, int* status,
-               cudaStream_t st) {
+int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, int rowsA, const uint16_t* B, int N,
+                    int katoms_total, int katoms, int M, int Nvalid, long long* out, long long ldo,
+                    bool atomic, int* status) {
     if (N % 16 || N < 16 || N > 128 || katoms < 1 || katoms > 10 || katoms_total % katoms || M <= 0 ||
-        Nvalid > N) {
+        Nvalid > N || rowsA < M) {
         nof_set_error("digit_gemm: unsupported shape");
         return NOF_EINVAL;
     }
-    CUtensorMap ma, mb;
-    NOF_TRY(make_map(&ma, A, rowsA, katoms_total, kBM));
-    NOF_TRY(make_map(&mb, B, N, katoms_total, N));
-    DigitGemmArgs g;
+    NOF_TRY(make_map(&p->ma, A, rowsA, katoms_total, kBM));
+    NOF_TRY(make_map(&p->mb, B, N, katoms_total, N));
+    DigitGemmArgs& g = p->g;
     g.M = M; g.N = N; g.Nvalid = Nvalid; g.katoms = katoms;
     g.out = out; g.ldo = ldo; g.atomic = atomic ? 1 : 0; g.status = status;
     int cols = 32;
     while (cols < 4 * N) cols *= 2;
     g.tmem_cols = cols;
-    size_t smem = digit_gemm_smem(N);
+    p->smem = digit_gemm_smem(N);
+    p->grid = dim3((M + kBM - 1) / kBM, katoms_total / katoms);
     static bool attr_done = false;
     if (!attr_done) {
         NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)digit_gemm_smem(128)));
         attr_done = true;
     }
-    dim3 grid((M + kBM - 1) / kBM, katoms_total / katoms);
-    k_digit_gemm<<<grid, 128, smem, st>>>(ma, mb, g);
+    return NOF_OK;
+}
+
+int digit_gemm_run(const DigitGemmPlan& p, cudaStream_t st) {
+    k_digit_gemm<<<p.grid, 128, p.smem, st>>>(p.ma, p.mb, p.g);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
+}
+
+// A: atom-major planes with rowsA rows (>= M), B: atom-major planes with N rows (padded N),
+// both with katoms_total K atoms. K range per CTA: katoms (split-K chunks = katoms_total/katoms).
+int digit_gemm(const uint16_t* A, int rowsA, const uint16_t* B, int N, int katoms_total, int katoms,
+               int M, int Nvalid, long long* out, long long ldo, bool atomic, int* status,
+               cudaStream_t st) {
+    DigitGemmPlan p;
+    NOF_TRY(digit_gemm_plan(&p, A, rowsA, B, N, katoms_total, katoms, M, Nvalid, out, ldo, atomic, status));
+    return digit_gemm_run(p, st);
 }
 
 // ---------------------------------------------------------------------------------------
