@@ -91,7 +91,7 @@ void free_system(nof_ctx* c) {
     dfree(c->HC); dfree(c->Lam); dfree(c->lam); dfree(c->hpp); dfree(c->A); dfree(c->Bc);
     dfree(c->s); dfree(c->t); dfree(c->ds); dfree(c->dt); dfree(c->occ); dfree(c->E);
     dfree(c->part); dfree(c->ggam); dfree(c->gorb);
-    dfree(c->y); dfree(c->U); dfree(c->U2); dfree(c->tmpn);
+    dfree(c->y); dfree(c->U); dfree(c->U2); dfree(c->tmpn); dfree(c->gwork);
     c->built = 0;
 }
 
@@ -368,6 +368,13 @@ int nof_build_B(nof_ctx* c, int natom, const double* xyz, const double* Z, int c
     NOF_TRY(dalloc(&c->ds, (size_t)a * ncwo)); NOF_TRY(dalloc(&c->dt, (size_t)a * ncwo));
     NOF_TRY(dalloc(&c->E, 1)); NOF_TRY(dalloc(&c->part, 3 * (size_t)a)); NOF_TRY(dalloc(&c->ggam, c->ngamma));
     NOF_TRY(dalloc(&c->y, nn)); NOF_TRY(dalloc(&c->U, nn)); NOF_TRY(dalloc(&c->U2, nn)); NOF_TRY(dalloc(&c->tmpn, nn));
+    {   // split-K scratch for the small FP64 GEMMs (n x n, n x a, a x a, X x a outputs)
+        size_t big = nn > (size_t)X * a ? nn : (size_t)X * a;
+        size_t cap = 304 * big;
+        if (cap > ((size_t)32 << 20)) cap = (size_t)32 << 20;
+        c->gwork_cap = cap;
+        NOF_TRY(dalloc(&c->gwork, cap));
+    }
     if (!plain) {
         r = fast_prepare(c);
         if (r != NOF_OK) {

@@ -28,7 +28,7 @@ struct FastState {
     unsigned* maxT3; int* eT3;  // per mu
     uint16_t* Td3;              // [4][X ap / 16][n][16]
     long long* bfix;            // [X ap][ap]
-    float2* Wdf;                // [X][ap][ap]  W^P_rp at (P, r, p)
+    float2* Wdf;                // [X][ap][ap]  W^P_rp at (P, p, r)
     unsigned* maxW; int* eW3;   // per p
     uint16_t* Wd3;              // [4][X ap / 16][ap][16]
     long long* Lfix;            // [n][ap]
@@ -62,10 +62,19 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
     return quick_two_sum(p, e);
 }
 __device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+// 2^e as an FP32 (exact for -126 <= e <= 127; ldexpf handles the rest)
+__device__ __forceinline__ float pow2f(int e) {
+    if (e >= -126 && e <= 127) return __int_as_float((e + 127) << 23);
+    return ldexpf(1.0f, e);
+}
 // exact integer (|V| < 2^62) times 2^e as a double-float
 __device__ __forceinline__ float2 df_from_fix(long long V, int e) {
     float hi = (float)V;
     float lo = (float)(V - (long long)hi);
+    if (e >= -126 && e <= 127) {
+        float s = pow2f(e);
+        return make_float2(hi * s, lo * s);
+    }
     return make_float2(ldexpf(hi, e), ldexpf(lo, e));
 }
 __device__ __forceinline__ double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
@@ -158,13 +167,28 @@ __global__ void k_T2_digits(const long long* Tfix, const int* eB, const int* eC,
         eBs[i] = eB[(long long)P * n + i];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n * ap; i += blockDim.x) {
-        long long v = Tfix[base + i];
-        int mu = i / ap, p = i - mu * ap;
-        Ts[mu * (ap + 1) + p] = v;
-        float f = fabsf(ldexpf((float)v, eBs[mu] + eC[p] - 40));
-        atomicMax(&colmax[p], __float_as_uint(f));
-        atomicMax(&rowmax[mu], __float_as_uint(f));
+    {   // warp w takes rows mu = w, w + nwarps, ...; lane l takes columns p = l, l + 32, ...
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        float cm[4] = {0.f, 0.f, 0.f, 0.f};  // ap <= 128
+        float sC[4];
+        for (int j = 0; j < 4; ++j) sC[j] = (lane + 32 * j < ap) ? pow2f(eC[lane + 32 * j] - 40) : 0.f;
+        for (int mu = warp; mu < n; mu += nw) {
+            float rm = 0.f;
+            float sB = pow2f(eBs[mu]);
+            for (int j = 0; j < 4; ++j) {
+                int p = lane + 32 * j;
+                if (p >= ap) break;
+                long long v = Tfix[base + (long long)mu * ap + p];
+                Ts[mu * (ap + 1) + p] = v;
+                float f = fabsf((float)v * sC[j] * sB);
+                cm[j] = fmaxf(cm[j], f);
+                rm = fmaxf(rm, f);
+            }
+            for (int o = 16; o; o >>= 1) rm = fmaxf(rm, __shfl_xor_sync(0xffffffffu, rm, o));
+            if (lane == 0) rowmax[mu] = __float_as_uint(rm);
+        }
+        for (int j = 0; j < 4; ++j)
+            if (lane + 32 * j < ap) atomicMax(&colmax[lane + 32 * j], __float_as_uint(cm[j]));
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) atomicMax(&maxT3[i], rowmax[i]);
@@ -235,12 +259,14 @@ __global__ void __launch_bounds__(256) k_perP_JK(const long long* bfix, const in
     }
 }
 
+// out[i] = sum_b part[b][i], one warp per output, fixed order (lane-strided then a fixed tree)
 __global__ void k_reduce_parts(const double* part, int nparts, int cnt, double* out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (i >= cnt) return;
     double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += part[(long long)b * cnt + i];
-    out[i] = s;
+    for (int b = lane; b < nparts; b += 32) s += part[(long long)b * cnt + i];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[i] = s;
 }
 
 __global__ void k_to_df(const double* src, int cnt, float2* dst) {
@@ -252,7 +278,7 @@ __global__ void k_to_df(const double* src, int cnt, float2* dst) {
 }
 
 // Persistent blocks over P: D^P = A d^P, W^P_rp = delta_rp D^P_p - B_pr b^P_rp (double-float),
-// stored at (P, r, p); per-p maxima for the digit scale of GEMM3's B operand.
+// stored at (P, p, r); per-p maxima for the digit scale of GEMM3's B operand.
 __global__ void __launch_bounds__(256) k_perP_W(const long long* bfix, const int* e2, const int* eC,
                                                 const float2* Adf, const float2* Bcdf, int X, int a, int ap,
                                                 float2* Wdf, unsigned* maxW) {
@@ -271,14 +297,20 @@ __global__ void __launch_bounds__(256) k_perP_W(const long long* bfix, const int
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < aa; idx += blockDim.x) {
-            int r = idx / ap, p = idx - r * ap;
+            int p = idx / ap, r = idx - p * ap;  // stored at (P, p, r)
             float2 w = make_float2(0.f, 0.f);
             if (r < a && p < a) {
                 w = df_neg(df_mul(Bcdf[p * a + r], b_val(bfix, e2, eC, ap, P, r, p)));
                 if (r == p) w = df_add(w, Ds[p]);
             }
             Wdf[(long long)P * aa + idx] = w;
-            atomicMax(&wmax[p], __float_as_uint(fabsf(w.x)));
+            unsigned wb = __float_as_uint(fabsf(w.x));
+            if ((ap & 31) == 0) {  // the whole warp shares p
+                for (int o = 16; o; o >>= 1) wb = max(wb, __shfl_xor_sync(0xffffffffu, wb, o));
+                if ((threadIdx.x & 31) == 0) atomicMax(&wmax[p], wb);
+            } else {
+                atomicMax(&wmax[p], wb);
+            }
         }
     }
     __syncthreads();
@@ -290,12 +322,14 @@ __global__ void k_W_digits(const float2* Wdf, const int* eW3, int X, int ap, uin
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long tot = (long long)X * ap * ap;
     if (idx >= tot) return;
-    long long Pr = idx / ap;  // P ap + r
-    int p = (int)(idx - Pr * ap);
+    long long Pp = idx / ap;  // P ap + p
+    int r = (int)(idx - Pp * ap);
+    long long P = Pp / ap;
+    int p = (int)(Pp - P * ap);
     float2 w = Wdf[idx];
     int s = 32 - eW3[p];
     long long Y = __float2ll_rn(ldexpf(w.x, s)) + __float2ll_rn(ldexpf(w.y, s));
-    put_digits(Wd3, (int)((long long)X * ap / 16), ap, p, Pr, Y);
+    put_digits(Wd3, (int)((long long)X * ap / 16), ap, p, P * ap + r, Y);
 }
 
 __global__ void k_lambda_from_fix(const long long* Lfix, const int* eT3, const int* eW3, int n, int a, int ap,
@@ -417,9 +451,9 @@ int fast_jk(nof_ctx* c, const double* C) {
     NOF_TRY(digit_gemm_run(f->g2, st));
     k_perP_JK<<<f->nblk, 256, 0, st>>>(f->bfix, f->e2, f->eC, X, a, ap, f->Jpart, f->Kpart);
     NOF_LAUNCH_CHECK();
-    k_reduce_parts<<<nblk(a * a), 256, 0, st>>>(f->Jpart, f->nblk, a * a, c->J);
+    k_reduce_parts<<<nblk((long long)a * a * 32), 256, 0, st>>>(f->Jpart, f->nblk, a * a, c->J);
     NOF_LAUNCH_CHECK();
-    k_reduce_parts<<<nblk(a * a), 256, 0, st>>>(f->Kpart, f->nblk, a * a, c->K);
+    k_reduce_parts<<<nblk((long long)a * a * 32), 256, 0, st>>>(f->Kpart, f->nblk, a * a, c->K);
     NOF_LAUNCH_CHECK();
     return pnof_hpp(c, C);
 }

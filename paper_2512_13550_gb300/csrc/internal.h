@@ -60,6 +60,8 @@ struct nof_ctx {
     size_t part_elems;
     // step workspaces
     double *y, *U, *U2, *tmpn;
+    double* gwork;  // split-K scratch of the FP64 GEMMs
+    size_t gwork_cap;
     int* status;
     FastState* fast;
     // dominant-kernel timing (nof_profile)
@@ -88,6 +90,10 @@ struct Gemm64 {
     double* C = nullptr;
     long long sCm = 0, sCn = 1, bC = 0;
     double alpha = 1.0, beta = 0.0;
+    // Optional scratch for an automatic split-K when the output has too few 64x64 tiles to fill
+    // the GPU (FP64 runs at 2 FMA/clk/SM on GB300, so a single CTA per tile is far too slow).
+    double* work = nullptr;
+    size_t work_cap = 0;  // doubles
 };
 int gemm64(const Gemm64& g, cudaStream_t st);
 // Same contraction with the K range split over `splits` CTAs; partial results are written

@@ -86,6 +86,36 @@ __global__ void __launch_bounds__(256) k_gemm64(Gemm64 g, int splits, double* wo
     }
 }
 
+// Skinny outputs: 16x16 tile per CTA, one output per thread, K range split over grid z.
+// Writes raw partials to work[split][M][N].
+__global__ void __launch_bounds__(256) k_gemm64_small(Gemm64 g, int splits, double* work) {
+    __shared__ double As[16][17];
+    __shared__ double Bs[16][17];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * 16, n0 = blockIdx.x * 16, split = blockIdx.z;
+    int kchunk = (g.K + splits - 1) / splits;
+    kchunk = (kchunk + 15) / 16 * 16;
+    const int k_lo = split * kchunk, k_hi = min(g.K, k_lo + kchunk);
+    const bool a_kfast = (g.sAk0 == 1);
+    double acc = 0.0;
+    for (int kt = k_lo; kt < k_hi; kt += 16) {
+        {   // A tile: rows m0.., k kt..
+            int mm = a_kfast ? ty : tx, kk = a_kfast ? tx : ty;
+            int m = m0 + mm, k = kt + kk;
+            As[kk][mm] = (m < g.M && k < k_hi) ? g.A[a_off(g, m, k)] : 0.0;
+            int nn = (g.sBn == 1) ? tx : ty, kb = (g.sBn == 1) ? ty : tx;
+            int n = n0 + nn, kq = kt + kb;
+            Bs[kb][nn] = (n < g.N && kq < k_hi) ? g.B[b_off(g, n, kq)] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) acc = fma(As[kk][ty], Bs[kk][tx], acc);
+        __syncthreads();
+    }
+    int m = m0 + ty, n = n0 + tx;
+    if (m < g.M && n < g.N) work[((long long)split * g.M + m) * g.N + n] = acc;
+}
+
 __global__ void k_splitk_reduce(Gemm64 g, int splits, const double* work) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long MN = (long long)g.M * g.N;
@@ -207,6 +237,24 @@ Gemm64 square_gemm(const double* A, const double* B, double* C, int n) {
 
 int gemm64(const Gemm64& g, cudaStream_t st) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return NOF_OK;
+    long long tiles = (long long)((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM) * g.batch;
+    if (g.work && g.batch == 1 && tiles < 304) {
+        // small output: 16x16 tiles and a K split so that about 600 CTAs share the work
+        long long t16 = (long long)((g.N + 15) / 16) * ((g.M + 15) / 16);
+        long long splits = (608 + t16 - 1) / t16;
+        long long maxs = (g.K + 15) / 16;
+        if (splits > maxs) splits = maxs;
+        long long cap = (long long)(g.work_cap / ((size_t)g.M * g.N));
+        if (splits > cap) splits = cap;
+        if (splits >= 1 && cap >= 1) {
+            dim3 grid((g.N + 15) / 16, (g.M + 15) / 16, (unsigned)splits);
+            k_gemm64_small<<<grid, 256, 0, st>>>(g, (int)splits, g.work);
+            NOF_LAUNCH_CHECK();
+            k_splitk_reduce<<<blocks_for((long long)g.M * g.N), 256, 0, st>>>(g, (int)splits, g.work);
+            NOF_LAUNCH_CHECK();
+            return NOF_OK;
+        }
+    }
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
     if (grid.y > 65535u || grid.z > 65535u) {
         nof_set_error("gemm64: grid too large");

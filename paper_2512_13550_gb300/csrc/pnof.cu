@@ -103,13 +103,14 @@ __global__ void k_coefficients(const double* s, const double* t, const int* pair
     Bc[idx] = bv;
 }
 
-// hpp_p = sum_mu C_mu,p (H C)_mu,p
+// hpp_p = sum_mu C_mu,p (H C)_mu,p, one warp per p
 __global__ void k_hpp(const double* C, const double* HC, int n, int a, double* hpp) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    int p = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (p >= a) return;
     double s = 0.0;
-    for (int mu = 0; mu < n; ++mu) s = fma(C[(long long)mu * n + p], HC[(long long)mu * a + p], s);
-    hpp[p] = s;
+    for (int mu = lane; mu < n; mu += 32) s = fma(C[(long long)mu * n + p], HC[(long long)mu * a + p], s);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) hpp[p] = s;
 }
 
 // Single-block energy reduction in a fixed order.
@@ -299,8 +300,9 @@ int pnof_hpp(nof_ctx* c, const double* C) {
     g.A = c->H; g.sAm = n; g.sAk0 = 1;
     g.B = C; g.sBn = 1; g.sBk0 = n;
     g.C = c->HC; g.sCm = a; g.sCn = 1;
+    g.work = c->gwork; g.work_cap = c->gwork_cap;
     NOF_TRY(gemm64(g, c->stream));
-    k_hpp<<<nblk(a, 128), 128, 0, c->stream>>>(C, c->HC, n, a, c->hpp);
+    k_hpp<<<nblk((long long)a * 32), 256, 0, c->stream>>>(C, c->HC, n, a, c->hpp);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
@@ -331,6 +333,7 @@ int pnof_jk_from_b(nof_ctx* c) {
     g.A = c->d; g.sAm = 1; g.sAk0 = a;
     g.B = c->d; g.sBn = 1; g.sBk0 = a;
     g.C = c->J; g.sCm = a; g.sCn = 1;
+    g.work = c->gwork; g.work_cap = c->gwork_cap;
     NOF_TRY(gemm64(g, c->stream));
     k_ksum<<<nblk((long long)a * a), 256, 0, c->stream>>>(c->b, X, a, c->K);
     NOF_LAUNCH_CHECK();
@@ -344,6 +347,7 @@ int pnof_build_W(nof_ctx* c) {
     g.A = c->d; g.sAm = a; g.sAk0 = 1;
     g.B = c->A; g.sBn = a; g.sBk0 = 1;
     g.C = c->D; g.sCm = a; g.sCn = 1;
+    g.work = c->gwork; g.work_cap = c->gwork_cap;
     NOF_TRY(gemm64(g, c->stream));
     k_build_W<<<nblk((long long)X * a * a), 256, 0, c->stream>>>(c->b, c->D, c->Bc, X, a, c->W);
     NOF_LAUNCH_CHECK();
@@ -362,6 +366,7 @@ int pnof_lambda_and_g(nof_ctx* c, const double* C, double* g_out) {
     g.A = C; g.sAm = 1; g.sAk0 = n;
     g.B = c->Lam; g.sBn = 1; g.sBk0 = a;
     g.C = c->lam; g.sCm = n; g.sCn = 1;
+    g.work = c->gwork; g.work_cap = c->gwork_cap;
     NOF_TRY(gemm64(g, c->stream));
     k_orbital_gradient<<<nblk((long long)n * n), 256, 0, c->stream>>>(c->lam, n, g_out);
     NOF_LAUNCH_CHECK();
@@ -455,6 +460,7 @@ int pnof_adam_rotate(nof_ctx* c, double* C, double* m, double* v, int* t, double
     g.A = C; g.sAm = n; g.sAk0 = 1;
     g.B = c->U; g.sBn = 1; g.sBk0 = n;
     g.C = c->tmpn; g.sCm = n; g.sCn = 1;
+    g.work = c->gwork; g.work_cap = c->gwork_cap;
     NOF_TRY(gemm64(g, st));
     NOF_CUDA(cudaMemcpyAsync(C, c->tmpn, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
     return NOF_OK;
