@@ -149,6 +149,22 @@ int nof_profile_read(nof_ctx* ctx, double* ms, int* launches, const char** name)
 int nof_selftest_digit_gemm(int M, int N, int katoms, int splits, unsigned int seed,
                             long long* max_abs_diff);
 
+/* J and K exactly as nof_jk computes them in FP64, without a context and without allocating
+ * any device memory (the paper has no counterpart; this is a deployment variant).
+ * Some callers cannot call cudaMalloc: an application whose device memory is owned by another
+ * allocator (a framework's caching pool that has reserved the GPU, or a fixed memory budget),
+ * or code that must not stall or fail on an allocation mid-run. This entry point keeps its
+ * scratch in a fixed 48 MiB device array inside the library (held by every GPU that loads the
+ * library until exit) and only launches kernels on `stream` (a cudaStream_t; NULL = default).
+ *   B: device FP64 [naux][nbf][nbf] RI tensor (e.g. from nof_get_B); C: device FP64
+ *   [nbf][nbf] orbitals (first nact columns used); J, K: device FP64 [nact][nact] outputs.
+ * Limit: naux*nbf*nact + naux*nact*(nact + 1) <= 6291456 doubles, else NOF_EINVAL.
+ * The first call on each device (with that device current) looks up the array's device
+ * address; make it before any stream capture. Calls share the array: calls that overlap on
+ * the GPU race. Asynchronous like every other call. */
+int nof_jk_static(int naux, int nbf, int nact, const double* B, const double* C, double* J,
+                  double* K, void* stream);
+
 /* Thread-local description of the last error (never NULL). */
 const char* nof_last_error(void);
 

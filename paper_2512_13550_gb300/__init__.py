@@ -70,6 +70,7 @@ SIGNATURES = {
     "nof_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
     "nof_selftest_digit_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_uint, _P]),
+    "nof_jk_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]),
     "nof_last_error": (ctypes.c_char_p, []),
 }
 
