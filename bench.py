@@ -38,13 +38,15 @@ ACC_GATE = 1e-6
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--precision", choices=["auto", "split", "fp64"], default="auto")
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time plain API calls instead of CUDA-graph replays of one evaluation")
     ap.add_argument("--profile-evals", type=int, default=0,
                     help="profiling mode: build, warm up, run this many evaluations inside the NVTX "
                          "range 'evals' (for ncu --nvtx --nvtx-include evals/) and exit")
@@ -242,24 +244,43 @@ def main():
                           "E": float(E.item())}), flush=True)
         return 0
 
-    def timed_loop(c, steps, warmup, profile=False):
+    def timed_loop(c, steps, warmup, profile=False, graph=False):
+        """Time `steps` evaluations, L2 flushed before each; returns (ms, kernel launches, profile).
+        With graph=True one evaluation is captured in a CUDA graph and replayed (the library makes no
+        host synchronisation or allocation inside an evaluation, so the capture holds all of it)."""
         for _ in range(warmup):
             c.energy_grad(C, gam, E, g, gg)
         torch.cuda.synchronize()
-        if profile:
-            c.profile(True)
+        run = lambda: c.energy_grad(C, gam, E, g, gg)
+        per_eval = None
+        if graph:
+            cg = torch.cuda.CUDAGraph()
+            l0 = nof.kernel_launches()
+            with torch.cuda.graph(cg, stream=stream):
+                c.energy_grad(C, gam, E, g, gg)
+            per_eval = nof.kernel_launches() - l0
+            torch.cuda.synchronize()
+            for _ in range(warmup):
+                cg.replay()
+            torch.cuda.synchronize()
+            run = cg.replay
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         l0 = nof.kernel_launches()
         for i in range(steps):
             flush.fill_(float(i))
             evs[i][0].record(stream)
-            c.energy_grad(C, gam, E, g, gg)
+            run()
             evs[i][1].record(stream)
         torch.cuda.synchronize()
-        launches = nof.kernel_launches() - l0
+        launches = nof.kernel_launches() - l0 if per_eval is None else per_eval * steps
         ms = sum(a.elapsed_time(b) for a, b in evs)
-        prof = c.profile_read() if profile else None
-        if profile:
+        prof = None
+        if profile:  # the dominant kernel, timed with CUDA events inside the library on its stream
+            c.profile(True)
+            for i in range(steps):
+                flush.fill_(float(i))
+                c.energy_grad(C, gam, E, g, gg)
+            prof = c.profile_read()
             c.profile(False)
         return ms, launches, prof
 
@@ -267,7 +288,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        ms, launches, prof = timed_loop(ctx, args.steps, args.warmup, profile=True)
+        ms, launches, prof = timed_loop(ctx, args.steps, args.warmup, profile=True, graph=not args.no_graph)
     torch.cuda.synchronize()
     t_max = ms
     if dist is not None:
@@ -284,7 +305,7 @@ def main():
         ms64, steps64 = ms, args.steps
     else:
         ctx64 = make_ctx(nof.PREC_FP64)
-        ms64, _, _ = timed_loop(ctx64, args.fp64_steps, 1)
+        ms64, _, _ = timed_loop(ctx64, args.fp64_steps, 3, graph=not args.no_graph)
         steps64 = args.fp64_steps
         E64 = float(E.item())
         dE = abs(E_fast - E64)
@@ -326,6 +347,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "path": "split-bf16 tcgen05" if prec else "plain fp64",
                    "l2": "flushed (256 MiB write) before every timed step",
+                   "timing": "CUDA-graph replay of one evaluation per step" if not args.no_graph
+                             else "one API call per step",
                    "parallelism": f"replicas x{world}"},
         "accuracy": {"max_abs_dE_vs_fp64_gpu": dE, "max_abs_dg_vs_fp64_gpu": dg,
                      "gate": ACC_GATE, "pass": bool(dE <= ACC_GATE and dg <= ACC_GATE)},
@@ -357,6 +380,10 @@ def _peaks():
 # measured on GB300: 1.19 TFLOP/s), x 152 SMs x 2.07 GHz x 2 FLOP = 1.26 TFLOP/s.
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
+# DRAM bytes (read + write) of one GEMM1 launch on this workload from an ncu capture of the current
+# kernel (profiles/), or None when the kernel has changed since the counters were taken.
+TRAFFIC_GEMM1_BYTES = None
+
 
 def roofline(prec, s, ms_per_launch, name):
     n, X, a = s["nbf"], s["naux"], s["nact"]
@@ -368,8 +395,15 @@ def roofline(prec, s, ms_per_launch, name):
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None, "traffic": None,
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe-measured rate)"}
-    return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None,
-            "frac": None, "traffic": None, "peak_source": src}
+    # half transform GEMM1: reads the four BF16 digit planes of B (8 bytes per element of B) and
+    # writes T as double-floats (8 bytes per element of T)
+    nbytes = 8.0 * X * n * n + 8.0 * X * n * a
+    achieved = nbytes / (ms_per_launch / 1e3) / 1e9
+    peak = peaks["hbm_gbs"]
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": TRAFFIC_GEMM1_BYTES,
+            "algorithmic_bytes": nbytes, "ms_per_launch": ms_per_launch,
+            "peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
 
 if __name__ == "__main__":

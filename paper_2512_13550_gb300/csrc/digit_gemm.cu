@@ -10,13 +10,14 @@
 // accumulators hold the level sums exactly. The epilogue returns the exact integer
 // V = S_0 256^3 + S_1 256^2 + S_2 256 + S_3 (|V| < 2^49), value = 2^{e_m + f_n - 40} V.
 //
-// Storage ("atom-major"): plane p, K atom t (16 consecutive k), row r, lane j at
-// ((p * katoms + t) * rows + r) * 16 + j. A TMA box (16, 128 rows, 2 atoms, 4 planes) lands in
-// shared memory as eight 4 KB K-major SWIZZLE_32B atoms, the canonical layout the MMA reads.
+// Storage: digit_gemm.h's tile-major core-matrix layout, so one pipeline stage (2 K atoms x 4
+// planes) of a 128-row tile of A, or of all N rows of B, is one contiguous block that a single
+// bulk copy (cp.async.bulk) places in shared memory in the no-swizzle K-major canonical layout
+// (core matrices of 8 rows x 16 bytes; 128 bytes between K-adjacent, 256 bytes between
+// row-adjacent core matrices).
 //
-// Roles (128 threads): warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs, all four warps
-// drain TMEM (warp w owns lanes 32w..32w+31 = tile rows). Every mbarrier wait is bounded; on
-// timeout the kernel sets NOF_DEV_TIMEOUT in the status word, drains what it issued and exits.
+// Every mbarrier wait is bounded; on timeout the kernel sets NOF_DEV_TIMEOUT in the status word,
+// lets what it issued land and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -31,7 +32,6 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kStageAtoms = 2;
-constexpr int kStages = 2;
 constexpr unsigned long long kTimeoutNs = 4000000000ull;  // 4 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -72,23 +72,22 @@ __device__ bool mbar_wait(uint32_t a, uint32_t phase, int* status) {
         }
     }
 }
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, int c3, uint32_t mbar) {
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
     asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(mbar)
         : "memory");
 }
-// Shared-memory matrix descriptor: K-major, SWIZZLE_32B atoms of 8 rows x 32 B (SBO = 256 B).
+// Shared-memory matrix descriptor: K-major, no swizzle; core matrices of 8 rows x 16 bytes,
+// 128 bytes between K-adjacent (leading byte offset) and 256 bytes between row-adjacent
+// (stride byte offset) core matrices.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(256 >> 4) << 32;   // stride byte offset between 8-row groups
+    d |= (uint64_t)(128 >> 4) << 16;   // leading byte offset: next core matrix along K
+    d |= (uint64_t)(256 >> 4) << 32;   // stride byte offset: next 8-row group
     d |= (uint64_t)1 << 46;            // descriptor version for tcgen05
-    d |= (uint64_t)6 << 61;            // SWIZZLE_32B
-    return d;
+    return d;                          // swizzle mode 0 (none)
 }
 // Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int N) {
@@ -120,38 +119,63 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// One CTA computes a 128-row x N tile over K atoms [blockIdx.y * katoms, +katoms).
-__global__ void __launch_bounds__(128, 2)
-k_digit_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-             DigitGemmArgs g) {
+// exact integer V (|V| < 2^62) times 2^e as a double-float (hi, lo), from 24-bit pieces
+__device__ __forceinline__ float2 fix_to_df(long long V, int e) {
+    const float p0 = (float)(int)(V & 0xFFFFFF);
+    const float p1 = (float)(int)((V >> 24) & 0xFFFFFF) * 16777216.0f;
+    const float p2 = (float)(int)(V >> 48) * 281474976710656.0f;
+    float s = p2 + p1;  // two-sum of p2 and p1, then add p0
+    float bb = s - p2;
+    float err = (p2 - (s - bb)) + (p1 - bb) + p0;
+    float hi = s + err;
+    float lo = err - (hi - s);
+    if (e >= -126 && e <= 127) {  // exact scaling by a normal power of two
+        const float sc = __int_as_float((e + 127) << 23);
+        return make_float2(hi * sc, lo * sc);
+    }
+    return make_float2(ldexpf(hi, e), ldexpf(lo, e));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+// Persistent, warp-specialised tile loop. Tiles are (128-row block, K chunk) pairs, row block
+// fastest. Warp 0 lane 0 streams A and B stages with TMA through a ring of g.stages shared-memory
+// slots that carries over from one tile to the next; warp 1 lane 0 issues the 10 digit-product
+// MMAs per K atom into one of g.nbuf TMEM accumulator sets (4 levels x N columns each); warps
+// 2..5 drain a finished set (lanes 32*(w%4)..+31), hand it back, and write the exact int64 result.
+// With two sets the drain of tile i overlaps the MMAs of tile i + 1.
+__global__ void __launch_bounds__(192, 1)
+k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, DigitGemmArgs g) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1 KB alignment for the swizzled atoms
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int N = g.N;
+    const int N = g.N, S = g.stages, NB = g.nbuf;
     const uint32_t a_stage_bytes = 4u * kStageAtoms * kBM * 32u;
     const uint32_t b_stage_bytes = 4u * kStageAtoms * (uint32_t)N * 32u;
     unsigned char* sA = smem;
-    unsigned char* sB = smem + kStages * a_stage_bytes;
-    uint64_t* bars = (uint64_t*)(sB + kStages * b_stage_bytes);  // full[2], empty[2], done
-    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages + 1);
-
+    unsigned char* sB = smem + S * a_stage_bytes;
+    uint64_t* bars = (uint64_t*)(sB + S * b_stage_bytes);  // full[S] empty[S] tfull[2] tempty[2]
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile_m = blockIdx.x;
-    const int katom0 = blockIdx.y * g.katoms;
-    const int nk = (g.katoms + kStageAtoms - 1) / kStageAtoms;  // pipeline iterations
-    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kStages]),
-                   done = smem_u32(&bars[2 * kStages]);
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[S]),
+                   tfull0 = smem_u32(&bars[2 * S]), tempty0 = smem_u32(&bars[2 * S + 2]);
+    const int ntiles = g.tiles_m * g.kchunks;
+    const int nk = (g.katoms + kStageAtoms - 1) / kStageAtoms;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull0 + 8 * b, 1);
+            mbar_init(tempty0 + 8 * b, 4);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"((uint32_t)g.tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -162,172 +186,218 @@ k_digit_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
 
-    if (warp == 0 && lane == 0) {
-        // TMA producer
-        for (int it = 0; it < nk && ok; ++it) {
-            int s = it % kStages;
-            if (it >= kStages) ok = mbar_wait(empty0 + 8 * s, ((it / kStages) - 1) & 1, g.status);
-            if (!ok) break;
-            // a TMA box always delivers all kStageAtoms atoms (zero-filled past the tensor end)
-            uint32_t bytes = (uint32_t)kStageAtoms * 4u * 32u * (kBM + (uint32_t)N);
-            mbar_expect_tx(full0 + 8 * s, bytes);
-            int ka = katom0 + it * kStageAtoms;
-            tma_load_4d(smem_u32(sA + s * a_stage_bytes), &mapA, 0, tile_m * kBM, ka, 0, full0 + 8 * s);
-            tma_load_4d(smem_u32(sB + s * b_stage_bytes), &mapB, 0, 0, ka, 0, full0 + 8 * s);
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const int tm = tile % g.tiles_m, kc = tile / g.tiles_m;
+                for (int st = 0; st < nk && ok; ++st, ++it) {
+                    const int s = it % S;
+                    if (it >= S) ok = mbar_wait(empty0 + 8 * s, ((it / S) - 1) & 1, g.status);
+                    if (!ok) break;
+                    const int ka = kc * g.katoms + st * kStageAtoms;
+                    const int atoms = min(kStageAtoms, g.katoms - st * kStageAtoms);
+                    const uint32_t abytes = (uint32_t)atoms * 4u * kBM * 32u;
+                    const uint32_t bbytes = (uint32_t)atoms * 4u * (uint32_t)N * 32u;
+                    mbar_expect_tx(full0 + 8 * s, abytes + bbytes);
+                    bulk_load(smem_u32(sA + s * a_stage_bytes),
+                              A + digit_offset(kBM, g.katoms_total, (long long)tm * kBM, (long long)ka * 16, 0),
+                              abytes, full0 + 8 * s);
+                    bulk_load(smem_u32(sB + s * b_stage_bytes),
+                              B + digit_offset(N, g.katoms_total, 0, (long long)ka * 16, 0), bbytes,
+                              full0 + 8 * s);
+                }
+            }
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer: level l = i + j accumulates in TMEM columns [l N, (l+1) N)
-        const uint32_t idesc = idesc_bf16(N);
-        bool started[4] = {false, false, false, false};
-        for (int it = 0; it < nk && ok; ++it) {
-            int s = it % kStages;
-            ok = mbar_wait(full0 + 8 * s, (it / kStages) & 1, g.status);
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            const uint32_t idesc = idesc_bf16(N);
+            int it = 0, local = 0;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++local) {
+                const int b = local % NB, use = local / NB;
+                if (use > 0) ok = mbar_wait(tempty0 + 8 * b, (use - 1) & 1, g.status);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(b * 4 * N);
+                bool started[4] = {false, false, false, false};
+                for (int st = 0; st < nk && ok; ++st, ++it) {
+                    const int s = it % S;
+                    ok = mbar_wait(full0 + 8 * s, (it / S) & 1, g.status);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const int atoms = min(kStageAtoms, g.katoms - st * kStageAtoms);
+                    const uint32_t aBase = smem_u32(sA + s * a_stage_bytes), bBase = smem_u32(sB + s * b_stage_bytes);
+                    for (int t = 0; t < atoms; ++t) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                            for (int j = 0; j < 4 - i; ++j) {
+                                const int l = i + j;
+                                // stage block order [atom][plane][rows x 16]
+                                uint64_t ad = sdesc(aBase + (uint32_t)((t * 4 + i) * kBM * 32));
+                                uint64_t bd = sdesc(bBase + (uint32_t)((t * 4 + j) * N * 32));
+                                mma_bf16(acc + (uint32_t)(l * N), ad, bd, idesc, started[l] ? 1u : 0u);
+                                started[l] = true;
+                            }
+                        }
+                    }
+                    mma_commit(empty0 + 8 * s);
+                }
+                if (ok) mma_commit(tfull0 + 8 * b);
+            }
+        }
+    } else {  // epilogue warps 2..5
+        const int q = warp & 3;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        int local = 0;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++local) {
+            const int b = local % NB, use = local / NB;
+            ok = mbar_wait(tfull0 + 8 * b, use & 1, g.status);
             if (!ok) break;
             tc_fence_after();
-            int atoms = min(kStageAtoms, g.katoms - it * kStageAtoms);
-            uint32_t aBase = smem_u32(sA + s * a_stage_bytes), bBase = smem_u32(sB + s * b_stage_bytes);
-            for (int t = 0; t < atoms; ++t) {
+            const int tm = tile % g.tiles_m;
+            const int row = tm * kBM + q * 32 + lane;
+            long long* orow = g.out + (long long)row * g.ldo;
+            const uint32_t acc = tmem + lane_base + (uint32_t)(b * 4 * N);
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float v0[16], v1[16], v2[16], v3[16];
+                tmem_ld16(acc + (uint32_t)c0, v0);
+                tmem_ld16(acc + (uint32_t)(N + c0), v1);
+                tmem_ld16(acc + (uint32_t)(2 * N + c0), v2);
+                tmem_ld16(acc + (uint32_t)(3 * N + c0), v3);
+                tmem_wait_ld();
+                if (c0 + 16 >= N) {  // last chunk read: hand the accumulator set back
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+                }
+                if (row < g.M) {
+                    // level sums are exact integers below 2^24: 32-bit conversions, 64-bit integer sum
+                    // (64-bit int <-> float conversions run at the FP64 rate on this part)
+                    long long V[16];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                    for (int j = 0; j < 16; ++j)
+                        V[j] = ((long long)__float2int_rn(v0[j]) << 24) + ((long long)__float2int_rn(v1[j]) << 16) +
+                               ((long long)__float2int_rn(v2[j]) << 8) + (long long)__float2int_rn(v3[j]);
+                    if (g.outf) {
+                        // exact V -> double-float: 24-bit pieces convert exactly with 32-bit conversions
+                        const int er = g.erow[row] - 40;
+                        float2* frow = g.outf + (long long)row * g.ldo + c0;
 #pragma unroll
-                    for (int j = 0; j < 4 - i; ++j) {
-                        int l = i + j;
-                        // box layout [plane][atom][rows][16]: plane stride = atoms-in-box * rows * 32 B
-                        uint64_t ad = sdesc(aBase + (uint32_t)((i * kStageAtoms + t) * kBM * 32));
-                        uint64_t bd = sdesc(bBase + (uint32_t)((j * kStageAtoms + t) * N * 32));
-                        mma_bf16(tmem + (uint32_t)(l * N), ad, bd, idesc, started[l] ? 1u : 0u);
-                        started[l] = true;
+                        for (int j = 0; j < 16; j += 2) {
+                            float4 pr;
+                            float2 r0 = fix_to_df(V[j], er + g.ecol[c0 + j]);
+                            float2 r1 = fix_to_df(V[j + 1], er + g.ecol[c0 + j + 1]);
+                            pr.x = r0.x; pr.y = r0.y; pr.z = r1.x; pr.w = r1.y;
+                            if (c0 + j + 1 < g.Nvalid)
+                                *reinterpret_cast<float4*>(frow + j) = pr;
+                            else if (c0 + j < g.Nvalid)
+                                frow[j] = r0;
+                        }
+                    } else if (g.atomic) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < g.Nvalid) atomicAdd((unsigned long long*)(orow + c0 + j), (unsigned long long)V[j]);
+                    } else if (c0 + 16 <= g.Nvalid && (g.ldo & 1) == 0) {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 2)
+                            *reinterpret_cast<longlong2*>(orow + c0 + j) = make_longlong2(V[j], V[j + 1]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < g.Nvalid) orow[c0 + j] = V[j];
                     }
                 }
             }
-            mma_commit(empty0 + 8 * s);  // frees the stage once these MMAs retire
         }
-        if (ok) mma_commit(done);
     }
     __syncwarp();
-    // epilogue: every warp drains its 32 TMEM lanes
-    bool ready = mbar_wait(done, 0, g.status);
-    tc_fence_after();
-    if (ready) {
-        const int row = tile_m * kBM + warp * 32 + lane;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        for (int c0 = 0; c0 < N; c0 += 16) {
-            float v0[16], v1[16], v2[16], v3[16];
-            tmem_ld16(tmem + lane_base + (uint32_t)c0, v0);
-            tmem_ld16(tmem + lane_base + (uint32_t)(N + c0), v1);
-            tmem_ld16(tmem + lane_base + (uint32_t)(2 * N + c0), v2);
-            tmem_ld16(tmem + lane_base + (uint32_t)(3 * N + c0), v3);
-            tmem_wait_ld();
-            if (row < g.M) {
-                long long* orow = g.out + (long long)row * g.ldo;
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    int col = c0 + q;
-                    if (col >= g.Nvalid) continue;
-                    long long V = __float2ll_rn(v0[q]) * 16777216LL + __float2ll_rn(v1[q]) * 65536LL +
-                                  __float2ll_rn(v2[q]) * 256LL + __float2ll_rn(v3[q]);
-                    if (g.atomic)
-                        atomicAdd((unsigned long long*)(orow + col), (unsigned long long)V);
-                    else
-                        orow[col] = V;
-                }
-            }
-        }
+    if (!ok) {
+        // a wait gave up: give the copies and MMAs this CTA issued time to land (bounded) before
+        // the shared memory and TMEM go away
+        unsigned long long t0 = globaltimer();
+        while (globaltimer() - t0 < 200000ull) __nanosleep(1000);
     }
     tc_fence_before();
     __syncthreads();
-    if (!ok && threadIdx.x == 0) {
-        // a wait gave up: let the copies this CTA issued land before the shared memory goes away
-        for (int s = 0; s < kStages; ++s) (void)mbar_wait(full0 + 8 * s, 0, g.status);
-    }
-    __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)g.tmem_cols));
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
-    return fn;
-}
-
-// 4-D map over atom-major digit planes: (16 lanes, rows, K atoms, 4 planes), box (16, box_rows,
-// stage atoms, 4), SWIZZLE_32B.
-int make_map(CUtensorMap* m, const void* base, int rows, int katoms, int box_rows) {
-    auto enc = get_encode();
-    if (!enc) {
-        nof_set_error("cuTensorMapEncodeTiled is unavailable from the driver");
-        return NOF_ECUDA;
-    }
-    cuuint64_t dims[4] = {16, (cuuint64_t)rows, (cuuint64_t)katoms, 4};
-    cuuint64_t strides[3] = {32, (cuuint64_t)rows * 32, (cuuint64_t)katoms * rows * 32};
-    cuuint32_t box[4] = {16, (cuuint32_t)box_rows, (cuuint32_t)kStageAtoms, 4};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        nof_set_error("cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
-        return NOF_ECUDA;
-    }
-    return NOF_OK;
-}
-
 }  // namespace
 
+static int stages_for(int N) { return N <= 64 ? 4 : 3; }
+
 size_t digit_gemm_smem(int N) {
-    return (size_t)kStages * 4 * kStageAtoms * 32 * (kBM + N) + 8 * (2 * kStages + 1) + 16 + 1024;
+    return (size_t)stages_for(N) * 4 * kStageAtoms * 32 * (kBM + N) + 8 * (2 * stages_for(N) + 4) + 16 + 1024;
 }
 
-int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, int rowsA, const uint16_t* B, int N,
-                    int katoms_total, int katoms, int M, int Nvalid, long long* out, long long ldo,
-                    bool atomic, int* status) {
+int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int N, int katoms_total,
+                    int katoms, int M, int Nvalid, long long* out, long long ldo, bool atomic, int* status) {
     if (N % 16 || N < 16 || N > 128 || katoms < 1 || katoms > 10 || katoms_total % katoms || M <= 0 ||
-        Nvalid > N || rowsA < M) {
+        Nvalid > N) {
         nof_set_error("digit_gemm: unsupported shape");
         return NOF_EINVAL;
     }
-    NOF_TRY(make_map(&p->ma, A, rowsA, katoms_total, kBM));
-    NOF_TRY(make_map(&p->mb, B, N, katoms_total, N));
+    p->A = A;
+    p->B = B;
     DigitGemmArgs& g = p->g;
-    g.M = M; g.N = N; g.Nvalid = Nvalid; g.katoms = katoms;
+    g.outf = nullptr;
+    g.erow = nullptr;
+    g.ecol = nullptr;
+    g.M = M; g.N = N; g.Nvalid = Nvalid; g.katoms = katoms; g.katoms_total = katoms_total;
     g.out = out; g.ldo = ldo; g.atomic = atomic ? 1 : 0; g.status = status;
+    g.stages = stages_for(N);
+    g.nbuf = (8 * N <= 512) ? 2 : 1;
+    g.tiles_m = (M + kBM - 1) / kBM;
+    g.kchunks = katoms_total / katoms;
     int cols = 32;
-    while (cols < 4 * N) cols *= 2;
+    while (cols < g.nbuf * 4 * N) cols *= 2;
     g.tmem_cols = cols;
     p->smem = digit_gemm_smem(N);
-    p->grid = dim3((M + kBM - 1) / kBM, katoms_total / katoms);
-    static bool attr_done = false;
-    if (!attr_done) {
-        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)digit_gemm_smem(128)));
-        attr_done = true;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        NOF_CUDA(cudaGetDevice(&dev));
+        NOF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     }
+    if (p->smem > 200 * 1024) {
+        nof_set_error("digit_gemm: shared memory plan too large");
+        return NOF_EINVAL;
+    }
+    const int ntiles = g.tiles_m * g.kchunks;
+    p->grid = dim3(ntiles < sms ? ntiles : sms, 1);
+    return NOF_OK;
+}
+
+int digit_gemm_plan_scaled(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int N, int katoms, int M,
+                           int Nvalid, float2* out, long long ldo, const int* erow, const int* ecol, int* status) {
+    if (ldo & 1) {
+        nof_set_error("digit_gemm: the scaled output needs an even leading dimension");
+        return NOF_EINVAL;
+    }
+    NOF_TRY(digit_gemm_plan(p, A, B, N, katoms, katoms, M, Nvalid, nullptr, ldo, false, status));
+    p->g.outf = out;
+    p->g.erow = erow;
+    p->g.ecol = ecol;
     return NOF_OK;
 }
 
 int digit_gemm_run(const DigitGemmPlan& p, cudaStream_t st) {
-    k_digit_gemm<<<p.grid, 128, p.smem, st>>>(p.ma, p.mb, p.g);
+    k_digit_gemm<<<p.grid, 192, p.smem, st>>>(p.A, p.B, p.g);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
 
-// A: atom-major planes with rowsA rows (>= M), B: atom-major planes with N rows (padded N),
-// both with katoms_total K atoms. K range per CTA: katoms (split-K chunks = katoms_total/katoms).
-int digit_gemm(const uint16_t* A, int rowsA, const uint16_t* B, int N, int katoms_total, int katoms,
-               int M, int Nvalid, long long* out, long long ldo, bool atomic, int* status,
-               cudaStream_t st) {
+// A: digit planes with M rows (tiles of 128), B: digit planes with N rows (one tile), both with
+// katoms_total K atoms. Each tile accumulates katoms atoms (split-K chunks = katoms_total/katoms).
+int digit_gemm(const uint16_t* A, const uint16_t* B, int N, int katoms_total, int katoms, int M,
+               int Nvalid, long long* out, long long ldo, bool atomic, int* status, cudaStream_t st) {
     DigitGemmPlan p;
-    NOF_TRY(digit_gemm_plan(&p, A, rowsA, B, N, katoms_total, katoms, M, Nvalid, out, ldo, atomic, status));
+    NOF_TRY(digit_gemm_plan(&p, A, B, N, katoms_total, katoms, M, Nvalid, out, ldo, atomic, status));
     return digit_gemm_run(p, st);
 }
 
@@ -340,34 +410,36 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
     return x;
 }
-// plane 0 digits in [-256, 256], others in [-128, 128]; rows >= valid_rows are zero
-__global__ void k_random_digits(uint16_t* P, int rows, int valid_rows, int katoms, uint32_t seed) {
+// element (row r, k, plane) of a digit tensor: plane 0 digits in [-256, 256], others in
+// [-128, 128]; rows >= valid_rows are zero
+__global__ void k_random_digits(uint16_t* P, int RT, int rows_pad, int valid_rows, int katoms, uint32_t seed) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long per_plane = (long long)katoms * rows * 16;
+    long long per_plane = (long long)rows_pad * katoms * 16;
     if (idx >= 4 * per_plane) return;
     int plane = (int)(idx / per_plane);
     long long rem = idx - plane * per_plane;
-    int r = (int)((rem / 16) % rows);
+    long long r = rem / (katoms * 16);
+    long long k = rem - r * (katoms * 16);
     int range = plane == 0 ? 513 : 257;
     int v = (int)(hash32((uint32_t)idx * 2654435761u + seed) % (uint32_t)range) - range / 2;
     if (r >= valid_rows) v = 0;
     __nv_bfloat16 b = __int2bfloat16_rn(v);
-    P[idx] = *reinterpret_cast<uint16_t*>(&b);
+    P[digit_offset(RT, katoms, r, k, plane)] = *reinterpret_cast<uint16_t*>(&b);
 }
-__device__ __forceinline__ int digit_at(const uint16_t* P, int rows, int katoms, int plane, int r, int k) {
-    uint16_t u = P[(((long long)plane * katoms + k / 16) * rows + r) * 16 + (k & 15)];
+__device__ __forceinline__ int digit_at(const uint16_t* P, int RT, int katoms, int plane, int r, int k) {
+    uint16_t u = P[digit_offset(RT, katoms, r, k, plane)];
     __nv_bfloat16 b = *reinterpret_cast<__nv_bfloat16*>(&u);
     return (int)__bfloat162float(b);
 }
-__global__ void k_ref_digit_gemm(const uint16_t* A, int rowsA, const uint16_t* B, int rowsB, int katoms,
-                                 int M, int N, long long* out) {
+__global__ void k_ref_digit_gemm(const uint16_t* A, const uint16_t* B, int NB, int katoms, int M, int N,
+                                 long long* out) {
     int m = blockIdx.x * blockDim.x + threadIdx.x, n = blockIdx.y;
     if (m >= M || n >= N) return;
     long long S[4] = {0, 0, 0, 0};
     for (int k = 0; k < katoms * 16; ++k)
         for (int i = 0; i < 4; ++i)
             for (int j = 0; j < 4 - i; ++j)
-                S[i + j] += (long long)digit_at(A, rowsA, katoms, i, m, k) * digit_at(B, rowsB, katoms, j, n, k);
+                S[i + j] += (long long)digit_at(A, 128, katoms, i, m, k) * digit_at(B, NB, katoms, j, n, k);
     out[(long long)m * N + n] = S[0] * 16777216LL + S[1] * 65536LL + S[2] * 256LL + S[3];
 }
 __global__ void k_max_absdiff(const long long* a, const long long* b, long long n, unsigned long long* out) {
@@ -387,6 +459,7 @@ extern "C" int nof_selftest_digit_gemm(int M, int N, int katoms, int splits, uns
         return NOF_EINVAL;
     }
     int rowsA = (M + 127) / 128 * 128;
+    const long long na = digit_elems(128, M, katoms), nb = digit_elems(N, N, katoms);
     uint16_t *A = nullptr, *B = nullptr;
     long long *C1 = nullptr, *C2 = nullptr;
     unsigned long long* dmax = nullptr;
@@ -394,8 +467,8 @@ extern "C" int nof_selftest_digit_gemm(int M, int N, int katoms, int splits, uns
     int r = NOF_OK;
     auto fail = [&](cudaError_t e, const char* w) { r = nof_cuda_fail(e, w, __FILE__, __LINE__); };
     cudaError_t e;
-    if ((e = cudaMalloc(&A, 4ull * katoms * rowsA * 16 * 2)) != cudaSuccess) fail(e, "malloc A");
-    if (r == NOF_OK && (e = cudaMalloc(&B, 4ull * katoms * N * 16 * 2)) != cudaSuccess) fail(e, "malloc B");
+    if ((e = cudaMalloc(&A, 2ull * na)) != cudaSuccess) fail(e, "malloc A");
+    if (r == NOF_OK && (e = cudaMalloc(&B, 2ull * nb)) != cudaSuccess) fail(e, "malloc B");
     if (r == NOF_OK && (e = cudaMalloc(&C1, 8ull * M * N)) != cudaSuccess) fail(e, "malloc C1");
     if (r == NOF_OK && (e = cudaMalloc(&C2, 8ull * M * N)) != cudaSuccess) fail(e, "malloc C2");
     if (r == NOF_OK && (e = cudaMalloc(&dmax, 8)) != cudaSuccess) fail(e, "malloc max");
@@ -404,13 +477,12 @@ extern "C" int nof_selftest_digit_gemm(int M, int N, int katoms, int splits, uns
         cudaMemset(dmax, 0, 8);
         cudaMemset(status, 0, 4);
         cudaMemset(C1, 0, 8ull * M * N);
-        long long na = 4ll * katoms * rowsA * 16, nb = 4ll * katoms * N * 16;
-        k_random_digits<<<(unsigned)((na + 255) / 256), 256>>>(A, rowsA, M, katoms, seed);
-        k_random_digits<<<(unsigned)((nb + 255) / 256), 256>>>(B, N, N, katoms, seed ^ 0x9e3779b9u);
-        r = digit_gemm(A, rowsA, B, N, katoms, katoms / splits, M, N, C1, N, splits > 1, status, 0);
+        k_random_digits<<<(unsigned)((na + 255) / 256), 256>>>(A, 128, rowsA, M, katoms, seed);
+        k_random_digits<<<(unsigned)((nb + 255) / 256), 256>>>(B, N, N, N, katoms, seed ^ 0x9e3779b9u);
+        r = digit_gemm(A, B, N, katoms, katoms / splits, M, N, C1, N, splits > 1, status, 0);
     }
     if (r == NOF_OK) {
-        k_ref_digit_gemm<<<dim3((M + 127) / 128, N), 128>>>(A, rowsA, B, N, katoms, M, N, C2);
+        k_ref_digit_gemm<<<dim3((M + 127) / 128, N), 128>>>(A, B, N, katoms, M, N, C2);
         k_max_absdiff<<<(unsigned)(((long long)M * N + 255) / 256), 256>>>(C1, C2, (long long)M * N, dmax);
         unsigned long long h = 0;
         int hs = 0;
