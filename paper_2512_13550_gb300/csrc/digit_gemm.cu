@@ -119,17 +119,22 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// exact integer V (|V| < 2^62) times 2^e as a double-float (hi, lo), from 24-bit pieces
-__device__ __forceinline__ float2 fix_to_df(long long V, int e) {
-    const float p0 = (float)(int)(V & 0xFFFFFF);
-    const float p1 = (float)(int)((V >> 24) & 0xFFFFFF) * 16777216.0f;
-    const float p2 = (float)(int)(V >> 48) * 281474976710656.0f;
-    float s = p2 + p1;  // two-sum of p2 and p1, then add p0
-    float bb = s - p2;
-    float err = (p2 - (s - bb)) + (p1 - bb) + p0;
-    float hi = s + err;
-    float lo = err - (hi - s);
-    if (e >= -126 && e <= 127) {  // exact scaling by a normal power of two
+// 2^{e} (S0 2^24 + S1 2^16 + S2 2^8 + S3) as a double-float, for level sums S_k that are exact
+// integers below 2^24 held in FP32: error-free two-sums, no integer conversions.
+__device__ __forceinline__ float2 levels_to_df(float S0, float S1, float S2, float S3, int e) {
+    const float a = S0 * 16777216.0f, b = S1 * 65536.0f, c = S2 * 256.0f;
+    float h = a + b;
+    float bb = h - a;
+    float err = (a - (h - bb)) + (b - bb);
+    float h2 = h + c;
+    bb = h2 - h;
+    err += (h - (h2 - bb)) + (c - bb);
+    float h3 = h2 + S3;
+    bb = h3 - h2;
+    err += (h2 - (h3 - bb)) + (S3 - bb);
+    const float hi = h3 + err;
+    const float lo = err - (hi - h3);
+    if (e >= -126 && e <= 127) {
         const float sc = __int_as_float((e + 127) << 23);
         return make_float2(hi * sc, lo * sc);
     }
@@ -146,7 +151,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
 // MMAs per K atom into one of g.nbuf TMEM accumulator sets (4 levels x N columns each); warps
 // 2..5 drain a finished set (lanes 32*(w%4)..+31), hand it back, and write the exact int64 result.
 // With two sets the drain of tile i overlaps the MMAs of tile i + 1.
-__global__ void __launch_bounds__(192, 1)
+constexpr int kEpiWarps = 8;  // two per TMEM lane group, each owning half of the columns
+
+__global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
 k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, DigitGemmArgs g) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -157,6 +164,9 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
     unsigned char* sB = smem + S * a_stage_bytes;
     uint64_t* bars = (uint64_t*)(sB + S * b_stage_bytes);  // full[S] empty[S] tfull[2] tempty[2]
     uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 4);
+    // per epilogue warp: 32 rows x 16 double-floats (+1 pad) to turn row-per-thread results into
+    // coalesced row segments
+    float2* stage_out = (float2*)(((uintptr_t)(tmem_slot + 4) + 15) & ~(uintptr_t)15);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[S]),
                    tfull0 = smem_u32(&bars[2 * S]), tempty0 = smem_u32(&bars[2 * S + 2]);
@@ -170,7 +180,7 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull0 + 8 * b, 1);
-            mbar_init(tempty0 + 8 * b, 4);
+            mbar_init(tempty0 + 8 * b, kEpiWarps);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -246,8 +256,13 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                 if (ok) mma_commit(tfull0 + 8 * b);
             }
         }
-    } else {  // epilogue warps 2..5
+    } else {  // epilogue warps 2..2+kEpiWarps-1: lane group q, column half h
         const int q = warp & 3;
+        const int h = (warp - 2) / 4;
+        // column halves for N >= 32 (a chunk may run up to 7 columns past its half, still inside
+        // the allocation); for N = 16 the second warp of each lane group has no columns
+        const int cbeg = N >= 32 ? h * (N / 2) : 0;
+        const int cend = N >= 32 ? cbeg + N / 2 : (h ? 0 : N);
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         int local = 0;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++local) {
@@ -259,19 +274,14 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
             const int row = tm * kBM + q * 32 + lane;
             long long* orow = g.out + (long long)row * g.ldo;
             const uint32_t acc = tmem + lane_base + (uint32_t)(b * 4 * N);
-            for (int c0 = 0; c0 < N; c0 += 16) {
+            for (int c0 = cbeg; c0 < cend; c0 += 16) {
                 float v0[16], v1[16], v2[16], v3[16];
                 tmem_ld16(acc + (uint32_t)c0, v0);
                 tmem_ld16(acc + (uint32_t)(N + c0), v1);
                 tmem_ld16(acc + (uint32_t)(2 * N + c0), v2);
                 tmem_ld16(acc + (uint32_t)(3 * N + c0), v3);
                 tmem_wait_ld();
-                if (c0 + 16 >= N) {  // last chunk read: hand the accumulator set back
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(tempty0 + 8 * b);
-                }
-                if (row < g.M) {
+                if (!g.outf && row < g.M) {
                     // level sums are exact integers below 2^24: 32-bit conversions, 64-bit integer sum
                     // (64-bit int <-> float conversions run at the FP64 rate on this part)
                     long long V[16];
@@ -279,36 +289,56 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                     for (int j = 0; j < 16; ++j)
                         V[j] = ((long long)__float2int_rn(v0[j]) << 24) + ((long long)__float2int_rn(v1[j]) << 16) +
                                ((long long)__float2int_rn(v2[j]) << 8) + (long long)__float2int_rn(v3[j]);
-                    if (g.outf) {
-                        // exact V -> double-float: 24-bit pieces convert exactly with 32-bit conversions
-                        const int er = g.erow[row] - 40;
-                        float2* frow = g.outf + (long long)row * g.ldo + c0;
-#pragma unroll
-                        for (int j = 0; j < 16; j += 2) {
-                            float4 pr;
-                            float2 r0 = fix_to_df(V[j], er + g.ecol[c0 + j]);
-                            float2 r1 = fix_to_df(V[j + 1], er + g.ecol[c0 + j + 1]);
-                            pr.x = r0.x; pr.y = r0.y; pr.z = r1.x; pr.w = r1.y;
-                            if (c0 + j + 1 < g.Nvalid)
-                                *reinterpret_cast<float4*>(frow + j) = pr;
-                            else if (c0 + j < g.Nvalid)
-                                frow[j] = r0;
-                        }
-                    } else if (g.atomic) {
+                    const int lim = min(cend, g.Nvalid);  // columns owned by this warp
+                    if (g.atomic) {
 #pragma unroll
                         for (int j = 0; j < 16; ++j)
-                            if (c0 + j < g.Nvalid) atomicAdd((unsigned long long*)(orow + c0 + j), (unsigned long long)V[j]);
-                    } else if (c0 + 16 <= g.Nvalid && (g.ldo & 1) == 0) {
+                            if (c0 + j < lim) atomicAdd((unsigned long long*)(orow + c0 + j), (unsigned long long)V[j]);
+                    } else if (c0 + 16 <= lim && (g.ldo & 1) == 0) {
 #pragma unroll
                         for (int j = 0; j < 16; j += 2)
                             *reinterpret_cast<longlong2*>(orow + c0 + j) = make_longlong2(V[j], V[j + 1]);
                     } else {
 #pragma unroll
                         for (int j = 0; j < 16; ++j)
-                            if (c0 + j < g.Nvalid) orow[c0 + j] = V[j];
+                            if (c0 + j < lim) orow[c0 + j] = V[j];
                     }
                 }
+                if (g.outf) {
+                    // exact V -> scaled double-float (24-bit pieces, 32-bit conversions), staged in
+                    // shared memory, then written as whole 128-byte row segments (8 lanes per row)
+                    float2* st = stage_out + (warp - 2) * 32 * 17;
+                    const int cw = min(16, cend - c0);  // columns of this chunk owned by the warp
+                    const int er = row < g.M ? g.erow[row] - 40 : 0;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (j < cw) st[lane * 17 + j] = levels_to_df(v0[j], v1[j], v2[j], v3[j], er + g.ecol[c0 + j]);
+                    __syncwarp();
+                    const int rbase = tm * kBM + q * 32;
+#pragma unroll
+                    for (int it2 = 0; it2 < 4; ++it2) {
+                        const int rr = it2 * 8 + (lane >> 2);  // 8 rows per pass, 4 lanes per row
+                        const int cc = (lane & 3) * 4;         // 4 double-floats (32 bytes) per lane
+                        const int grow = rbase + rr;
+                        if (cc >= cw) continue;
+                        if (grow < g.M && c0 + cc + 3 < g.Nvalid && cc + 3 < cw) {
+                            float2* dst = g.outf + (long long)grow * g.ldo + c0 + cc;
+                            const float2* src = st + rr * 17 + cc;
+                            reinterpret_cast<float4*>(dst)[0] = make_float4(src[0].x, src[0].y, src[1].x, src[1].y);
+                            reinterpret_cast<float4*>(dst)[1] = make_float4(src[2].x, src[2].y, src[3].x, src[3].y);
+                        } else if (grow < g.M) {
+                            for (int u = 0; u < 4; ++u)
+                                if (c0 + cc + u < g.Nvalid && cc + u < cw)
+                                    g.outf[(long long)grow * g.ldo + c0 + cc + u] = st[rr * 17 + cc + u];
+                        }
+                    }
+                    __syncwarp();
+                }
             }
+            // every TMEM read of this set is complete: hand it back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty0 + 8 * b);
         }
     }
     __syncwarp();
@@ -328,10 +358,11 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
 
 }  // namespace
 
-static int stages_for(int N) { return N <= 64 ? 4 : 3; }
+static int stages_for(int N) { return N > 64 ? 2 : 3; }
 
 size_t digit_gemm_smem(int N) {
-    return (size_t)stages_for(N) * 4 * kStageAtoms * 32 * (kBM + N) + 8 * (2 * stages_for(N) + 4) + 16 + 1024;
+    return (size_t)stages_for(N) * 4 * kStageAtoms * 32 * (kBM + N) + 8 * (2 * stages_for(N) + 4) + 16 + 16 +
+           kEpiWarps * 32 * 17 * sizeof(float2) + 1024;
 }
 
 int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int N, int katoms_total,
@@ -362,9 +393,9 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
         int dev = 0;
         NOF_CUDA(cudaGetDevice(&dev));
         NOF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     }
-    if (p->smem > 200 * 1024) {
+    if (p->smem > 220 * 1024) {
         nof_set_error("digit_gemm: shared memory plan too large");
         return NOF_EINVAL;
     }
@@ -387,7 +418,7 @@ int digit_gemm_plan_scaled(DigitGemmPlan* p, const uint16_t* A, const uint16_t* 
 }
 
 int digit_gemm_run(const DigitGemmPlan& p, cudaStream_t st) {
-    k_digit_gemm<<<p.grid, 192, p.smem, st>>>(p.A, p.B, p.g);
+    k_digit_gemm<<<p.grid, 64 + 32 * kEpiWarps, p.smem, st>>>(p.A, p.B, p.g);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
