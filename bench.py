@@ -290,11 +290,8 @@ def main():
     with ClockSampler(local) as clk:
         ms, launches, prof = timed_loop(ctx, args.steps, args.warmup, profile=True, graph=not args.no_graph)
     torch.cuda.synchronize()
-    t_max = ms
+    value, t_max = aggregate(ms, args.steps, world, dist, device="cuda")
     if dist is not None:
-        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
         dist.barrier()
     E_fast = float(E.item())
     g_fast = g.clone()
@@ -336,7 +333,6 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    value = world * args.steps / (t_max / 1e3)
     dom_ms, dom_launches, dom_name = prof
     roof = roofline(prec, s, dom_ms / max(dom_launches, 1), dom_name)
     line = {
@@ -366,6 +362,18 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def aggregate(ms_local: float, steps: int, world: int, dist=None, device=None):
+    """Whole-job throughput of `world` replicas: each rank evaluated `steps` of its own geometries
+    in ms_local; the job takes as long as the slowest rank. Returns (value per second, t_max ms)."""
+    t_max = ms_local
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    return world * steps / (t_max / 1e3), t_max
 
 
 def _peaks():

@@ -427,7 +427,8 @@ int nof_lowdin(nof_ctx* c, const double* Q, double* C) {
     }
     const int n = c->nbf;
     // workspaces: y, U, U2, tmpn as Newton-Schulz scratch, lam as the result S^{-1/2}
-    NOF_TRY(newton_schulz_invsqrt(c->S, c->lam, c->y, c->U, c->U2, c->tmpn, n, 40, c->stream));
+    NOF_TRY(newton_schulz_invsqrt(c->S, c->lam, c->y, c->U, c->U2, c->tmpn, n, 40, c->stream, c->gwork,
+                                  c->gwork_cap));
     Gemm64 g;
     g.M = n; g.N = n; g.K = n;
     g.A = c->lam; g.sAm = n; g.sAk0 = 1;

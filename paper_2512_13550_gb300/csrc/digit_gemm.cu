@@ -141,6 +141,15 @@ __device__ __forceinline__ float2 levels_to_df(float S0, float S1, float S2, flo
     return make_float2(ldexpf(hi, e), ldexpf(lo, e));
 }
 
+// sum of two double-floats
+__device__ __forceinline__ float2 df2_add(float2 a, float2 b) {
+    float s = a.x + b.x;
+    float bb = s - a.x;
+    float e = (a.x - (s - bb)) + (b.x - bb) + a.y + b.y;
+    float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t a) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
@@ -228,8 +237,8 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                 if (use > 0) ok = mbar_wait(tempty0 + 8 * b, (use - 1) & 1, g.status);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t acc = tmem + (uint32_t)(b * 4 * N);
-                bool started[4] = {false, false, false, false};
+                const uint32_t acc = tmem + (uint32_t)(b * g.kparts * 4 * N);
+                uint32_t started = 0u;  // bit (part * 4 + level): accumulator already initialised
                 for (int st = 0; st < nk && ok; ++st, ++it) {
                     const int s = it % S;
                     ok = mbar_wait(full0 + 8 * s, (it / S) & 1, g.status);
@@ -238,16 +247,19 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                     const int atoms = min(kStageAtoms, g.katoms - st * kStageAtoms);
                     const uint32_t aBase = smem_u32(sA + s * a_stage_bytes), bBase = smem_u32(sB + s * b_stage_bytes);
                     for (int t = 0; t < atoms; ++t) {
+                        const int part = (st * kStageAtoms + t) / g.apart;
+                        const uint32_t pacc = acc + (uint32_t)(part * 4 * N);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
 #pragma unroll
                             for (int j = 0; j < 4 - i; ++j) {
                                 const int l = i + j;
+                                const uint32_t bit = 1u << (part * 4 + l);
                                 // stage block order [atom][plane][rows x 16]
                                 uint64_t ad = sdesc(aBase + (uint32_t)((t * 4 + i) * kBM * 32));
                                 uint64_t bd = sdesc(bBase + (uint32_t)((t * 4 + j) * N * 32));
-                                mma_bf16(acc + (uint32_t)(l * N), ad, bd, idesc, started[l] ? 1u : 0u);
-                                started[l] = true;
+                                mma_bf16(pacc + (uint32_t)(l * N), ad, bd, idesc, (started & bit) ? 1u : 0u);
+                                started |= bit;
                             }
                         }
                     }
@@ -273,52 +285,59 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
             const int tm = tile % g.tiles_m;
             const int row = tm * kBM + q * 32 + lane;
             long long* orow = g.out + (long long)row * g.ldo;
-            const uint32_t acc = tmem + lane_base + (uint32_t)(b * 4 * N);
+            const uint32_t acc = tmem + lane_base + (uint32_t)(b * g.kparts * 4 * N);
+            float2* st = stage_out + (warp - 2) * 32 * 17;  // this warp's 32 x 16 (+1) staging tile
+            long long* stI = reinterpret_cast<long long*>(st);
             for (int c0 = cbeg; c0 < cend; c0 += 16) {
-                float v0[16], v1[16], v2[16], v3[16];
-                tmem_ld16(acc + (uint32_t)c0, v0);
-                tmem_ld16(acc + (uint32_t)(N + c0), v1);
-                tmem_ld16(acc + (uint32_t)(2 * N + c0), v2);
-                tmem_ld16(acc + (uint32_t)(3 * N + c0), v3);
-                tmem_wait_ld();
-                if (!g.outf && row < g.M) {
-                    // level sums are exact integers below 2^24: 32-bit conversions, 64-bit integer sum
-                    // (64-bit int <-> float conversions run at the FP64 rate on this part)
-                    long long V[16];
+                const int cw = min(16, cend - c0);  // columns of this chunk owned by the warp
+                // the K parts are summed in the staging tile: exactly as int64, or as double-floats
+                const int er = (g.outf && row < g.M) ? g.erow[row] - 40 : 0;
+                for (int part = 0; part < g.kparts; ++part) {
+                    float v0[16], v1[16], v2[16], v3[16];
+                    const uint32_t pacc = acc + (uint32_t)(part * 4 * N);
+                    tmem_ld16(pacc + (uint32_t)c0, v0);
+                    tmem_ld16(pacc + (uint32_t)(N + c0), v1);
+                    tmem_ld16(pacc + (uint32_t)(2 * N + c0), v2);
+                    tmem_ld16(pacc + (uint32_t)(3 * N + c0), v3);
+                    tmem_wait_ld();
+                    if (!g.outf) {
+                        // level sums are exact integers below 2^24: 32-bit conversions and a 64-bit
+                        // integer sum (64-bit int <-> float conversions run at the FP64 rate here)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        V[j] = ((long long)__float2int_rn(v0[j]) << 24) + ((long long)__float2int_rn(v1[j]) << 16) +
-                               ((long long)__float2int_rn(v2[j]) << 8) + (long long)__float2int_rn(v3[j]);
-                    const int lim = min(cend, g.Nvalid);  // columns owned by this warp
-                    if (g.atomic) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (c0 + j < lim) atomicAdd((unsigned long long*)(orow + c0 + j), (unsigned long long)V[j]);
-                    } else if (c0 + 16 <= lim && (g.ldo & 1) == 0) {
-#pragma unroll
-                        for (int j = 0; j < 16; j += 2)
-                            *reinterpret_cast<longlong2*>(orow + c0 + j) = make_longlong2(V[j], V[j + 1]);
+                        for (int j = 0; j < 16; ++j) {
+                            const long long Vp = ((long long)__float2int_rn(v0[j]) << 24) +
+                                                 ((long long)__float2int_rn(v1[j]) << 16) +
+                                                 ((long long)__float2int_rn(v2[j]) << 8) + (long long)__float2int_rn(v3[j]);
+                            stI[lane * 17 + j] = part ? stI[lane * 17 + j] + Vp : Vp;
+                        }
                     } else {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (c0 + j < lim) orow[c0 + j] = V[j];
+                        for (int j = 0; j < 16; ++j) {
+                            const float2 x = levels_to_df(v0[j], v1[j], v2[j], v3[j], er + g.ecol[min(c0 + j, N - 1)]);
+                            st[lane * 17 + j] = part ? df2_add(st[lane * 17 + j], x) : x;
+                        }
                     }
                 }
-                if (g.outf) {
-                    // exact V -> scaled double-float (24-bit pieces, 32-bit conversions), staged in
-                    // shared memory, then written as whole 128-byte row segments (8 lanes per row)
-                    float2* st = stage_out + (warp - 2) * 32 * 17;
-                    const int cw = min(16, cend - c0);  // columns of this chunk owned by the warp
-                    const int er = row < g.M ? g.erow[row] - 40 : 0;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (j < cw) st[lane * 17 + j] = levels_to_df(v0[j], v1[j], v2[j], v3[j], er + g.ecol[c0 + j]);
+                if (!g.outf) {
+                    if (row < g.M) {
+                        const int lim = min(cend, g.Nvalid);  // columns owned by this warp
+                        const long long* V = stI + lane * 17;
+                        if (g.atomic) {
+                            for (int j = 0; j < 16; ++j)
+                                if (c0 + j < lim) atomicAdd((unsigned long long*)(orow + c0 + j), (unsigned long long)V[j]);
+                        } else {
+                            for (int j = 0; j < 16; ++j)
+                                if (c0 + j < lim) orow[c0 + j] = V[j];
+                        }
+                    }
+                } else {
+                    // write as whole 128-byte row segments (4 lanes per row, 8 rows per pass)
                     __syncwarp();
                     const int rbase = tm * kBM + q * 32;
 #pragma unroll
                     for (int it2 = 0; it2 < 4; ++it2) {
-                        const int rr = it2 * 8 + (lane >> 2);  // 8 rows per pass, 4 lanes per row
-                        const int cc = (lane & 3) * 4;         // 4 double-floats (32 bytes) per lane
+                        const int rr = it2 * 8 + (lane >> 2);
+                        const int cc = (lane & 3) * 4;
                         const int grow = rbase + rr;
                         if (cc >= cw) continue;
                         if (grow < g.M && c0 + cc + 3 < g.Nvalid && cc + 3 < cw) {
@@ -332,8 +351,8 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                                     g.outf[(long long)grow * g.ldo + c0 + cc + u] = st[rr * 17 + cc + u];
                         }
                     }
-                    __syncwarp();
                 }
+                __syncwarp();
             }
             // every TMEM read of this set is complete: hand it back to the MMA warp
             tc_fence_before();
@@ -367,8 +386,9 @@ size_t digit_gemm_smem(int N) {
 
 int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int N, int katoms_total,
                     int katoms, int M, int Nvalid, long long* out, long long ldo, bool atomic, int* status) {
-    if (N % 16 || N < 16 || N > 128 || katoms < 1 || katoms > 10 || katoms_total % katoms || M <= 0 ||
-        Nvalid > N) {
+    const int kparts = (katoms + 9) / 10;
+    if (N % 16 || N < 16 || N > 128 || katoms < 1 || katoms_total % katoms || M <= 0 || Nvalid > N ||
+        kparts * 4 * N > 512) {
         nof_set_error("digit_gemm: unsupported shape");
         return NOF_EINVAL;
     }
@@ -381,11 +401,13 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
     g.M = M; g.N = N; g.Nvalid = Nvalid; g.katoms = katoms; g.katoms_total = katoms_total;
     g.out = out; g.ldo = ldo; g.atomic = atomic ? 1 : 0; g.status = status;
     g.stages = stages_for(N);
-    g.nbuf = (8 * N <= 512) ? 2 : 1;
+    g.kparts = kparts;
+    g.apart = (katoms + kparts - 1) / kparts;
+    g.nbuf = (2 * kparts * 4 * N <= 512) ? 2 : 1;
     g.tiles_m = (M + kBM - 1) / kBM;
     g.kchunks = katoms_total / katoms;
     int cols = 32;
-    while (cols < g.nbuf * 4 * N) cols *= 2;
+    while (cols < g.nbuf * kparts * 4 * N) cols *= 2;
     g.tmem_cols = cols;
     p->smem = digit_gemm_smem(N);
     static int sms = 0;

@@ -8,7 +8,9 @@ struct DigitGemmArgs {
     int M;          // valid rows of A (rows of the output)
     int N;          // padded N (multiple of 16, <= 128); B has N rows
     int Nvalid;     // columns written
-    int katoms;     // K atoms (16 each) accumulated per tile (<= 10: exact for K <= 160)
+    int katoms;     // K atoms (16 each) accumulated per tile
+    int kparts;     // exact accumulations per tile: atoms [p * apart, (p + 1) * apart) go to TMEM level
+    int apart;      // set p (apart <= 10 keeps every FP32 partial sum exact); parts are summed in the epilogue
     int katoms_total;  // K atoms of the whole operand (storage stride)
     int tmem_cols;  // TMEM columns allocated (power of two >= 4 N)
     long long* out; // int64 fixed-point output, row-major with leading dimension ldo

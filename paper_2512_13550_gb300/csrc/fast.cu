@@ -396,8 +396,8 @@ int fast_release(nof_ctx* c) {
 
 int fast_prepare(nof_ctx* c) {
     const int n = c->nbf, X = c->naux, a = c->nact;
-    if (n > 160 || a > 64) {
-        nof_set_error("NOF_PREC_SPLIT_BF16 supports nbf <= 160 and nact <= 64 in this build");
+    if (n > 320 || a > 64) {
+        nof_set_error("NOF_PREC_SPLIT_BF16 supports nbf <= 320 and nact <= 64 in this build");
         return NOF_EINVAL;
     }
     FastState* f = new (std::nothrow) FastState();

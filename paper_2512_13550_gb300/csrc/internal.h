@@ -102,9 +102,10 @@ int gemm64_splitk(const Gemm64& g, int splits, double* work, cudaStream_t st);
 
 int cholesky_inverse(double* V, double* Linv, int X, int* status, cudaStream_t st);
 int newton_schulz_invsqrt(const double* S, double* Xout, double* w1, double* w2, double* w3,
-                          double* w4, int n, int iters, cudaStream_t st);
+                          double* w4, int n, int iters, cudaStream_t st, double* work = nullptr,
+                          size_t work_cap = 0);
 int expm_antisym_device(const double* y, double* U, double* w1, double* w2, int n,
-                        cudaStream_t st);
+                        cudaStream_t st, double* work = nullptr, size_t work_cap = 0);
 
 // Integrals (integrals.cu)
 int build_integrals(nof_ctx* c, double* M3 /* [X][n][n] */, double* V2 /* [X][X] */);

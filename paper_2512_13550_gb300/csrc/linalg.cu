@@ -224,12 +224,15 @@ __global__ void k_scale(const double* A, double s, double* out, long long n) {
 
 inline unsigned blocks_for(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-Gemm64 square_gemm(const double* A, const double* B, double* C, int n) {
+Gemm64 square_gemm(const double* A, const double* B, double* C, int n, double* work = nullptr,
+                   size_t work_cap = 0) {
     Gemm64 g;
     g.M = n; g.N = n; g.K = n;
     g.A = A; g.sAm = n; g.sAk0 = 1;
     g.B = B; g.sBn = 1; g.sBk0 = n;
     g.C = C; g.sCm = n; g.sCn = 1;
+    g.work = work;
+    g.work_cap = work_cap;
     return g;
 }
 
@@ -306,7 +309,7 @@ int cholesky_inverse(double* V, double* Linv, int X, int* status, cudaStream_t s
 // Coupled Newton-Schulz iteration for S^{-1/2} (Higham, Functions of Matrices, 2008, Sec. 6.3):
 // Y0 = S/c, Z0 = I, T = (3I - Z Y)/2, Y <- Y T, Z <- T Z; Z -> (S/c)^{-1/2}, c = ||S||_F.
 int newton_schulz_invsqrt(const double* S, double* Xout, double* Y, double* Z, double* T,
-                          double* P, int n, int iters, cudaStream_t st) {
+                          double* P, int n, int iters, cudaStream_t st, double* work, size_t work_cap) {
     long long nn = (long long)n * n;
     k_frob<<<1, 256, 0, st>>>(S, nn, T);
     NOF_LAUNCH_CHECK();
@@ -322,12 +325,12 @@ int newton_schulz_invsqrt(const double* S, double* Xout, double* Y, double* Z, d
     k_axpy_identity<<<blocks_for(nn), 256, 0, st>>>(S, 0.0, Z, n);  // Z = I
     NOF_LAUNCH_CHECK();
     for (int it = 0; it < iters; ++it) {
-        NOF_TRY(gemm64(square_gemm(Z, Y, P, n), st));   // P = Z Y
+        NOF_TRY(gemm64(square_gemm(Z, Y, P, n, work, work_cap), st));   // P = Z Y
         k_ns_mid<<<blocks_for(nn), 256, 0, st>>>(P, T, n);  // T = 1.5 I - 0.5 P
         NOF_LAUNCH_CHECK();
-        NOF_TRY(gemm64(square_gemm(Y, T, P, n), st));   // P = Y T
+        NOF_TRY(gemm64(square_gemm(Y, T, P, n, work, work_cap), st));   // P = Y T
         double* tmp = Y; Y = P; P = tmp;
-        NOF_TRY(gemm64(square_gemm(T, Z, P, n), st));   // P = T Z
+        NOF_TRY(gemm64(square_gemm(T, Z, P, n, work, work_cap), st));   // P = T Z
         tmp = Z; Z = P; P = tmp;
     }
     k_scale<<<blocks_for(nn), 256, 0, st>>>(Z, 1.0 / std::sqrt(h_nrm), Xout, nn);
@@ -338,7 +341,7 @@ int newton_schulz_invsqrt(const double* S, double* Xout, double* Y, double* Z, d
 // U = exp(y) for antisymmetric y: s = smallest integer with ||y||_F / 2^s <= 1/2,
 // Horner form of the degree-12 Taylor polynomial of z = y / 2^s, then s squarings.
 int expm_antisym_device(const double* y, double* U, double* w1, double* w2, int n,
-                        cudaStream_t st) {
+                        cudaStream_t st, double* work, size_t work_cap) {
     long long nn = (long long)n * n;
     k_frob<<<1, 256, 0, st>>>(y, nn, w1);
     NOF_LAUNCH_CHECK();
@@ -354,12 +357,12 @@ int expm_antisym_device(const double* y, double* U, double* w1, double* w2, int 
     k_axpy_identity<<<blocks_for(nn), 256, 0, st>>>(z, 0.0, U, n);
     NOF_LAUNCH_CHECK();
     for (int k = 12; k >= 1; --k) {
-        NOF_TRY(gemm64(square_gemm(z, U, w2, n), st));           // w2 = z U
+        NOF_TRY(gemm64(square_gemm(z, U, w2, n, work, work_cap), st));  // w2 = z U
         k_axpy_identity<<<blocks_for(nn), 256, 0, st>>>(w2, 1.0 / k, U, n);
         NOF_LAUNCH_CHECK();
     }
     for (int i = 0; i < s; ++i) {
-        NOF_TRY(gemm64(square_gemm(U, U, w2, n), st));
+        NOF_TRY(gemm64(square_gemm(U, U, w2, n, work, work_cap), st));
         NOF_CUDA(cudaMemcpyAsync(U, w2, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
     return NOF_OK;

@@ -454,7 +454,7 @@ int pnof_adam_rotate(nof_ctx* c, double* C, double* m, double* v, int* t, double
     NOF_LAUNCH_CHECK();
     k_step_stats<<<1, 256, 0, st>>>(c->E, c->gorb, c->lam, n, out);
     NOF_LAUNCH_CHECK();
-    NOF_TRY(expm_antisym_device(c->y, c->U, c->U2, c->tmpn, n, st));
+    NOF_TRY(expm_antisym_device(c->y, c->U, c->U2, c->tmpn, n, st, c->gwork, c->gwork_cap));
     Gemm64 g;  // tmp = C U
     g.M = n; g.N = n; g.K = n;
     g.A = C; g.sAm = n; g.sAk0 = 1;

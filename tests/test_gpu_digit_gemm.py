@@ -11,6 +11,9 @@ pytestmark = pytest.mark.gpu
     (257, 48, 9, 1),     # ragged M, N not a power of two
     (200, 128, 8, 1),    # widest N (512 TMEM columns)
     (256, 64, 20, 4),    # split-K with integer atomics, 5 atoms per chunk
+    (300, 64, 12, 1),    # K = 192 > 160: two exact accumulations of 6 atoms summed in the epilogue
+    (150, 32, 20, 1),    # K = 320: two parts of 10 atoms
+    (256, 64, 24, 2),    # two K parts per tile and split-K atomics together
 ])
 def test_digit_gemm_exact(M, N, katoms, splits):
     import paper_2512_13550_gb300 as nof

@@ -36,6 +36,7 @@ CASES = {
     "H22": lambda: systems.chain3s(22),            # n = 66, a = 22 (a padded to 32)
     "H8_ncwo2": lambda: systems.chain3s(8, ncwo=2),  # two weak orbitals per pair
     "H50": lambda: systems.h50(),                  # the benchmark workload (n = 150, a = 50)
+    "H64": lambda: systems.chain3s(64, seed=5),    # n = 192 > 160: two exact K accumulations
 }
 
 
@@ -99,6 +100,6 @@ def test_split_rejects_unsupported_sizes():
     import paper_2512_13550_gb300 as nof
     orb, aux = inputs.basis_3s_10aux()
     ctx = nof.Context(precision=nof.PREC_SPLIT_BF16)
-    with pytest.raises(nof.NofError) as e:   # nbf = 180 > 160
-        ctx.build_B(inputs.chain(60), orb, aux)
+    with pytest.raises(nof.NofError) as e:   # nact = 66 > 64
+        ctx.build_B(inputs.chain(66), orb, aux)
     assert e.value.code == nof.NOF_EINVAL
