@@ -128,6 +128,17 @@ int nof_energy_grad(nof_ctx* ctx, const double* C, const double* gamma, double* 
  * out (device, 3 doubles): E at (C_old, gamma_new), ||g||_F, max |lambda - lambda^T|. */
 int nof_step(nof_ctx* ctx, double* C, double* gamma, double* m, double* v, int* t, double* out);
 
+/* Batched evaluation (the batching of many geometries): `count` independent contexts, each built
+ * with its own geometry and created on its own stream, evaluate nof_energy_grad concurrently.
+ * The call forks from `stream` (a cudaStream_t) onto every context's stream with events and joins
+ * back, so capturing `stream` in a CUDA graph captures the whole batch as one graph launch. The
+ * pointer arrays are host arrays of `count` device pointers (C, gamma, E required; g_orb and
+ * g_gamma may be NULL or hold NULL entries). Results equal those of the same instances evaluated
+ * one by one. */
+int nof_energy_grad_batch(nof_ctx* const* ctxs, int count, const double* const* C,
+                          const double* const* gamma, double* const* E, double* const* g_orb,
+                          double* const* g_gamma, void* stream);
+
 /* Wait for the context's stream and report any device-side status word. */
 int nof_sync(nof_ctx* ctx);
 

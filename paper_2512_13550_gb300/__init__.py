@@ -65,6 +65,7 @@ SIGNATURES = {
     "nof_energy_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "nof_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "nof_sync": (ctypes.c_int, [_P]),
+    "nof_energy_grad_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]),
     "nof_kernel_launches": (ctypes.c_longlong, []),
     "nof_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "nof_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -101,6 +102,19 @@ def selftest_digit_gemm(M: int, N: int, katoms: int, splits: int = 1, seed: int 
     out = ctypes.c_longlong(-1)
     _check(load_library().nof_selftest_digit_gemm(M, N, katoms, splits, seed, ctypes.byref(out)))
     return out.value
+
+
+def energy_grad_batch(contexts, Cs, gammas, Es, gs=None, ggs=None, stream=None):
+    """Evaluate several contexts concurrently (each on its own stream), forked from `stream`."""
+    import torch
+    n = len(contexts)
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    arr = lambda ts: (ctypes.c_void_p * n)(*[None if t is None else _dptr(t).value for t in ts])
+    hs = (ctypes.c_void_p * n)(*[c._h.value for c in contexts])
+    _check(load_library().nof_energy_grad_batch(hs, n, arr(Cs), arr(gammas), arr(Es),
+                                                None if gs is None else arr(gs),
+                                                None if ggs is None else arr(ggs),
+                                                ctypes.c_void_p(stream.cuda_stream)))
 
 
 def _check(rc: int):

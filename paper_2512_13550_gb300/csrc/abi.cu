@@ -197,10 +197,13 @@ int nof_create(nof_ctx** out, const nof_options* opt, void* stream) {
         return r;
     }
     cudaError_t e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
         cudaFree(c->status);
         delete c;
-        return nof_cuda_fail(e, "cudaMemsetAsync(status)", __FILE__, __LINE__);
+        return nof_cuda_fail(e, "context set-up", __FILE__, __LINE__);
     }
     *out = c;
     return NOF_OK;
@@ -212,6 +215,8 @@ int nof_destroy(nof_ctx* c) {
     prof_clear(c);
     delete static_cast<EventPairs*>(c->prof_events);
     free_system(c);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     dfree(c->status);
     delete c;
     return NOF_OK;
@@ -480,6 +485,32 @@ int nof_step(nof_ctx* c, double* C, double* gamma, double* m, double* v, int* t,
     NOF_TRY(pnof_on_update(c, gamma));
     NOF_TRY(run_grad(c, C, gamma, true));
     return pnof_adam_rotate(c, C, m, v, t, out);
+}
+
+int nof_energy_grad_batch(nof_ctx* const* ctxs, int count, const double* const* C, const double* const* gamma,
+                          double* const* E, double* const* g_orb, double* const* g_gamma, void* stream) {
+    if (count <= 0 || !ctxs || !C || !gamma || !E) {
+        nof_set_error("nof_energy_grad_batch: bad count or null array");
+        return NOF_EINVAL;
+    }
+    for (int i = 0; i < count; ++i) {
+        NOF_TRY(check_ctx(ctxs[i], true));
+        if (!C[i] || !gamma[i] || !E[i]) {
+            nof_set_error("nof_energy_grad_batch: null C, gamma or E entry");
+            return NOF_EINVAL;
+        }
+    }
+    cudaStream_t master = (cudaStream_t)stream;
+    NOF_CUDA(cudaEventRecord(ctxs[0]->ev_fork, master));
+    for (int i = 0; i < count; ++i) {
+        nof_ctx* c = ctxs[i];
+        NOF_CUDA(cudaStreamWaitEvent(c->stream, ctxs[0]->ev_fork, 0));
+        NOF_TRY(nof_energy_grad(c, C[i], gamma[i], E[i], g_orb ? g_orb[i] : nullptr,
+                                g_gamma ? g_gamma[i] : nullptr));
+        NOF_CUDA(cudaEventRecord(c->ev_join, c->stream));
+        NOF_CUDA(cudaStreamWaitEvent(master, c->ev_join, 0));
+    }
+    return NOF_OK;
 }
 
 long long nof_kernel_launches(void) { return g_launches.load(); }

@@ -64,6 +64,8 @@ struct nof_ctx {
     size_t gwork_cap;
     int* status;
     FastState* fast;
+    // fork/join events of the batched evaluation
+    cudaEvent_t ev_fork, ev_join;
     // dominant-kernel timing (nof_profile)
     int prof_on;
     const char* prof_name;
