@@ -338,7 +338,7 @@ int nof_build_B(nof_ctx* c, int natom, const double* xyz, const double* Z, int c
     if (r == NOF_OK) {  // Bp = L^{-1} M3 over the packed pair index
         Gemm64 g;
         g.M = X; g.N = (int)npk; g.K = X;
-        g.A = Linv; g.sAm = X; g.sAk0 = 1;
+        g.A = Linv; g.sAm = X; g.sAk0 = 1; g.a_lower = true;
         g.B = M3; g.sBn = 1; g.sBk0 = (long long)npk;
         g.C = Bp; g.sCm = (long long)npk; g.sCn = 1;
         r = gemm64(g, st);

@@ -92,6 +92,7 @@ struct Gemm64 {
     double* C = nullptr;
     long long sCm = 0, sCn = 1, bC = 0;
     double alpha = 1.0, beta = 0.0;
+    bool a_lower = false;  // A(m, k) = 0 for k > m: each output row block stops its K loop there
     // Optional scratch for an automatic split-K when the output has too few 64x64 tiles to fill
     // the GPU (FP64 runs at 2 FMA/clk/SM on GB300, so a single CTA per tile is far too slow).
     double* work = nullptr;

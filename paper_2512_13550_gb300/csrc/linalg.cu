@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(256) k_gemm64(Gemm64 g, int splits, double* wo
     int kchunk = (g.K + splits - 1) / splits;
     kchunk = (kchunk + BK - 1) / BK * BK;
     const int k_lo = split * kchunk;
-    const int k_hi = min(g.K, k_lo + kchunk);
+    int k_hi = min(g.K, k_lo + kchunk);
+    if (g.a_lower) k_hi = min(k_hi, m0 + BM);  // lower-triangular A: nothing past the diagonal block
     const bool a_kfast = (g.sAk0 == 1);
     const bool b_nfast = (g.sBn == 1);
     double acc[4][4] = {};
