@@ -108,6 +108,12 @@ int nof_get_B(nof_ctx* ctx, double* B);
  * device). Q: nbf x nbf orthogonal. Gives S-orthonormal orbitals for any orthogonal Q. */
 int nof_lowdin(nof_ctx* ctx, const double* Q, double* C);
 
+/* Core-Hamiltonian starting orbitals: C0 = X U with X = S^{-1/2} (Newton-Schulz) and U the
+ * eigenvectors of X^T H X in ascending order of the eigenvalues (cyclic Jacobi on the device).
+ * eps (device, nbf; may be NULL) receives the eigenvalues. Columns of C0 are S-orthonormal.
+ * Degenerate eigenvalues leave the basis of their subspace arbitrary. */
+int nof_core_guess(nof_ctx* ctx, double* C0, double* eps);
+
 /* J_pq = sum_P b^P_pp b^P_qq and K_pq = sum_P (b^P_pq)^2 over the active orbitals, with
  * b^P = C_a^T B^P C_a (the orbital transformation of the RI tensor; Eq. PNOF uses J and K,
  * and L = K for real orbitals). J, K: nact x nact. */

@@ -61,6 +61,7 @@ SIGNATURES = {
     "nof_get_SH": (ctypes.c_int, [_P, _P, _P]),
     "nof_get_B": (ctypes.c_int, [_P, _P]),
     "nof_lowdin": (ctypes.c_int, [_P, _P, _P]),
+    "nof_core_guess": (ctypes.c_int, [_P, _P, _P]),
     "nof_jk": (ctypes.c_int, [_P, _P, _P, _P]),
     "nof_energy_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "nof_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
@@ -211,6 +212,13 @@ class Context:
         C = self._empty(n, n)
         _check(load_library().nof_lowdin(self._h, _dptr(Q), _dptr(C)))
         return C
+
+    def core_guess(self):
+        """Core-Hamiltonian orbitals C0 and their energies (ascending)."""
+        n = self.sizes["nbf"]
+        C, eps = self._empty(n, n), self._empty(n)
+        _check(load_library().nof_core_guess(self._h, _dptr(C), _dptr(eps)))
+        return C, eps
 
     def jk(self, C, J=None, K=None):
         a = self.sizes["nact"]

@@ -442,6 +442,35 @@ int nof_lowdin(nof_ctx* c, const double* Q, double* C) {
     return gemm64(g, c->stream);
 }
 
+int nof_core_guess(nof_ctx* c, double* C0, double* eps) {
+    NOF_TRY(check_ctx(c, true));
+    if (!C0) {
+        nof_set_error("nof_core_guess: null output");
+        return NOF_EINVAL;
+    }
+    const int n = c->nbf;
+    cudaStream_t st = c->stream;
+    // X = S^{-1/2} into lam; A = X^T H X into U (via tmpn = H X); eigenvectors into y; C0 = X y
+    NOF_TRY(newton_schulz_invsqrt(c->S, c->lam, c->y, c->U, c->U2, c->tmpn, n, 40, st, c->gwork, c->gwork_cap));
+    Gemm64 g;
+    g.M = n; g.N = n; g.K = n;
+    g.A = c->H; g.sAm = n; g.sAk0 = 1;
+    g.B = c->lam; g.sBn = 1; g.sBk0 = n;
+    g.C = c->tmpn; g.sCm = n; g.sCn = 1;
+    g.work = c->gwork; g.work_cap = c->gwork_cap;
+    NOF_TRY(gemm64(g, st));
+    g.A = c->lam; g.sAm = 1; g.sAk0 = n;  // X^T (X is symmetric; written generally)
+    g.B = c->tmpn; g.sBn = 1; g.sBk0 = n;
+    g.C = c->U;
+    NOF_TRY(gemm64(g, st));
+    double* w = eps ? eps : c->gorb;  // eigenvalues (scratch when the caller does not want them)
+    NOF_TRY(sym_eig(c->U, c->U2, c->y, w, n, (int*)c->part, st));
+    g.A = c->lam; g.sAm = n; g.sAk0 = 1;
+    g.B = c->y; g.sBn = 1; g.sBk0 = n;
+    g.C = C0;
+    return gemm64(g, st);
+}
+
 int nof_jk(nof_ctx* c, const double* C, double* J, double* K) {
     NOF_TRY(check_ctx(c, true));
     if (!C || !J || !K) {

@@ -110,6 +110,8 @@ int newton_schulz_invsqrt(const double* S, double* Xout, double* w1, double* w2,
 int expm_antisym_device(const double* y, double* U, double* w1, double* w2, int n,
                         cudaStream_t st, double* work = nullptr, size_t work_cap = 0);
 
+int sym_eig(double* A, double* Vwork, double* Vout, double* w, int n, int* sweeps_dev, cudaStream_t st);
+
 // Integrals (integrals.cu)
 int build_integrals(nof_ctx* c, double* M3 /* [X][n][n] */, double* V2 /* [X][X] */);
 

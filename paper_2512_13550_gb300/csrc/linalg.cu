@@ -237,7 +237,140 @@ Gemm64 square_gemm(const double* A, const double* B, double* C, int n, double* w
     return g;
 }
 
+// ---- symmetric eigendecomposition: cyclic Jacobi, round-robin pair order ---------------------
+// One CTA. A (n x n, symmetric, destroyed) and V (n x n, starts as I) live in global memory. In
+// each round the n/2 disjoint pairs (p, q) of a round-robin tournament (position 0 fixed, the
+// others rotating) each get a Givens rotation zeroing A_pq (Golub & Van Loan, Matrix
+// Computations, Sec. 8.5: t = sign(th)/(|th| + sqrt(th^2 + 1)), th = (A_qq - A_pp)/(2 A_pq));
+// the rotations are applied to rows, then columns, of A and to the columns of V. Sweeps stop
+// when the off-diagonal Frobenius norm falls below tol times the total norm, or after max_sweeps.
+__global__ void __launch_bounds__(1024) k_jacobi(double* A, double* V, int n, int max_sweeps, double tol,
+                                                 int* sweeps_out) {
+    extern __shared__ double sh[];
+    const int m = n + (n & 1);      // players (a dummy index n when n is odd)
+    double* cs = sh;                // [m/2] cos
+    double* sn = sh + m / 2;        // [m/2] sin
+    int* pp = (int*)(sn + m / 2);   // [m/2]
+    int* qq = pp + m / 2;           // [m/2]
+    __shared__ double red[1024];
+    __shared__ int done;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (long long i = tid; i < (long long)n * n; i += nt) V[i] = ((i / n) == (i % n)) ? 1.0 : 0.0;
+    if (tid == 0) done = 0;
+    __syncthreads();
+    int sweep = 0;
+    for (; sweep < max_sweeps && !done; ++sweep) {
+        for (int r = 0; r < m - 1; ++r) {
+            // pairs of round r: position 0 holds player 0, positions 1..m-1 hold players rotated by r
+            for (int i = tid; i < m / 2; i += nt) {
+                int a = (i == 0) ? 0 : 1 + (i - 1 + r) % (m - 1);
+                int b = 1 + (m - 2 - i + r) % (m - 1);
+                int p = min(a, b), q = max(a, b);
+                double c = 1.0, s = 0.0;
+                if (q < n) {
+                    double apq = A[(long long)p * n + q];
+                    if (fabs(apq) > 1e-300) {
+                        double th = (A[(long long)q * n + q] - A[(long long)p * n + p]) / (2.0 * apq);
+                        double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        s = t * c;
+                    }
+                }
+                cs[i] = c; sn[i] = s; pp[i] = p; qq[i] = q;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (long long e = tid; e < (long long)(m / 2) * n; e += nt) {
+                int i = (int)(e / n), k = (int)(e % n);
+                int p = pp[i], q = qq[i];
+                if (q >= n) continue;
+                double c = cs[i], s = sn[i];
+                double ap = A[(long long)p * n + k], aq = A[(long long)q * n + k];
+                A[(long long)p * n + k] = c * ap - s * aq;
+                A[(long long)q * n + k] = s * ap + c * aq;
+            }
+            __syncthreads();
+            // columns: A <- A J, V <- V J
+            for (long long e = tid; e < (long long)(m / 2) * n; e += nt) {
+                int i = (int)(e / n), k = (int)(e % n);
+                int p = pp[i], q = qq[i];
+                if (q >= n) continue;
+                double c = cs[i], s = sn[i];
+                double ap = A[(long long)k * n + p], aq = A[(long long)k * n + q];
+                A[(long long)k * n + p] = c * ap - s * aq;
+                A[(long long)k * n + q] = s * ap + c * aq;
+                double vp = V[(long long)k * n + p], vq = V[(long long)k * n + q];
+                V[(long long)k * n + p] = c * vp - s * vq;
+                V[(long long)k * n + q] = s * vp + c * vq;
+            }
+            __syncthreads();
+        }
+        // convergence: off-diagonal vs total Frobenius norm
+        double off = 0.0, tot = 0.0;
+        for (long long i = tid; i < (long long)n * n; i += nt) {
+            double v = A[i] * A[i];
+            tot += v;
+            if ((i / n) != (i % n)) off += v;
+        }
+        red[tid] = off;
+        __syncthreads();
+        for (int o = nt / 2; o; o >>= 1) {
+            if (tid < o) red[tid] += red[tid + o];
+            __syncthreads();
+        }
+        double offs = red[0];
+        __syncthreads();
+        red[tid] = tot;
+        __syncthreads();
+        for (int o = nt / 2; o; o >>= 1) {
+            if (tid < o) red[tid] += red[tid + o];
+            __syncthreads();
+        }
+        if (tid == 0 && offs <= tol * tol * red[0]) done = 1;
+        __syncthreads();
+    }
+    if (tid == 0) *sweeps_out = sweep;
+}
+
+// Ascending order of the eigenvalues diag(A) (ties keep index order) and the matching columns:
+// out[mu][j] = V[mu][perm[j]], w[j] = A[perm[j]][perm[j]].
+__global__ void k_eig_sort(const double* A, const double* V, int n, double* out, double* w) {
+    extern __shared__ int perm[];
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < n; ++i) perm[i] = i;
+        for (int i = 1; i < n; ++i) {  // insertion sort (stable)
+            int x = perm[i];
+            double ax = A[(long long)x * n + x];
+            int j = i - 1;
+            while (j >= 0 && A[(long long)perm[j] * n + perm[j]] > ax) {
+                perm[j + 1] = perm[j];
+                --j;
+            }
+            perm[j + 1] = x;
+        }
+    }
+    __syncthreads();
+    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+        int mu = (int)(e / n), j = (int)(e % n);
+        out[e] = V[(long long)mu * n + perm[j]];
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) w[j] = A[(long long)perm[j] * n + perm[j]];
+}
+
 }  // namespace
+
+// Eigendecomposition of the symmetric A (destroyed): vectors (ascending eigenvalues) into Vout
+// (columns), eigenvalues into w. Work: Vwork (n x n).
+int sym_eig(double* A, double* Vwork, double* Vout, double* w, int n, int* sweeps_dev, cudaStream_t st) {
+    const int m = n + (n & 1);
+    size_t shm = (size_t)(m / 2) * (2 * sizeof(double) + 2 * sizeof(int));
+    if (shm > 48 * 1024) NOF_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    k_jacobi<<<1, 1024, shm, st>>>(A, Vwork, n, 30, 1e-14, sweeps_dev);
+    NOF_LAUNCH_CHECK();
+    k_eig_sort<<<1, 1024, (size_t)n * sizeof(int), st>>>(A, Vwork, n, Vout, w);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
 
 int gemm64(const Gemm64& g, cudaStream_t st) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return NOF_OK;
