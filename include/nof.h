@@ -145,6 +145,23 @@ int nof_energy_grad_batch(nof_ctx* const* ctxs, int count, const double* const* 
                           const double* const* gamma, double* const* E, double* const* g_orb,
                           double* const* g_gamma, void* stream);
 
+/* Learned starting guess (no counterpart in the paper, which only notes that its Python version
+ * suits machine-learning workflows): a perceptron x (F) -> relu (H) -> relu (H) -> y (O) in FP32
+ * with hand-written kernels. Parameters theta are packed W1 [H][F], b1 [H], W2 [H][H], b2 [H],
+ * W3 [O][H], b3 [O] (nof_mlp_param_count floats). X: [B][F], Y and T: [B][O], all device FP32,
+ * row-major. work: device scratch of nof_mlp_work_size(B, H, O) floats owned by the caller.
+ * nof_mlp_loss_grad writes loss = mean over the batch of sum_o (y - t)^2 (device scalar, may be
+ * NULL) and its gradient (packed like theta). nof_mlp_adam takes one bias-corrected Adam step
+ * with decoupled weight decay wd (t >= 1 is the step count) on P parameters in place. */
+long long nof_mlp_param_count(int F, int H, int O);
+long long nof_mlp_work_size(int B, int H, int O);
+int nof_mlp_forward(int B, int F, int H, int O, const float* theta, const float* X, float* Y, float* work,
+                    void* stream);
+int nof_mlp_loss_grad(int B, int F, int H, int O, const float* theta, const float* X, const float* T,
+                      float* loss, float* grad, float* work, void* stream);
+int nof_mlp_adam(long long P, float* theta, const float* grad, float* m, float* v, int t, float lr, float b1,
+                 float b2, float eps, float wd, void* stream);
+
 /* Wait for the context's stream and report any device-side status word. */
 int nof_sync(nof_ctx* ctx);
 

@@ -1,0 +1,193 @@
+"""Learned starting guess for the occupation angles (a machine-learning add-on; the paper has none).
+
+A perceptron (x -> relu 256 -> relu 256 -> y) maps per-pair features to y = sin^2 gamma_g (twice the
+weak occupation of subspace g; unlike gamma itself it is unique, since the trigonometric mapping is
+even and pi-periodic in gamma) of the occupation optimum at the core-Hamiltonian orbitals, so a new
+geometry can start from predicted occupations instead of a constant. Training pairs come from the
+method itself: nof_core_guess, then one nof_step with the orbital rate set to zero and a long
+occupation loop (the ON optimisation of the paper with J, K fixed). Every network operation runs
+in the library's FP32 kernels (nof_mlp_forward / nof_mlp_loss_grad / nof_mlp_adam); the features
+are host-side statistics of the geometry and of the core-guess orbital energies.
+
+Features of subspace g (strong orbital g, weak orbital N - 1 - g for N_g = 1): the core energies of
+both orbitals and their gap, the distance of the pair from the Fermi level (g' = N/2 - 1 - g) as
+g'/(N/2) and 1/(g' + 1), 8/N, and the mean and spread of the bond lengths (bohr).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _check, inputs, load_library
+
+NFEAT = 8
+
+
+def pair_features(xyz: np.ndarray, eps: np.ndarray, nelec: int) -> np.ndarray:
+    npair = nelec // 2
+    d = np.linalg.norm(np.diff(xyz, axis=0), axis=1) if xyz.shape[0] > 1 else np.zeros(1)
+    out = np.zeros((npair, NFEAT))
+    for g in range(npair):
+        p = 2 * npair - 1 - g
+        gp = npair - 1 - g
+        out[g] = [eps[g], eps[p], eps[p] - eps[g], gp / npair, 1.0 / (gp + 1), 8.0 / nelec,
+                  d.mean(), d.std()]
+    return out
+
+
+def _he_init(F, H, O, seed):
+    """He-style normal weights and zero biases from the shared seeded generator (host, once)."""
+    parts, k = [], 0
+    for shape in [(H, F), (H,), (H, H), (H,), (O, H), (O,)]:
+        m = int(np.prod(shape))
+        parts.append(inputs.normal(seed * 7919 + k, m) * np.sqrt(2.0 / shape[1]) if len(shape) == 2 else np.zeros(m))
+        k += 1
+    return np.concatenate(parts)
+
+
+class MLP:
+    """FP32 perceptron on the device, trained with Adam; parameters and moments are torch tensors."""
+
+    def __init__(self, F: int = NFEAT, H: int = 256, O: int = 1, seed: int = 0):
+        import torch
+        lib = load_library()
+        self.F, self.H, self.O = F, H, O
+        self.P = int(lib.nof_mlp_param_count(F, H, O))
+        self.theta = torch.tensor(_he_init(F, H, O, seed), dtype=torch.float32, device="cuda")
+        self.m = torch.zeros_like(self.theta)
+        self.v = torch.zeros_like(self.theta)
+        self.grad = torch.zeros_like(self.theta)
+        self.t = 0
+        self.mu = np.zeros(F)
+        self.sd = np.ones(F)
+
+
+def _fptr(t):
+    import torch
+    assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def mlp_loss_grad(net: MLP, X, T, work=None):
+    """Loss and gradient (into net.grad) for device FP32 batches X [B][F], T [B][O]."""
+    import torch
+    B = X.shape[0]
+    work = torch.empty(int(load_library().nof_mlp_work_size(B, net.H, net.O)), dtype=torch.float32,
+                       device="cuda") if work is None else work
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    _check(load_library().nof_mlp_loss_grad(B, net.F, net.H, net.O, _fptr(net.theta), _fptr(X), _fptr(T),
+                                            _fptr(loss), _fptr(net.grad), _fptr(work), _stream()))
+    return loss
+
+
+def mlp_forward(net: MLP, X):
+    import torch
+    B = X.shape[0]
+    work = torch.empty(int(load_library().nof_mlp_work_size(B, net.H, net.O)), dtype=torch.float32, device="cuda")
+    Y = torch.empty(B, net.O, dtype=torch.float32, device="cuda")
+    _check(load_library().nof_mlp_forward(B, net.F, net.H, net.O, _fptr(net.theta), _fptr(X), _fptr(Y),
+                                          _fptr(work), _stream()))
+    return Y
+
+
+def mlp_adam(net: MLP, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, wd=0.0):
+    net.t += 1
+    _check(load_library().nof_mlp_adam(net.P, _fptr(net.theta), _fptr(net.grad), _fptr(net.m), _fptr(net.v),
+                                       net.t, lr, b1, b2, eps, wd, _stream()))
+
+
+def train(net: MLP, feats: np.ndarray, targets: np.ndarray, iters: int = 800, lr: float = 1e-3, wd: float = 0.3):
+    """Full-batch Adam on standardised features; returns the loss history (host floats)."""
+    import torch
+    net.mu = feats.mean(0)
+    net.sd = feats.std(0) + 1e-8
+    X = torch.tensor((feats - net.mu) / net.sd, dtype=torch.float32, device="cuda")
+    T = torch.tensor(targets.reshape(-1, net.O), dtype=torch.float32, device="cuda")
+    work = torch.empty(int(load_library().nof_mlp_work_size(X.shape[0], net.H, net.O)), dtype=torch.float32,
+                       device="cuda")
+    hist = []
+    for it in range(iters):
+        loss = mlp_loss_grad(net, X, T, work)
+        mlp_adam(net, lr, wd=wd)
+        if it % 20 == 0 or it == iters - 1:
+            hist.append(float(loss.item()))
+    return hist
+
+
+def predict(net: MLP, feats: np.ndarray) -> np.ndarray:
+    """Network output y (= predicted sin^2 gamma) per pair."""
+    import torch
+    X = torch.tensor((feats - net.mu) / net.sd, dtype=torch.float32, device="cuda")
+    return mlp_forward(net, X).cpu().numpy().reshape(-1).astype(np.float64)
+
+
+def angles(y: np.ndarray) -> np.ndarray:
+    """Occupation angles in [0, pi/2] from predicted sin^2 gamma."""
+    return np.arcsin(np.sqrt(np.clip(y, 0.0, 1.0)))
+
+
+# ----------------------------------------------------------------------------------------------
+# Data from the method itself
+# ----------------------------------------------------------------------------------------------
+
+def optimise(ctx, gamma0: np.ndarray, steps: int, C0=None):
+    """Run `steps` alternating ON/NO steps from the core guess (or C0); returns the per-step energies,
+    the final gamma (host) and the core orbital energies."""
+    import torch
+    n = ctx.sizes["nbf"]
+    if C0 is None:
+        C, eps = ctx.core_guess()
+    else:
+        C, eps = C0.clone(), None
+    gam = torch.tensor(gamma0, dtype=torch.float64, device="cuda")
+    m = torch.zeros(n, n, dtype=torch.float64, device="cuda")
+    v = torch.zeros_like(m)
+    ctx.t = ctypes.c_int(0)
+    Es = []
+    for _ in range(steps):
+        out = ctx.step(C, gam, m, v)
+        Es.append(out)
+    Es = torch.stack(Es).cpu().numpy()
+    return Es, gam.cpu().numpy(), (eps.cpu().numpy() if eps is not None else None)
+
+
+def generate(sizes, orb, aux, seed=11, precision=1, on_iters=300, gamma0=0.3):
+    """(features, sin^2 gamma*) pairs for displaced H chains of the given lengths, gamma* being the
+    occupation optimum at the core-Hamiltonian orbitals."""
+    from . import Context
+    feats, targs = [], []
+    for i, N in enumerate(sizes):
+        xyz = inputs.displaced_chain(int(N), seed=seed * 100003 + i)
+        ctx = Context(precision=precision, lr=0.0, on_iters=on_iters)
+        ctx.build_B(xyz, orb, aux)
+        _, gam, eps = optimise(ctx, np.full(ctx.sizes["ngamma"], gamma0), 1)
+        feats.append(pair_features(xyz, eps, int(N)))
+        targs.append(np.sin(gam[: int(N) // 2]) ** 2)
+        ctx.close()
+    return np.concatenate(feats), np.concatenate(targs)
+
+
+def evaluate(net: MLP, sizes, orb, aux, steps=60, seed=13, precision=1, gamma0=0.3):
+    """Energies along the optimisation from the core guess with learned vs constant starting
+    angles, for held-out geometries: list of (N, E_learned[steps], E_constant[steps])."""
+    from . import Context
+    out = []
+    for i, N in enumerate(sizes):
+        xyz = inputs.displaced_chain(int(N), seed=seed * 100003 + i)
+        ctx = Context(precision=precision)
+        ctx.build_B(xyz, orb, aux)
+        C0, eps = ctx.core_guess()
+        ng = ctx.sizes["ngamma"]
+        g_learn = np.full(ng, gamma0)
+        g_learn[: int(N) // 2] = angles(predict(net, pair_features(xyz, eps.cpu().numpy(), int(N))))
+        E1, _, _ = optimise(ctx, g_learn, steps, C0=C0)
+        E2, _, _ = optimise(ctx, np.full(ng, gamma0), steps, C0=C0)
+        out.append((int(N), E1[:, 0], E2[:, 0]))
+        ctx.close()
+    return out
