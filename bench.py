@@ -45,9 +45,10 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["h50", "batch"], default="h50",
-                    help="h50: the single-geometry benchmark; batch: many uneven H-chain frames "
-                         "evaluated concurrently as one CUDA-graph launch")
+    ap.add_argument("--workload", choices=["h50", "h200", "batch"], default="h50",
+                    help="h50: the single-geometry benchmark; h200: the 10 x 20 lattice (nbf 600, "
+                         "naux 2000, nact 200); batch: many uneven H-chain frames evaluated "
+                         "concurrently as one CUDA-graph launch")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-max", type=int, default=32, help="largest chain length in the batch")
     ap.add_argument("--no-graph", action="store_true",
@@ -58,9 +59,15 @@ def parse():
     return ap.parse_args()
 
 
-def workload(seed=2):
+WORKLOAD_H200 = ("H200 10x20 square lattice, spacing 2.0 bohr, 3 s/H (0.2*4^k) + 10 aux s/H (0.1*3^k): "
+                 "nbf=600, naux=2000, nact=200, PNOF7, 100 pairs, N_g=1")
+
+
+def workload(seed=2, name="h50"):
     from paper_2512_13550_gb300 import inputs
     orb, aux = inputs.basis_3s_10aux()
+    if name == "h200":
+        return inputs.lattice(10, 20, 2.0), orb, aux
     xyz = inputs.jittered_chain(50, seed)
     return xyz, orb, aux
 
@@ -273,7 +280,8 @@ def main():
     prec = {"auto": nof.PREC_SPLIT_BF16, "split": nof.PREC_SPLIT_BF16, "fp64": nof.PREC_FP64}[args.precision]
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    xyz, orb, aux = workload(2 + rank)
+    xyz, orb, aux = workload(2 + rank, args.workload)
+    wl_name = WORKLOAD_H200 if args.workload == "h200" else WORKLOAD
 
     def make_ctx(p):
         ctx = nof.Context(precision=p, stream=stream)
@@ -290,6 +298,11 @@ def main():
         ctx = make_ctx(prec)
     s = ctx.sizes
     n = s["nbf"]
+    tiles = None
+    if prec == nof.PREC_SPLIT_BF16:
+        t = ctx.tuned_tiles()
+        tiles = {"gemm1_bn": t[0], "gemm2_bn": t[1], "gemm3_bn": t[2], "gemm3_chunk_atoms": t[3],
+                 "picked_by": "autotuner (CUDA-event timing of candidate launch shapes at set-up)"}
     Q = torch.tensor(inputs.random_orthogonal(n, 0), dtype=torch.float64, device="cuda")
     C = ctx.lowdin(Q)
     gam = torch.tensor(inputs.random_gamma(s["ngamma"], 1), dtype=torch.float64, device="cuda")
@@ -401,14 +414,16 @@ def main():
         return 0
 
     dom_ms, dom_launches, dom_name = prof
-    roof = roofline(prec, s, dom_ms / max(dom_launches, 1), dom_name)
+    roof = roofline(prec, s, dom_ms / max(dom_launches, 1), dom_name, traffic=(
+        TRAFFIC_GEMM1_BYTES if args.workload == "h50" else None))
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16" if prec == nof.PREC_SPLIT_BF16 else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "path": "split-bf16 tcgen05" if prec else "plain fp64",
+        "config": {"workload": wl_name, "path": "split-bf16 tcgen05" if prec else "plain fp64",
+                   "tiles": tiles,
                    "l2": "flushed (256 MiB write) before every timed step",
                    "timing": "CUDA-graph replay of one evaluation per step" if not args.no_graph
                              else "one API call per step",
@@ -423,7 +438,7 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and args.workload == "h50":
         line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -455,12 +470,12 @@ def _peaks():
 # measured on GB300: 1.19 TFLOP/s), x 152 SMs x 2.07 GHz x 2 FLOP = 1.26 TFLOP/s.
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
-# DRAM bytes (read + write) of one GEMM1 launch on this workload from an ncu capture of the current
-# kernel (profiles/), or None when the kernel has changed since the counters were taken.
-TRAFFIC_GEMM1_BYTES = 96442624 + 3868672  # profiles/digit_gemm_h50_ncu.md
+# DRAM bytes (read + write) of one GEMM1 launch on the H50 workload from an ncu capture of the
+# current kernel (profiles/), or None when the kernel has changed since the counters were taken.
+TRAFFIC_GEMM1_BYTES = None
 
 
-def roofline(prec, s, ms_per_launch, name):
+def roofline(prec, s, ms_per_launch, name, traffic=None):
     n, X, a = s["nbf"], s["naux"], s["nact"]
     peaks, src = _peaks()
     if prec == 0:
@@ -471,12 +486,24 @@ def roofline(prec, s, ms_per_launch, name):
                 "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None, "traffic": None,
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe-measured rate)"}
     # half transform GEMM1: reads the four BF16 digit planes of B (8 bytes per element of B) and
-    # writes T as double-floats (8 bytes per element of T)
+    # writes T as double-floats (8 bytes per element of T); on the tensor cores it is 10 BF16
+    # digit-plane products of (X n) x n x a
     nbytes = 8.0 * X * n * n + 8.0 * X * n * a
-    achieved = nbytes / (ms_per_launch / 1e3) / 1e9
+    flops = 10 * 2.0 * X * n * n * a
+    t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
+    t_tc = flops / (peaks["bf16_tflops"] * 1e12)
+    sec = ms_per_launch / 1e3
+    if t_tc > t_hbm:
+        achieved = flops / sec / 1e12
+        peak = peaks["bf16_tflops"]
+        return {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "algorithmic_flops": flops,
+                "algorithmic_bytes": nbytes, "ms_per_launch": ms_per_launch,
+                "peak_source": f"{src} BF16 dense GEMM burst (MEASURED_PEAKS.json bf16_tflops)"}
+    achieved = nbytes / sec / 1e9
     peak = peaks["hbm_gbs"]
     return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": TRAFFIC_GEMM1_BYTES,
+            "frac": achieved / peak, "traffic": traffic,
             "algorithmic_bytes": nbytes, "ms_per_launch": ms_per_launch,
             "peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 

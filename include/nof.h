@@ -43,8 +43,9 @@ extern "C" {
 
 /* Arithmetic of the JK / Lagrangian contractions. */
 #define NOF_PREC_FP64 0       /* plain FP64 SIMT kernels */
-#define NOF_PREC_SPLIT_BF16 1 /* tcgen05 tensor cores on exact BF16 digit planes (4 digits,
-                                 FP32 exact partial sums, about 32 significant bits) */
+#define NOF_PREC_SPLIT_BF16 1 /* tcgen05 tensor cores on exact BF16 digit planes (4 or 5 base-256
+                                 digits per element, about 32 or 40 significant bits; FP32 exact
+                                 partial sums) */
 
 typedef struct nof_ctx nof_ctx;
 
@@ -60,6 +61,10 @@ typedef struct {
     double lr;        /* ADAM learning rate for the orbital rotation (default 0.02) */
     double b1, b2;    /* ADAM moment decays (default 0.9, 0.999) */
     double eps;       /* ADAM epsilon (default 1e-8) */
+    int digits;       /* NOF_PREC_SPLIT_BF16 only: BF16 digits per element, 4 or 5; 0 (default)
+                         chooses 5 when naux * nact > 80000 (where the truncation error of 4
+                         digits, accumulated over the naux * nact terms of the Lagrangian, nears
+                         1e-6), else 4 */
 } nof_options;
 
 /* s-only contracted basis repeated on every atom (host arrays). Shell s has nprim[s]
@@ -103,6 +108,12 @@ int nof_get_SH(nof_ctx* ctx, double* S, double* H);
 /* Copy the fitted tensor B as FP64 [naux][nbf][nbf] (reconstructed from the stored digit
  * planes under NOF_PREC_SPLIT_BF16). Used to check sum_P B^P B^P against exact ERIs. */
 int nof_get_B(nof_ctx* ctx, double* B);
+
+/* Launch shapes the autotuner chose at nof_build_B for the split path (no paper counterpart):
+ * out[0..3] (host) = N-tile widths of the three digit GEMMs (half transform, full transform,
+ * Lagrangian contraction) and the Lagrangian's split-K chunk in K atoms of 16.
+ * NOF_EINVAL unless the context is built with NOF_PREC_SPLIT_BF16. */
+int nof_tuned_tiles(nof_ctx* ctx, int* out);
 
 /* C = S^{-1/2} Q (Loewdin orthonormalisation, S^{-1/2} by a Newton-Schulz iteration on the
  * device). Q: nbf x nbf orthogonal. Gives S-orthonormal orbitals for any orthogonal Q. */
@@ -176,11 +187,13 @@ int nof_profile(nof_ctx* ctx, int enable);
 int nof_profile_read(nof_ctx* ctx, double* ms, int* launches, const char** name);
 
 /* Self-test of the exact BF16 digit-plane tensor-core GEMM (no paper counterpart): random
- * digit planes (M x K and N x K, K = 16 katoms) multiplied on tcgen05 with `splits` K chunks
- * (integer atomics when splits > 1) and by a SIMT integer reference; *max_abs_diff (host)
- * receives the largest difference of the exact fixed-point results (0 when correct).
- * Allocates and frees its own buffers; synchronises the device. */
-int nof_selftest_digit_gemm(int M, int N, int katoms, int splits, unsigned int seed,
+ * digit planes (M x K and N x K, K = 16 katoms, nd = 4 or 5 digits) multiplied on tcgen05 with
+ * N tiles of `bn` columns (16, 32 or 64 with 4 digits; 16 or 32 with 5) and K chunks of
+ * `chunk_atoms` atoms (integer atomics when chunk_atoms < katoms; the last chunk may be
+ * shorter), and by a SIMT integer reference; *max_abs_diff (host) receives the largest
+ * difference of the exact fixed-point results (0 when correct). Allocates and frees its own
+ * buffers; synchronises the device. */
+int nof_selftest_digit_gemm(int M, int N, int bn, int nd, int katoms, int chunk_atoms, unsigned int seed,
                             long long* max_abs_diff);
 
 /* J and K exactly as nof_jk computes them in FP64, without a context and without allocating

@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
     _fields_ = [("ipnof", ctypes.c_int), ("isoftmax", ctypes.c_int), ("ncwo", ctypes.c_int),
                 ("precision", ctypes.c_int), ("on_iters", ctypes.c_int), ("on_lr", ctypes.c_double),
                 ("lr", ctypes.c_double), ("b1", ctypes.c_double), ("b2", ctypes.c_double),
-                ("eps", ctypes.c_double)]
+                ("eps", ctypes.c_double), ("digits", ctypes.c_int)]
 
 
 class CBasis(ctypes.Structure):
@@ -60,6 +60,7 @@ SIGNATURES = {
     "nof_query": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "nof_get_SH": (ctypes.c_int, [_P, _P, _P]),
     "nof_get_B": (ctypes.c_int, [_P, _P]),
+    "nof_tuned_tiles": (ctypes.c_int, [_P, _P]),
     "nof_lowdin": (ctypes.c_int, [_P, _P, _P]),
     "nof_core_guess": (ctypes.c_int, [_P, _P, _P]),
     "nof_jk": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -71,7 +72,7 @@ SIGNATURES = {
     "nof_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "nof_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
     "nof_selftest_digit_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                                ctypes.c_uint, _P]),
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_uint, _P]),
     "nof_jk_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]),
     "nof_mlp_param_count": (ctypes.c_longlong, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "nof_mlp_work_size": (ctypes.c_longlong, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -105,10 +106,13 @@ def kernel_launches() -> int:
     return int(load_library().nof_kernel_launches())
 
 
-def selftest_digit_gemm(M: int, N: int, katoms: int, splits: int = 1, seed: int = 1) -> int:
-    """Largest |difference| between the tcgen05 digit GEMM and a SIMT integer reference."""
+def selftest_digit_gemm(M: int, N: int, bn: int, katoms: int, chunk_atoms: int = 0, seed: int = 1,
+                        nd: int = 4) -> int:
+    """Largest |difference| between the tcgen05 digit GEMM (nd digits, N tiles of bn, K chunks of
+    chunk_atoms atoms; 0 = one chunk) and a SIMT integer reference."""
     out = ctypes.c_longlong(-1)
-    _check(load_library().nof_selftest_digit_gemm(M, N, katoms, splits, seed, ctypes.byref(out)))
+    chunk = chunk_atoms if chunk_atoms > 0 else katoms
+    _check(load_library().nof_selftest_digit_gemm(M, N, bn, nd, katoms, chunk, seed, ctypes.byref(out)))
     return out.value
 
 
@@ -213,6 +217,12 @@ class Context:
         B = self._empty(s["naux"], s["nbf"], s["nbf"])
         _check(load_library().nof_get_B(self._h, _dptr(B)))
         return B
+
+    def tuned_tiles(self):
+        """(N tile of GEMM1, of GEMM2, of GEMM3, GEMM3 split-K chunk in atoms) chosen by the autotuner."""
+        out = (ctypes.c_int * 4)()
+        _check(load_library().nof_tuned_tiles(self._h, out))
+        return tuple(out)
 
     def lowdin(self, Q):
         n = self.sizes["nbf"]

@@ -157,6 +157,7 @@ void nof_default_options(nof_options* o) {
     o->b1 = 0.9;
     o->b2 = 0.999;
     o->eps = 1e-8;
+    o->digits = 0;
 }
 
 const char* nof_last_error(void) { return g_last_error.c_str(); }
@@ -179,8 +180,9 @@ int nof_create(nof_ctx** out, const nof_options* opt, void* stream) {
         return NOF_EINVAL;
     }
     if (o.ncwo < 1 || o.on_iters < 0 ||
-        (o.precision != NOF_PREC_FP64 && o.precision != NOF_PREC_SPLIT_BF16)) {
-        nof_set_error("nof_create: bad ncwo, on_iters or precision");
+        (o.precision != NOF_PREC_FP64 && o.precision != NOF_PREC_SPLIT_BF16) ||
+        (o.digits != 0 && o.digits != 4 && o.digits != 5)) {
+        nof_set_error("nof_create: bad ncwo, on_iters, precision or digits");
         return NOF_EINVAL;
     }
     nof_ctx* c = new (std::nothrow) nof_ctx;
@@ -386,6 +388,7 @@ int nof_build_B(nof_ctx* c, int natom, const double* xyz, const double* Z, int c
             free_system(c);
             return r;
         }
+        dfree(c->B);  // the split path keeps only the digit planes of B
     }
     c->built = 1;
     return NOF_OK;
@@ -410,6 +413,15 @@ int nof_get_SH(nof_ctx* c, double* S, double* H) {
     if (S) NOF_CUDA(cudaMemcpyAsync(S, c->S, bytes, cudaMemcpyDeviceToDevice, c->stream));
     if (H) NOF_CUDA(cudaMemcpyAsync(H, c->H, bytes, cudaMemcpyDeviceToDevice, c->stream));
     return NOF_OK;
+}
+
+int nof_tuned_tiles(nof_ctx* c, int* out) {
+    NOF_TRY(check_ctx(c, true));
+    if (!out || !c->fast) {
+        nof_set_error("nof_tuned_tiles: null output or not a split-precision context");
+        return NOF_EINVAL;
+    }
+    return fast_tiles(c, out);
 }
 
 int nof_get_B(nof_ctx* c, double* B) {

@@ -1,17 +1,23 @@
-// Exact digit-plane GEMM on the 5th-generation tensor cores (tcgen05 + TMEM + TMA), sm_103a.
+// Exact digit-plane GEMM on the 5th-generation tensor cores (tcgen05 + TMEM, bulk copies), sm_103a.
 //
 // Operands are "digit planes": a real matrix X with a power-of-two scale 2^e per row is written
-// as X = 2^e sum_{i<4} d_i 256^{-(i+1)} with integer digits |d_0| <= 256, |d_i| <= 128 (i > 0),
-// each plane stored as BF16 (integers up to 256 are exact in BF16). For A (M x K) and B (N x K),
-//   sum_k A_mk B_nk = 2^{e_m + f_n} 2^{-16} sum_{lvl=0..3} 256^{-lvl} S_lvl,
+// as X = 2^e sum_{i<nd} d_i 256^{-(i+1)} with integer digits |d_0| <= 256, |d_i| <= 128 (i > 0),
+// nd = 4 or 5, each plane stored as BF16 (integers up to 256 are exact in BF16). For A (M x K)
+// and B (N x K),
+//   sum_k A_mk B_nk = 2^{e_m + f_n} 2^{-16} sum_{lvl<nd} 256^{-lvl} S_lvl,
 //   S_lvl = sum_{i+j=lvl} sum_k dA_i[m][k] dB_j[n][k],
-// truncated at digit order 3 (10 plane products). Every product is exact and every partial sum
-// is an integer below 2^24 as long as one accumulation covers K <= 160, so the FP32 TMEM
-// accumulators hold the level sums exactly. The epilogue returns the exact integer
-// V = S_0 256^3 + S_1 256^2 + S_2 256 + S_3 (|V| < 2^49), value = 2^{e_m + f_n - 40} V.
+// truncated at digit order nd - 1 (10 plane products for nd = 4, 15 for nd = 5). Every product
+// is exact and every partial sum is an integer below 2^24 as long as one accumulation covers
+// K <= 160 (nd = 4) or K <= 128 (nd = 5), so the FP32 TMEM accumulators hold the level sums
+// exactly. The epilogue returns the exact integer V = sum_l S_l 256^{nd-1-l}, value
+// 2^{e_m + f_n - 8 (nd + 1)} V.
+// Output modes: the exact int64 V (stored, or added atomically for split-K), the scaled value as
+// a double-float, or, when each row of A and B carries its own scale on every part of K
+// (kPartAtoms atoms), the sum over parts of 2^{e_m,part + f_n,part - 8 (nd + 1)} V_part as FP64
+// (added atomically, or stored per K chunk for a fixed-order reduction).
 //
 // Storage: digit_gemm.h's tile-major core-matrix layout, so one pipeline stage (2 K atoms x 4
-// planes) of a 128-row tile of A, or of all N rows of B, is one contiguous block that a single
+// planes) of a 128-row tile of A, or of a BN-row tile of B, is one contiguous block that a single
 // bulk copy (cp.async.bulk) places in shared memory in the no-swizzle K-major canonical layout
 // (core matrices of 8 rows x 16 bytes; 128 bytes between K-adjacent, 256 bytes between
 // row-adjacent core matrices).
@@ -21,12 +27,15 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cmath>
 #include <cstring>
 
 #include "internal.h"
 #include "digit_gemm.h"
 #include <cuda_bf16.h>
+#include <mutex>
 #include <string>
+#include <vector>
 
 namespace {
 
@@ -119,21 +128,23 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 2^{e} (S0 2^24 + S1 2^16 + S2 2^8 + S3) as a double-float, for level sums S_k that are exact
-// integers below 2^24 held in FP32: error-free two-sums, no integer conversions.
-__device__ __forceinline__ float2 levels_to_df(float S0, float S1, float S2, float S3, int e) {
-    const float a = S0 * 16777216.0f, b = S1 * 65536.0f, c = S2 * 256.0f;
-    float h = a + b;
-    float bb = h - a;
-    float err = (a - (h - bb)) + (b - bb);
-    float h2 = h + c;
-    bb = h2 - h;
-    err += (h - (h2 - bb)) + (c - bb);
-    float h3 = h2 + S3;
-    bb = h3 - h2;
-    err += (h2 - (h3 - bb)) + (S3 - bb);
-    const float hi = h3 + err;
-    const float lo = err - (hi - h3);
+// 2^{e} sum_l S_l 256^{ND-1-l} as a double-float, for level sums S_l that are exact integers
+// below 2^24 held in FP32: each scaled level is exact, and error-free two-sums collect the total
+// (no integer conversions).
+template <int ND>
+__device__ __forceinline__ float2 levels_to_df(const float* S, int e) {
+    float h = S[0] * (float)(1ull << (8 * (ND - 1)));
+    float err = 0.f;
+#pragma unroll
+    for (int l = 1; l < ND; ++l) {
+        const float c = S[l] * (float)(1u << (8 * (ND - 1 - l)));
+        const float h2 = h + c;
+        const float bb = h2 - h;
+        err += (h - (h2 - bb)) + (c - bb);
+        h = h2;
+    }
+    const float hi = h + err;
+    const float lo = err - (hi - h);
     if (e >= -126 && e <= 127) {
         const float sc = __int_as_float((e + 127) << 23);
         return make_float2(hi * sc, lo * sc);
@@ -154,33 +165,39 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
 
-// Persistent, warp-specialised tile loop. Tiles are (128-row block, K chunk) pairs, row block
-// fastest. Warp 0 lane 0 streams A and B stages with TMA through a ring of g.stages shared-memory
-// slots that carries over from one tile to the next; warp 1 lane 0 issues the 10 digit-product
-// MMAs per K atom into one of g.nbuf TMEM accumulator sets (4 levels x N columns each); warps
-// 2..5 drain a finished set (lanes 32*(w%4)..+31), hand it back, and write the exact int64 result.
-// With two sets the drain of tile i overlaps the MMAs of tile i + 1.
+// Persistent, warp-specialised tile loop. A tile is (N tile, 128-row block, K chunk), N tile
+// fastest so that the CTAs working on the N tiles of one row block at the same time share its A
+// stages through L2. A chunk is cut into parts of at most g.apart atoms (one exact accumulation
+// each). Warp 0 lane 0 streams A and B stages with bulk copies through a ring of g.stages
+// shared-memory slots that carries over from one tile to the next; warp 1 lane 0 issues the 10
+// digit-product MMAs per K atom of a part into one of g.nbuf TMEM accumulator sets (4 levels x BN
+// columns); the epilogue warps drain each finished part into a shared-memory staging tile (exact
+// int64 sums, or double-float sums of the scaled values), hand the set back, and after the last
+// part of a tile write the staged rows as contiguous segments. With two sets the drain of one part
+// overlaps the MMAs of the next.
 constexpr int kEpiWarps = 8;  // two per TMEM lane group, each owning half of the columns
 
+__host__ __device__ constexpr int stage_pitch(int BN) { return (BN >= 32 ? BN / 2 : 16) + 1; }
+
+template <int ND>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
 k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, DigitGemmArgs g) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int N = g.N, S = g.stages, NB = g.nbuf;
-    const uint32_t a_stage_bytes = 4u * kStageAtoms * kBM * 32u;
-    const uint32_t b_stage_bytes = 4u * kStageAtoms * (uint32_t)N * 32u;
+    const int BN = g.BN, S = g.stages, NB = g.nbuf;
+    const uint32_t a_stage_bytes = (uint32_t)ND * kStageAtoms * kBM * 32u;
+    const uint32_t b_stage_bytes = (uint32_t)ND * kStageAtoms * (uint32_t)BN * 32u;
     unsigned char* sA = smem;
     unsigned char* sB = smem + S * a_stage_bytes;
     uint64_t* bars = (uint64_t*)(sB + S * b_stage_bytes);  // full[S] empty[S] tfull[2] tempty[2]
     uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 4);
-    // per epilogue warp: 32 rows x 16 double-floats (+1 pad) to turn row-per-thread results into
-    // coalesced row segments
+    // per epilogue warp: 32 rows x (its columns + 1 pad) of int64 or double-float partial sums
+    const int SP = stage_pitch(BN);
     float2* stage_out = (float2*)(((uintptr_t)(tmem_slot + 4) + 15) & ~(uintptr_t)15);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[S]),
                    tfull0 = smem_u32(&bars[2 * S]), tempty0 = smem_u32(&bars[2 * S + 2]);
-    const int ntiles = g.tiles_m * g.kchunks;
-    const int nk = (g.katoms + kStageAtoms - 1) / kStageAtoms;
+    const int ntiles = g.tiles_n * g.tiles_m * g.kchunks;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -206,158 +223,206 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
     bool ok = true;
 
     if (warp == 0) {
-        if (lane == 0) {  // TMA producer
+        if (lane == 0) {  // bulk-copy producer
             int it = 0;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                const int tm = tile % g.tiles_m, kc = tile / g.tiles_m;
-                for (int st = 0; st < nk && ok; ++st, ++it) {
+                const int tn = tile % g.tiles_n, rest = tile / g.tiles_n;
+                const int tm = rest % g.tiles_m, kc = rest / g.tiles_m;
+                const int k0 = kc * g.katoms, tk = min(g.katoms, g.katoms_total - k0);
+                const int nst = (tk + kStageAtoms - 1) / kStageAtoms;
+                for (int st = 0; st < nst && ok; ++st, ++it) {
                     const int s = it % S;
                     if (it >= S) ok = mbar_wait(empty0 + 8 * s, ((it / S) - 1) & 1, g.status);
                     if (!ok) break;
-                    const int ka = kc * g.katoms + st * kStageAtoms;
-                    const int atoms = min(kStageAtoms, g.katoms - st * kStageAtoms);
-                    const uint32_t abytes = (uint32_t)atoms * 4u * kBM * 32u;
-                    const uint32_t bbytes = (uint32_t)atoms * 4u * (uint32_t)N * 32u;
+                    const int ka = k0 + st * kStageAtoms;
+                    const int atoms = min(kStageAtoms, tk - st * kStageAtoms);
+                    const uint32_t abytes = (uint32_t)atoms * ND * kBM * 32u;
+                    const uint32_t bbytes = (uint32_t)atoms * ND * (uint32_t)BN * 32u;
                     mbar_expect_tx(full0 + 8 * s, abytes + bbytes);
                     bulk_load(smem_u32(sA + s * a_stage_bytes),
-                              A + digit_offset(kBM, g.katoms_total, (long long)tm * kBM, (long long)ka * 16, 0),
+                              A + digit_offset(kBM, g.katoms_total, (long long)tm * kBM, (long long)ka * 16, 0, ND),
                               abytes, full0 + 8 * s);
                     bulk_load(smem_u32(sB + s * b_stage_bytes),
-                              B + digit_offset(N, g.katoms_total, 0, (long long)ka * 16, 0), bbytes,
-                              full0 + 8 * s);
+                              B + digit_offset(BN, g.katoms_total, (long long)tn * BN, (long long)ka * 16, 0, ND),
+                              bbytes, full0 + 8 * s);
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
-            const uint32_t idesc = idesc_bf16(N);
-            int it = 0, local = 0;
-            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++local) {
-                const int b = local % NB, use = local / NB;
-                if (use > 0) ok = mbar_wait(tempty0 + 8 * b, (use - 1) & 1, g.status);
-                if (!ok) break;
-                tc_fence_after();
-                const uint32_t acc = tmem + (uint32_t)(b * g.kparts * 4 * N);
-                uint32_t started = 0u;  // bit (part * 4 + level): accumulator already initialised
-                for (int st = 0; st < nk && ok; ++st, ++it) {
-                    const int s = it % S;
-                    ok = mbar_wait(full0 + 8 * s, (it / S) & 1, g.status);
+            const uint32_t idesc = idesc_bf16(BN);
+            int it = 0, unit = 0;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const int kc = tile / (g.tiles_n * g.tiles_m);
+                const int tk = min(g.katoms, g.katoms_total - kc * g.katoms);
+                const int nparts = (tk + g.apart - 1) / g.apart;
+                for (int part = 0; part < nparts && ok; ++part, ++unit) {
+                    const int b = unit % NB, use = unit / NB;
+                    if (use > 0) ok = mbar_wait(tempty0 + 8 * b, (use - 1) & 1, g.status);
                     if (!ok) break;
                     tc_fence_after();
-                    const int atoms = min(kStageAtoms, g.katoms - st * kStageAtoms);
-                    const uint32_t aBase = smem_u32(sA + s * a_stage_bytes), bBase = smem_u32(sB + s * b_stage_bytes);
-                    for (int t = 0; t < atoms; ++t) {
-                        const int part = (st * kStageAtoms + t) / g.apart;
-                        const uint32_t pacc = acc + (uint32_t)(part * 4 * N);
+                    const uint32_t acc = tmem + (uint32_t)(b * ND * BN);
+                    const int pa = min(g.apart, tk - part * g.apart);
+                    const int nst = (pa + kStageAtoms - 1) / kStageAtoms;
+                    uint32_t started = 0u;  // bit l: level l already initialised in this part
+                    for (int st = 0; st < nst && ok; ++st, ++it) {
+                        const int s = it % S;
+                        ok = mbar_wait(full0 + 8 * s, (it / S) & 1, g.status);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const int atoms = min(kStageAtoms, pa - st * kStageAtoms);
+                        const uint32_t aBase = smem_u32(sA + s * a_stage_bytes), bBase = smem_u32(sB + s * b_stage_bytes);
+                        for (int t = 0; t < atoms; ++t) {
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
+                            for (int i = 0; i < ND; ++i) {
 #pragma unroll
-                            for (int j = 0; j < 4 - i; ++j) {
-                                const int l = i + j;
-                                const uint32_t bit = 1u << (part * 4 + l);
-                                // stage block order [atom][plane][rows x 16]
-                                uint64_t ad = sdesc(aBase + (uint32_t)((t * 4 + i) * kBM * 32));
-                                uint64_t bd = sdesc(bBase + (uint32_t)((t * 4 + j) * N * 32));
-                                mma_bf16(pacc + (uint32_t)(l * N), ad, bd, idesc, (started & bit) ? 1u : 0u);
-                                started |= bit;
+                                for (int j = 0; j < ND - i; ++j) {
+                                    const int l = i + j;
+                                    // stage block order [atom][plane][rows x 16]
+                                    uint64_t ad = sdesc(aBase + (uint32_t)((t * ND + i) * kBM * 32));
+                                    uint64_t bd = sdesc(bBase + (uint32_t)((t * ND + j) * BN * 32));
+                                    mma_bf16(acc + (uint32_t)(l * BN), ad, bd, idesc, (started >> l) & 1u);
+                                    started |= 1u << l;
+                                }
                             }
                         }
+                        mma_commit(empty0 + 8 * s);
                     }
-                    mma_commit(empty0 + 8 * s);
+                    if (ok) mma_commit(tfull0 + 8 * b);
                 }
-                if (ok) mma_commit(tfull0 + 8 * b);
             }
         }
     } else {  // epilogue warps 2..2+kEpiWarps-1: lane group q, column half h
         const int q = warp & 3;
         const int h = (warp - 2) / 4;
-        // column halves for N >= 32 (a chunk may run up to 7 columns past its half, still inside
-        // the allocation); for N = 16 the second warp of each lane group has no columns
-        const int cbeg = N >= 32 ? h * (N / 2) : 0;
-        const int cend = N >= 32 ? cbeg + N / 2 : (h ? 0 : N);
+        // column halves for BN >= 32; for BN = 16 the second warp of each lane group has no columns
+        const int cbeg = BN >= 32 ? h * (BN / 2) : 0;
+        const int cend = BN >= 32 ? cbeg + BN / 2 : (h ? 0 : BN);
+        const int cw = cend - cbeg;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        int local = 0;
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++local) {
-            const int b = local % NB, use = local / NB;
-            ok = mbar_wait(tfull0 + 8 * b, use & 1, g.status);
-            if (!ok) break;
-            tc_fence_after();
-            const int tm = tile % g.tiles_m;
-            const int row = tm * kBM + q * 32 + lane;
-            long long* orow = g.out + (long long)row * g.ldo;
-            const uint32_t acc = tmem + lane_base + (uint32_t)(b * g.kparts * 4 * N);
-            float2* st = stage_out + (warp - 2) * 32 * 17;  // this warp's 32 x 16 (+1) staging tile
-            long long* stI = reinterpret_cast<long long*>(st);
-            for (int c0 = cbeg; c0 < cend; c0 += 16) {
-                const int cw = min(16, cend - c0);  // columns of this chunk owned by the warp
-                // the K parts are summed in the staging tile: exactly as int64, or as double-floats
-                const int er = (g.outf && row < g.M) ? g.erow[row] - 40 : 0;
-                for (int part = 0; part < g.kparts; ++part) {
-                    float v0[16], v1[16], v2[16], v3[16];
-                    const uint32_t pacc = acc + (uint32_t)(part * 4 * N);
-                    tmem_ld16(pacc + (uint32_t)c0, v0);
-                    tmem_ld16(pacc + (uint32_t)(N + c0), v1);
-                    tmem_ld16(pacc + (uint32_t)(2 * N + c0), v2);
-                    tmem_ld16(pacc + (uint32_t)(3 * N + c0), v3);
+        float2* st = stage_out + (warp - 2) * 32 * SP;  // this warp's 32 x SP staging tile
+        long long* stI = reinterpret_cast<long long*>(st);
+        int unit = 0;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int tn = tile % g.tiles_n, rest = tile / g.tiles_n;
+            const int tm = rest % g.tiles_m, kc = rest / g.tiles_m;
+            const int tk = min(g.katoms, g.katoms_total - kc * g.katoms);
+            const int nparts = (tk + g.apart - 1) / g.apart;
+            const int rbase = tm * kBM + q * 32;
+            const int row = rbase + lane;
+            const int col0 = tn * BN + cbeg;  // global column of staging column 0
+            const bool partsc = g.epA != nullptr;
+            const bool ints = !g.outf && !partsc;  // exact int64 sums
+            constexpr int kOff = 8 * (ND + 1);  // value = 2^{e_row + e_col - 8 (ND + 1)} V
+            const int er = (g.outf && row < g.M) ? g.erow[row] - kOff : 0;
+            for (int part = 0; part < nparts && ok; ++part, ++unit) {
+                const int b = unit % NB, use = unit / NB;
+                ok = mbar_wait(tfull0 + 8 * b, use & 1, g.status);
+                if (!ok) break;
+                tc_fence_after();
+                const long long gp = (long long)(kc * g.katoms) / g.apart + part;  // part index along K
+                const int erp = (partsc && row < g.M) ? g.epA[gp * g.M + row] - kOff : er;
+                const uint32_t acc = tmem + lane_base + (uint32_t)(b * ND * BN);
+                for (int c0 = 0; c0 < cw; c0 += 16) {
+                    float v[ND][16];
+                    const uint32_t col = (uint32_t)(cbeg + c0);
+#pragma unroll
+                    for (int l = 0; l < ND; ++l) tmem_ld16(acc + (uint32_t)(l * BN) + col, v[l]);
                     tmem_wait_ld();
-                    if (!g.outf) {
+                    if (ints) {
                         // level sums are exact integers below 2^24: 32-bit conversions and a 64-bit
                         // integer sum (64-bit int <-> float conversions run at the FP64 rate here)
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const long long Vp = ((long long)__float2int_rn(v0[j]) << 24) +
-                                                 ((long long)__float2int_rn(v1[j]) << 16) +
-                                                 ((long long)__float2int_rn(v2[j]) << 8) + (long long)__float2int_rn(v3[j]);
-                            stI[lane * 17 + j] = part ? stI[lane * 17 + j] + Vp : Vp;
+                            long long Vp = 0;
+#pragma unroll
+                            for (int l = 0; l < ND; ++l) Vp += (long long)__float2int_rn(v[l][j]) << (8 * (ND - 1 - l));
+                            long long& s = stI[lane * SP + c0 + j];
+                            s = part ? s + Vp : Vp;
                         }
                     } else {
+                        const int* ec = partsc ? g.epB + gp * g.Nvalid : g.ecol;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const float2 x = levels_to_df(v0[j], v1[j], v2[j], v3[j], er + g.ecol[min(c0 + j, N - 1)]);
-                            st[lane * 17 + j] = part ? df2_add(st[lane * 17 + j], x) : x;
+                            const int e = erp + ec[min(col0 + c0 + j, g.Nvalid - 1)];
+                            float S[ND];
+#pragma unroll
+                            for (int l = 0; l < ND; ++l) S[l] = v[l][j];
+                            const float2 x = levels_to_df<ND>(S, e);
+                            float2& s = st[lane * SP + c0 + j];
+                            s = part ? df2_add(s, x) : x;
                         }
                     }
                 }
-                if (!g.outf) {
-                    if (row < g.M) {
-                        const int lim = min(cend, g.Nvalid);  // columns owned by this warp
-                        const long long* V = stI + lane * 17;
-                        if (g.atomic) {
-                            for (int j = 0; j < 16; ++j)
-                                if (c0 + j < lim) atomicAdd((unsigned long long*)(orow + c0 + j), (unsigned long long)V[j]);
-                        } else {
-                            for (int j = 0; j < 16; ++j)
-                                if (c0 + j < lim) orow[c0 + j] = V[j];
-                        }
+                // every TMEM read of this set is complete: hand it back to the MMA warp
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+            }
+            if (!ok) break;
+            __syncwarp();
+            const int ncol = min(cw, g.Nvalid - col0);  // valid staged columns
+            if (ncol > 0) {
+                if (g.out) {
+                    for (int idx = lane; idx < 32 * cw; idx += 32) {
+                        const int rr = idx / cw, cc = idx - rr * cw;
+                        const int grow = rbase + rr;
+                        if (grow >= g.M || cc >= ncol) continue;
+                        long long* dst = g.out + (long long)grow * g.ldo + col0 + cc;
+                        const long long V = stI[rr * SP + cc];
+                        if (g.atomic) atomicAdd((unsigned long long*)dst, (unsigned long long)V);
+                        else *dst = V;
+                    }
+                } else if (g.outd) {
+                    for (int idx = lane; idx < 32 * cw; idx += 32) {
+                        const int rr = idx / cw, cc = idx - rr * cw;
+                        const int grow = rbase + rr;
+                        if (grow >= g.M || cc >= ncol) continue;
+                        double* dst = g.outd + (long long)kc * g.chunk_stride + (long long)grow * g.ldo + col0 + cc;
+                        const float2 x = st[rr * SP + cc];
+                        const double v = (double)x.x + (double)x.y;
+                        if (g.atomic) atomicAdd(dst, v);
+                        else *dst = v;
                     }
                 } else {
-                    // write as whole 128-byte row segments (4 lanes per row, 8 rows per pass)
-                    __syncwarp();
-                    const int rbase = tm * kBM + q * 32;
-#pragma unroll
-                    for (int it2 = 0; it2 < 4; ++it2) {
-                        const int rr = it2 * 8 + (lane >> 2);
-                        const int cc = (lane & 3) * 4;
+                    // pairs of columns as 16-byte stores, consecutive lanes along a row
+                    const int hp = cw / 2;
+                    for (int idx = lane; idx < 32 * hp; idx += 32) {
+                        const int rr = idx / hp, cc = 2 * (idx - rr * hp);
                         const int grow = rbase + rr;
-                        if (cc >= cw) continue;
-                        if (grow < g.M && c0 + cc + 3 < g.Nvalid && cc + 3 < cw) {
-                            float2* dst = g.outf + (long long)grow * g.ldo + c0 + cc;
-                            const float2* src = st + rr * 17 + cc;
-                            reinterpret_cast<float4*>(dst)[0] = make_float4(src[0].x, src[0].y, src[1].x, src[1].y);
-                            reinterpret_cast<float4*>(dst)[1] = make_float4(src[2].x, src[2].y, src[3].x, src[3].y);
-                        } else if (grow < g.M) {
-                            for (int u = 0; u < 4; ++u)
-                                if (c0 + cc + u < g.Nvalid && cc + u < cw)
-                                    g.outf[(long long)grow * g.ldo + c0 + cc + u] = st[rr * 17 + cc + u];
+                        if (grow >= g.M || cc >= ncol) continue;
+                        float2* dst = g.outf + (long long)grow * g.ldo + col0 + cc;
+                        const float2 x0 = st[rr * SP + cc];
+                        if (cc + 1 < ncol) {
+                            const float2 x1 = st[rr * SP + cc + 1];
+                            *reinterpret_cast<float4*>(dst) = make_float4(x0.x, x0.y, x1.x, x1.y);
+                        } else {
+                            *dst = x0;
                         }
                     }
+                    // column maxima per group: most candidates are below the running maximum,
+                    // so read before the atomic (a stale read only costs an extra atomic)
+                    if (g.colmax && lane < ncol && rbase < g.M) {  // lane = column: runs of rows of a group
+                        int grp = rbase / g.group_rows;
+                        int next = (grp + 1) * g.group_rows;  // first row of the next group
+                        const int rend = min(32, g.M - rbase);
+                        float m = 0.f;
+                        for (int rr = 0; rr < rend; ++rr) {
+                            if (rbase + rr == next) {
+                                unsigned* dst = g.colmax + (long long)grp * g.Nvalid + col0 + lane;
+                                if (__float_as_uint(m) > __ldcg(dst)) atomicMax(dst, __float_as_uint(m));
+                                m = 0.f;
+                                ++grp;
+                                next += g.group_rows;
+                            }
+                            m = fmaxf(m, fabsf(st[rr * SP + lane].x));
+                        }
+                        unsigned* dst = g.colmax + (long long)grp * g.Nvalid + col0 + lane;
+                        if (__float_as_uint(m) > __ldcg(dst)) atomicMax(dst, __float_as_uint(m));
+                    }
                 }
-                __syncwarp();
             }
-            // every TMEM read of this set is complete: hand it back to the MMA warp
-            tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(tempty0 + 8 * b);
         }
     }
     __syncwarp();
@@ -375,83 +440,170 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
     }
 }
 
-}  // namespace
+constexpr size_t kSmemLimit = 227 * 1024;
 
-static int stages_for(int N) { return N > 64 ? 2 : 3; }
-
-size_t digit_gemm_smem(int N) {
-    return (size_t)stages_for(N) * 4 * kStageAtoms * 32 * (kBM + N) + 8 * (2 * stages_for(N) + 4) + 16 + 16 +
-           kEpiWarps * 32 * 17 * sizeof(float2) + 1024;
+size_t smem_bytes(int BN, int stages, int nd) {
+    return (size_t)stages * nd * kStageAtoms * 32 * (kBM + BN) + 8 * (2 * stages + 4) + 16 + 16 +
+           (size_t)kEpiWarps * 32 * stage_pitch(BN) * sizeof(float2) + 1024;
 }
 
-int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int N, int katoms_total,
-                    int katoms, int M, int Nvalid, long long* out, long long ldo, bool atomic, int* status) {
-    const int kparts = (katoms + 9) / 10;
-    if (N % 16 || N < 16 || N > 128 || katoms < 1 || katoms_total % katoms || M <= 0 || Nvalid > N ||
-        kparts * 4 * N > 512) {
-        nof_set_error("digit_gemm: unsupported shape");
+}  // namespace
+
+int digit_gemm_max_stages(int BN, int nd) {
+    int s = 2;
+    while (s < 6 && smem_bytes(BN, s + 1, nd) <= kSmemLimit) ++s;
+    return s;
+}
+
+int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int M, int Nvalid, int BN, int nd,
+                    int katoms_total, int chunk_atoms, int stages, const DigitGemmOut& o, int* status) {
+    const int nout = (o.out != nullptr) + (o.outf != nullptr) + (o.outd != nullptr);
+    const bool partsc = o.epA != nullptr;
+    if ((nd != 4 && nd != 5) || !digit_bn_ok(BN, nd) || M <= 0 || Nvalid <= 0 || katoms_total < 1 ||
+        chunk_atoms < 1 || nout != 1 || (o.outf && ((o.ldo & 1) || !o.erow || !o.ecol || o.atomic)) ||
+        o.ldo < Nvalid || (o.colmax && (o.group_rows < 1 || !o.outf)) || (partsc != (o.epB != nullptr)) ||
+        (partsc && (!o.outd || chunk_atoms % kPartAtoms)) || (o.outd && !partsc) ||
+        (o.chunk_stride && (!o.outd || o.atomic || o.chunk_stride < (long long)M * o.ldo))) {
+        nof_set_error("digit_gemm: unsupported shape or output mode");
+        return NOF_EINVAL;
+    }
+    // the exact int64 result of one output element: per K element |V| <= 65536 256^{nd-1} (1 +
+    // 2^-8 + 1.25 2^-16 + ...) < 1.004 * 2^16 * 256^{nd-1}; keep the K sum below 2^63
+    if (o.out && (double)katoms_total * 16.0 * 1.004 * 65536.0 * std::pow(256.0, nd - 1) > 9.0e18) {
+        nof_set_error("digit_gemm: K too long for an exact int64 sum");
+        return NOF_EINVAL;
+    }
+    if (stages == 0) stages = digit_gemm_max_stages(BN, nd);
+    if (stages < 2 || smem_bytes(BN, stages, nd) > kSmemLimit) {
+        nof_set_error("digit_gemm: shared memory plan too large");
         return NOF_EINVAL;
     }
     p->A = A;
     p->B = B;
     DigitGemmArgs& g = p->g;
-    g.outf = nullptr;
-    g.erow = nullptr;
-    g.ecol = nullptr;
-    g.M = M; g.N = N; g.Nvalid = Nvalid; g.katoms = katoms; g.katoms_total = katoms_total;
-    g.out = out; g.ldo = ldo; g.atomic = atomic ? 1 : 0; g.status = status;
-    g.stages = stages_for(N);
-    g.kparts = kparts;
-    g.apart = (katoms + kparts - 1) / kparts;
-    g.nbuf = (2 * kparts * 4 * N <= 512) ? 2 : 1;
-    g.tiles_m = (M + kBM - 1) / kBM;
-    g.kchunks = katoms_total / katoms;
+    g.nd = nd;
+    g.M = M;
+    g.BN = BN;
+    g.tiles_n = (Nvalid + BN - 1) / BN;
+    g.Nvalid = Nvalid;
+    g.katoms = chunk_atoms < katoms_total ? chunk_atoms : katoms_total;
+    g.katoms_total = katoms_total;
+    g.apart = (partsc || nd == 5) ? kPartAtoms : 10;
+    g.nbuf = 2;
     int cols = 32;
-    while (cols < g.nbuf * kparts * 4 * N) cols *= 2;
+    while (cols < g.nbuf * nd * BN) cols *= 2;
     g.tmem_cols = cols;
-    p->smem = digit_gemm_smem(N);
+    g.out = o.out;
+    g.outf = o.outf;
+    g.outd = o.outd;
+    g.chunk_stride = o.chunk_stride;
+    g.ldo = o.ldo;
+    g.atomic = o.atomic ? 1 : 0;
+    g.erow = o.erow;
+    g.ecol = o.ecol;
+    g.epA = o.epA;
+    g.epB = o.epB;
+    g.colmax = o.colmax;
+    g.group_rows = o.group_rows;
+    g.status = status;
+    g.stages = stages;
+    g.tiles_m = (M + kBM - 1) / kBM;
+    g.kchunks = (katoms_total + g.katoms - 1) / g.katoms;
+    if (g.kchunks > 1 && !o.atomic && !o.chunk_stride) {
+        nof_set_error("digit_gemm: split-K needs an atomic or per-chunk output");
+        return NOF_EINVAL;
+    }
+    p->smem = smem_bytes(BN, stages, nd);
     static int sms = 0;
     if (!sms) {
         int dev = 0;
         NOF_CUDA(cudaGetDevice(&dev));
         NOF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
     }
-    if (p->smem > 220 * 1024) {
-        nof_set_error("digit_gemm: shared memory plan too large");
+    const long long ntiles = (long long)g.tiles_n * g.tiles_m * g.kchunks;
+    if (ntiles > 0x7fffffffLL) {
+        nof_set_error("digit_gemm: too many tiles");
         return NOF_EINVAL;
     }
-    const int ntiles = g.tiles_m * g.kchunks;
-    p->grid = dim3(ntiles < sms ? ntiles : sms, 1);
-    return NOF_OK;
-}
-
-int digit_gemm_plan_scaled(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int N, int katoms, int M,
-                           int Nvalid, float2* out, long long ldo, const int* erow, const int* ecol, int* status) {
-    if (ldo & 1) {
-        nof_set_error("digit_gemm: the scaled output needs an even leading dimension");
-        return NOF_EINVAL;
-    }
-    NOF_TRY(digit_gemm_plan(p, A, B, N, katoms, katoms, M, Nvalid, nullptr, ldo, false, status));
-    p->g.outf = out;
-    p->g.erow = erow;
-    p->g.ecol = ecol;
+    p->grid = dim3((unsigned)(ntiles < sms ? ntiles : sms), 1);
     return NOF_OK;
 }
 
 int digit_gemm_run(const DigitGemmPlan& p, cudaStream_t st) {
-    k_digit_gemm<<<p.grid, 64 + 32 * kEpiWarps, p.smem, st>>>(p.A, p.B, p.g);
+    if (p.g.nd == 5) k_digit_gemm<5><<<p.grid, 64 + 32 * kEpiWarps, p.smem, st>>>(p.A, p.B, p.g);
+    else k_digit_gemm<4><<<p.grid, 64 + 32 * kEpiWarps, p.smem, st>>>(p.A, p.B, p.g);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
 
-// A: digit planes with M rows (tiles of 128), B: digit planes with N rows (one tile), both with
-// katoms_total K atoms. Each tile accumulates katoms atoms (split-K chunks = katoms_total/katoms).
-int digit_gemm(const uint16_t* A, const uint16_t* B, int N, int katoms_total, int katoms, int M,
-               int Nvalid, long long* out, long long ldo, bool atomic, int* status, cudaStream_t st) {
-    DigitGemmPlan p;
-    NOF_TRY(digit_gemm_plan(&p, A, B, N, katoms_total, katoms, M, Nvalid, out, ldo, atomic, status));
-    return digit_gemm_run(p, st);
+// ---------------------------------------------------------------------------------------
+// Autotuner
+// ---------------------------------------------------------------------------------------
+namespace {
+struct TuneEntry {
+    DigitTuneKey key;
+    int best;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+bool same_key(const DigitTuneKey& a, const DigitTuneKey& b) {
+    return a.kind == b.kind && a.M == b.M && a.Nvalid == b.Nvalid && a.katoms_total == b.katoms_total &&
+           a.extra == b.extra;
+}
+}  // namespace
+
+int digit_gemm_pick(const DigitTuneKey& key, const DigitGemmPlan* cands, int ncand, cudaStream_t st, int* best) {
+    if (ncand < 1) {
+        nof_set_error("digit_gemm_pick: no candidates");
+        return NOF_EINVAL;
+    }
+    *best = 0;
+    if (ncand == 1) return NOF_OK;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const TuneEntry& e : g_tune)
+            if (same_key(e.key, key) && e.best < ncand) {
+                *best = e.best;
+                return NOF_OK;
+            }
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NOF_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return NOF_OK;  // no timing inside a capture
+    cudaEvent_t e0, e1;
+    NOF_CUDA(cudaEventCreate(&e0));
+    NOF_CUDA(cudaEventCreate(&e1));
+    float best_ms = 3.0e38f;
+    int r = NOF_OK;
+    for (int i = 0; i < ncand && r == NOF_OK; ++i) {
+        r = digit_gemm_run(cands[i], st);  // warm-up
+        float ms = 3.0e38f;
+        for (int rep = 0; rep < 3 && r == NOF_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            r = digit_gemm_run(cands[i], st);
+            cudaEventRecord(e1, st);
+            cudaError_t ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) {
+                r = nof_cuda_fail(ce, "autotune timing", __FILE__, __LINE__);
+                break;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = t < ms ? t : ms;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != NOF_OK) return r;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.push_back({key, *best});
+    return NOF_OK;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -463,12 +615,13 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
     return x;
 }
-// element (row r, k, plane) of a digit tensor: plane 0 digits in [-256, 256], others in
-// [-128, 128]; rows >= valid_rows are zero
-__global__ void k_random_digits(uint16_t* P, int RT, int rows_pad, int valid_rows, int katoms, uint32_t seed) {
+// element (row r, k, plane) of a digit tensor with nd planes: plane 0 digits in [-256, 256],
+// others in [-128, 128]; rows >= valid_rows are zero
+__global__ void k_random_digits(uint16_t* P, int RT, int rows_pad, int valid_rows, int katoms, int nd,
+                                uint32_t seed) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long per_plane = (long long)rows_pad * katoms * 16;
-    if (idx >= 4 * per_plane) return;
+    if (idx >= nd * per_plane) return;
     int plane = (int)(idx / per_plane);
     long long rem = idx - plane * per_plane;
     long long r = rem / (katoms * 16);
@@ -477,23 +630,26 @@ __global__ void k_random_digits(uint16_t* P, int RT, int rows_pad, int valid_row
     int v = (int)(hash32((uint32_t)idx * 2654435761u + seed) % (uint32_t)range) - range / 2;
     if (r >= valid_rows) v = 0;
     __nv_bfloat16 b = __int2bfloat16_rn(v);
-    P[digit_offset(RT, katoms, r, k, plane)] = *reinterpret_cast<uint16_t*>(&b);
+    P[digit_offset(RT, katoms, r, k, plane, nd)] = *reinterpret_cast<uint16_t*>(&b);
 }
-__device__ __forceinline__ int digit_at(const uint16_t* P, int RT, int katoms, int plane, int r, int k) {
-    uint16_t u = P[digit_offset(RT, katoms, r, k, plane)];
+__device__ __forceinline__ int digit_at(const uint16_t* P, int RT, int katoms, int nd, int plane, int r, int k) {
+    uint16_t u = P[digit_offset(RT, katoms, r, k, plane, nd)];
     __nv_bfloat16 b = *reinterpret_cast<__nv_bfloat16*>(&u);
     return (int)__bfloat162float(b);
 }
-__global__ void k_ref_digit_gemm(const uint16_t* A, const uint16_t* B, int NB, int katoms, int M, int N,
+// V = sum_{i + j < nd} 256^{nd-1-(i+j)} sum_k dA_i dB_j in int64 (plain loops)
+__global__ void k_ref_digit_gemm(const uint16_t* A, const uint16_t* B, int NB, int katoms, int nd, int M, int N,
                                  long long* out) {
     int m = blockIdx.x * blockDim.x + threadIdx.x, n = blockIdx.y;
     if (m >= M || n >= N) return;
-    long long S[4] = {0, 0, 0, 0};
+    long long S[5] = {0, 0, 0, 0, 0};
     for (int k = 0; k < katoms * 16; ++k)
-        for (int i = 0; i < 4; ++i)
-            for (int j = 0; j < 4 - i; ++j)
-                S[i + j] += (long long)digit_at(A, 128, katoms, i, m, k) * digit_at(B, NB, katoms, j, n, k);
-    out[(long long)m * N + n] = S[0] * 16777216LL + S[1] * 65536LL + S[2] * 256LL + S[3];
+        for (int i = 0; i < nd; ++i)
+            for (int j = 0; j < nd - i; ++j)
+                S[i + j] += (long long)digit_at(A, 128, katoms, nd, i, m, k) * digit_at(B, NB, katoms, nd, j, n, k);
+    long long V = 0;
+    for (int l = 0; l < nd; ++l) V = V * 256 + S[l];
+    out[(long long)m * N + n] = V;
 }
 __global__ void k_max_absdiff(const long long* a, const long long* b, long long n, unsigned long long* out) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -505,14 +661,15 @@ __global__ void k_max_absdiff(const long long* a, const long long* b, long long 
 
 }  // namespace
 
-extern "C" int nof_selftest_digit_gemm(int M, int N, int katoms, int splits, unsigned int seed,
-                                       long long* max_abs_diff) {
-    if (!max_abs_diff || M <= 0 || N <= 0 || N % 16 || katoms <= 0 || splits <= 0 || katoms % splits) {
+extern "C" int nof_selftest_digit_gemm(int M, int N, int bn, int nd, int katoms, int chunk_atoms,
+                                       unsigned int seed, long long* max_abs_diff) {
+    if (!max_abs_diff || M <= 0 || N <= 0 || (nd != 4 && nd != 5) || !digit_bn_ok(bn, nd) || katoms <= 0 ||
+        chunk_atoms <= 0) {
         nof_set_error("nof_selftest_digit_gemm: bad arguments");
         return NOF_EINVAL;
     }
-    int rowsA = (M + 127) / 128 * 128;
-    const long long na = digit_elems(128, M, katoms), nb = digit_elems(N, N, katoms);
+    const int rowsA = (M + 127) / 128 * 128, rowsB = (N + bn - 1) / bn * bn;
+    const long long na = digit_elems(128, M, katoms, nd), nb = digit_elems(bn, N, katoms, nd);
     uint16_t *A = nullptr, *B = nullptr;
     long long *C1 = nullptr, *C2 = nullptr;
     unsigned long long* dmax = nullptr;
@@ -530,12 +687,18 @@ extern "C" int nof_selftest_digit_gemm(int M, int N, int katoms, int splits, uns
         cudaMemset(dmax, 0, 8);
         cudaMemset(status, 0, 4);
         cudaMemset(C1, 0, 8ull * M * N);
-        k_random_digits<<<(unsigned)((na + 255) / 256), 256>>>(A, 128, rowsA, M, katoms, seed);
-        k_random_digits<<<(unsigned)((nb + 255) / 256), 256>>>(B, N, N, N, katoms, seed ^ 0x9e3779b9u);
-        r = digit_gemm(A, B, N, katoms, katoms / splits, M, N, C1, N, splits > 1, status, 0);
+        k_random_digits<<<(unsigned)((na + 255) / 256), 256>>>(A, 128, rowsA, M, katoms, nd, seed);
+        k_random_digits<<<(unsigned)((nb + 255) / 256), 256>>>(B, bn, rowsB, N, katoms, nd, seed ^ 0x9e3779b9u);
+        DigitGemmOut o;
+        o.out = C1;
+        o.ldo = N;
+        o.atomic = chunk_atoms < katoms;
+        DigitGemmPlan p;
+        r = digit_gemm_plan(&p, A, B, M, N, bn, nd, katoms, chunk_atoms, 0, o, status);
+        if (r == NOF_OK) r = digit_gemm_run(p, 0);
     }
     if (r == NOF_OK) {
-        k_ref_digit_gemm<<<dim3((M + 127) / 128, N), 128>>>(A, B, N, katoms, M, N, C2);
+        k_ref_digit_gemm<<<dim3((M + 127) / 128, N), 128>>>(A, B, bn, katoms, nd, M, N, C2);
         k_max_absdiff<<<(unsigned)(((long long)M * N + 255) / 256), 256>>>(C1, C2, (long long)M * N, dmax);
         unsigned long long h = 0;
         int hs = 0;

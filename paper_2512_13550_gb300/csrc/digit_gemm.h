@@ -4,38 +4,59 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Tile widths along N the kernel supports (two TMEM accumulator sets of nd levels x BN columns
+// must fit the 512 TMEM columns, and the epilogue splits BN >= 32 into two column halves):
+// 16, 32, 64 with 4 digits, 16, 32 with 5 digits.
+constexpr int kDigitBN[3] = {16, 32, 64};
+inline bool digit_bn_ok(int BN, int nd) { return (BN == 16 || BN == 32 || BN == 64) && 2 * nd * BN <= 512; }
+
 struct DigitGemmArgs {
-    int M;          // valid rows of A (rows of the output)
-    int N;          // padded N (multiple of 16, <= 128); B has N rows
-    int Nvalid;     // columns written
-    int katoms;     // K atoms (16 each) accumulated per tile
-    int kparts;     // exact accumulations per tile: atoms [p * apart, (p + 1) * apart) go to TMEM level
-    int apart;      // set p (apart <= 10 keeps every FP32 partial sum exact); parts are summed in the epilogue
-    int katoms_total;  // K atoms of the whole operand (storage stride)
-    int tmem_cols;  // TMEM columns allocated (power of two >= 4 N)
-    long long* out; // int64 fixed-point output, row-major with leading dimension ldo
+    int nd;            // digits per element (4 or 5): nd (nd + 1) / 2 plane products per K atom
+    int M;             // valid rows of A (rows of the output)
+    int BN;            // tile width along N: 16, 32 or 64; B is stored in tiles of BN rows
+    int tiles_n;       // N tiles
+    int Nvalid;        // output columns written (<= tiles_n * BN)
+    int katoms;        // K atoms (16 each) per split-K chunk; the last chunk may be shorter
+    int katoms_total;  // K atoms of the operands (storage stride)
+    int apart;         // atoms per exact accumulation (even; <= 10 with 4 digits, <= 8 with 5: every
+                       // FP32 partial sum stays an integer below 2^24); parts are summed in the epilogue
+    int tmem_cols;     // TMEM columns allocated (power of two >= nbuf * 4 * BN)
+    long long* out;    // int64 fixed-point output, row-major with leading dimension ldo
     long long ldo;
-    int atomic;     // 1: atomicAdd (split-K partials), 0: store
+    int atomic;        // 1: atomicAdd (split-K partials), 0: store
     // scaled output: when outf != nullptr the result 2^{erow[m] + ecol[n] - 40} V is stored as a
     // double-float (float2: hi, lo) at outf[m * ldo + n] instead of the int64 V
     float2* outf;
     const int* erow;
     const int* ecol;
-    int* status;    // device status word (NOF_DEV_TIMEOUT on a timed-out wait)
-    int stages;     // shared-memory ring slots (each 2 K atoms of A and B, 4 planes)
-    int nbuf;       // TMEM accumulator sets (2 when 8 N <= 512 columns)
-    int tiles_m;    // 128-row blocks
-    int kchunks;    // K chunks (split-K); tiles = tiles_m * kchunks, row block fastest
+    // per-part scales: when epA != nullptr the value of part gp (atoms [gp apart, (gp+1) apart)
+    // of K) is 2^{epA[gp * M + m] + epB[gp * Nvalid + n] - 40} V_part, summed as double-floats
+    // (each operand row carries its own scale on each part of K)
+    const int* epA;
+    const int* epB;
+    // double output: when outd != nullptr the (scaled) result is added (atomic) or stored as FP64,
+    // at outd + kc * chunk_stride for K chunk kc when chunk_stride > 0 (partials summed later)
+    double* outd;
+    long long chunk_stride;
+    // optional maxima of |value| (scaled output only; float bits, atomicMax, caller zeroes):
+    // colmax[(m / group_rows) * Nvalid + n] over the rows of a group of group_rows consecutive rows
+    unsigned* colmax;
+    int group_rows;
+    int* status;       // device status word (NOF_DEV_TIMEOUT on a timed-out wait)
+    int stages;        // shared-memory ring slots (each 2 K atoms of A and B, nd planes)
+    int nbuf;          // TMEM accumulator sets
+    int tiles_m;       // 128-row blocks
+    int kchunks;       // K chunks (split-K); tile order: N tile fastest, then row block, then chunk
 };
 
 // Digit-plane storage ("tile-major core-matrix" layout). An operand with R rows is cut into tiles
-// of RT rows (RT = 128 for the M side, RT = N for the N side; R padded to a multiple of RT with
-// zero rows) and K atoms of 16. Tile rt, atom t, plane i is one contiguous block of RT x 16 BF16
-// in the order the tensor core reads without swizzling: 8-row x 8-element core matrices
-// (128 bytes) ordered [row group r/8][k half kk/8][row r%8][element kk%8]. The two atoms and four
-// planes of one pipeline stage are therefore one contiguous RT * 256-byte block.
+// of RT rows (RT = 128 for the M side, RT = BN for the N side; R padded to a multiple of RT with
+// zero rows) and K atoms of 16. Tile rt, atom t, plane i (of nd) is one contiguous block of
+// RT x 16 BF16 in the order the tensor core reads without swizzling: 8-row x 8-element core
+// matrices (128 bytes) ordered [row group r/8][k half kk/8][row r%8][element kk%8]. The two atoms
+// and nd planes of one pipeline stage are therefore one contiguous RT * 64 nd-byte block.
 __host__ __device__ __forceinline__ long long digit_offset(int RT, int katoms, long long row, long long k,
-                                                           int plane) {
+                                                           int plane, int nd) {
     // 32-bit index arithmetic (rows and K stay below 2^31; 64-bit division is emulated)
     const unsigned ur = (unsigned)row, uk = (unsigned)k;
     unsigned tile, r;
@@ -52,13 +73,31 @@ __host__ __device__ __forceinline__ long long digit_offset(int RT, int katoms, l
         r = ur - tile * (unsigned)RT;
     }
     const unsigned t = uk >> 4, kk = uk & 15u;
-    const long long block = (((long long)tile * katoms + t) * 4 + plane) * (long long)(RT * 16);
+    const long long block = (((long long)tile * katoms + t) * nd + plane) * (long long)(RT * 16);
     return block + (long long)(((r >> 3) * 2 + (kk >> 3)) * 64 + (r & 7) * 8 + (kk & 7));
 }
-// elements of a digit tensor with R rows (padded to RT) and katoms atoms
-__host__ __device__ __forceinline__ long long digit_elems(int RT, long long R, int katoms) {
-    return (R + RT - 1) / RT * RT * (long long)katoms * 16 * 4;
+// elements of a digit tensor with R rows (padded to RT), katoms atoms and nd planes
+__host__ __device__ __forceinline__ long long digit_elems(int RT, long long R, int katoms, int nd) {
+    return (R + RT - 1) / RT * RT * (long long)katoms * 16 * nd;
 }
+
+// Where a GEMM writes (one of out / outf / outd) and how its parts are scaled.
+struct DigitGemmOut {
+    long long* out = nullptr;  // int64 V
+    float2* outf = nullptr;    // scaled double-float
+    double* outd = nullptr;    // FP64 (with per-part scales)
+    long long chunk_stride = 0;  // > 0: FP64 partial of K chunk kc at outd + kc * chunk_stride
+    long long ldo = 0;
+    bool atomic = false;
+    const int* erow = nullptr;
+    const int* ecol = nullptr;
+    const int* epA = nullptr;  // per-part scales [parts][M] and [parts][Nvalid]; parts of 8 atoms
+    const int* epB = nullptr;
+    unsigned* colmax = nullptr;
+    int group_rows = 1;
+};
+// K atoms per part when each operand row carries a scale per part of K
+constexpr int kPartAtoms = 8;
 
 // A launch plan (pointers and shapes fixed at set-up).
 struct DigitGemmPlan {
@@ -69,13 +108,18 @@ struct DigitGemmPlan {
     size_t smem;
 };
 
-size_t digit_gemm_smem(int N);
-int digit_gemm_plan(DigitGemmPlan* plan, const uint16_t* A, const uint16_t* B, int N, int katoms_total,
-                    int katoms, int M, int Nvalid, long long* out, long long ldo, bool atomic, int* status);
-// Same GEMM with the scaled double-float output (value = 2^{erow[m] + ecol[n] - 40} V).
-int digit_gemm_plan_scaled(DigitGemmPlan* plan, const uint16_t* A, const uint16_t* B, int N, int katoms,
-                           int M, int Nvalid, float2* out, long long ldo, const int* erow, const int* ecol,
-                           int* status);
+// Plan C = A B^T for A (M x 16 katoms_total, nd digit planes, row tiles of 128) and B (tiles of
+// BN rows), split-K in chunks of chunk_atoms; stages = 0 picks the deepest ring that fits.
+int digit_gemm_plan(DigitGemmPlan* plan, const uint16_t* A, const uint16_t* B, int M, int Nvalid, int BN,
+                    int nd, int katoms_total, int chunk_atoms, int stages, const DigitGemmOut& out,
+                    int* status);
 int digit_gemm_run(const DigitGemmPlan& plan, cudaStream_t st);
-int digit_gemm(const uint16_t* A, const uint16_t* B, int N, int katoms_total, int katoms, int M,
-               int Nvalid, long long* out, long long ldo, bool atomic, int* status, cudaStream_t st);
+int digit_gemm_max_stages(int BN, int nd);
+
+// Autotuner: times every candidate (one warm-up launch, then the best of three timed with CUDA
+// events on `st`) and returns the index of the fastest. Results are remembered per `key` for the
+// life of the process, so equal shapes are timed once.
+struct DigitTuneKey {
+    int kind, M, Nvalid, katoms_total, extra;
+};
+int digit_gemm_pick(const DigitTuneKey& key, const DigitGemmPlan* cands, int ncand, cudaStream_t st, int* best);

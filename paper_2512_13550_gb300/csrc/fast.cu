@@ -11,7 +11,11 @@
 //   GEMM3  Lam'_{mu p} = sum_{P, r} T^P_{mu r} W^P_{r p}   split-K over (P, r), integer atomics
 // with W^P_rp = delta_rp D^P_p - B_pr b^P_rp, D^P = A d^P, d^P_p = b^P_pp (Eq. PNOF coefficients).
 // Each operand carries 4 signed base-256 digits (about 32 significant bits) under a power-of-two
-// scale per row; each GEMM result is an exact int64 V with value 2^{e_row + e_col - 40} V.
+// scale per row (GEMM1, GEMM2) or per row and part of 128 K elements (GEMM3, whose K runs over
+// all aux indices, across which |T| and |W| vary by orders of magnitude); each exact part sum V
+// has value 2^{e_row + e_col - 40} V. GEMM1's epilogue also records the maxima of |T| per (P, p)
+// over mu that set the digit scales of T for GEMM2.
+// Tile widths, pipeline depth and the split-K chunk of each GEMM come from the autotuner.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -20,21 +24,21 @@
 #include "internal.h"
 
 struct FastState {
-    int n, X, a, ap, katK, nblk, katoms3;
+    int n, X, a, ap, katK, nkp, nd;
+    int bn1, bn2, bn3, nchunkJK;
     uint16_t* Bd;  int* eB;     // [4][katK][X n][16], per row (P, mu)
-    uint16_t* Cd;  int* eC;     // [4][katK][ap][16], per orbital p
+    uint16_t *Cd1, *Cd2; int* eC;  // C digits per orbital p (rows p, K = nu) in GEMM1's / GEMM2's tiles
     float2* Tdf;                // [X n][ap] T^P_{mu p} as double-floats
+    unsigned* colT;             // [X][ap] max_mu |T^P_{mu p}| (float bits)
     uint16_t* Td2; int* e2;     // [4][katK][X ap][16], per (P, p)
-    unsigned* maxT3; int* eT3;  // per mu
-    uint16_t* Td3;              // [4][X ap / 16][n][16]
+    uint16_t* Td3; int* epT;    // [4][8 nkp][n][16] (K = (P, r) padded to nkp parts), scale per (part, mu)
     float2* bdf;                // [X ap][ap] b^P_{p q} as double-floats
-    float2* Wdf;                // [X][ap][ap]  W^P_rp at (P, p, r)
-    unsigned* maxW; int* eW3;   // per p
-    uint16_t* Wd3;              // [4][X ap / 16][ap][16]
-    long long* Lfix;            // [n][ap]
-    float2 *Adf, *Bcdf;         // [a][a]
-    double *Jpart, *Kpart;      // [X / 8 chunks][a a]
     float2* ddf;                // [X][a] diagonals d^P_p
+    float2* Ddf;                // [X][a] D^P_p = sum_r A_pr d^P_r
+    uint16_t* Wd3; int* epW;    // rows p (tiles of bn3), K = (P, r); scale per (part, p)
+    float2 *Adf, *Bcdf;         // [a][a]
+    double *Jpart, *Kpart;      // [nchunkJK][a a]
+    double* Lpart;              // [GEMM3 K chunks][n][a] partials of Lambda' (fixed-order sum)
     DigitGemmPlan g1, g2, g3;
 };
 
@@ -70,27 +74,24 @@ __device__ __forceinline__ uint16_t bf16_bits(int d) {
     __nv_bfloat16 b = __float2bfloat16_rn((float)d);
     return *reinterpret_cast<uint16_t*>(&b);
 }
-// Y = d0 256^3 + d1 256^2 + d2 256 + d3 with |d1..d3| <= 128 (|Y| <= 2^32); writes the four
-// planes of element (row r, k) of a digit tensor stored in digit_gemm.h's layout (tiles of RT rows).
-__device__ __forceinline__ void put_digits(uint16_t* planes, int RT, int katoms, long long r, long long k,
+// Y = sum_i d_i 256^{nd-1-i} with |d_1..d_{nd-1}| <= 128 (|Y| <= 2^{8 nd}); writes the nd planes
+// of element (row r, k) of a digit tensor stored in digit_gemm.h's layout (tiles of RT rows).
+__device__ __forceinline__ void put_digits(uint16_t* planes, int RT, int katoms, int nd, long long r, long long k,
                                            long long Y) {
-    int d3 = (int)(((Y + 128) & 255) - 128);
-    int Y1 = (int)((Y - d3) >> 8);  // |Y1| <= 2^24 + 1: 32-bit from here on
-    int d2 = ((Y1 + 128) & 255) - 128;
-    Y1 = (Y1 - d2) >> 8;
-    int d1 = ((Y1 + 128) & 255) - 128;
-    int d0 = (Y1 - d1) >> 8;
-    long long base = digit_offset(RT, katoms, r, k, 0);
-    long long ps = (long long)RT * 16;  // next plane of the same (tile, atom) block
-    planes[base] = bf16_bits(d0);
-    planes[base + ps] = bf16_bits(d1);
-    planes[base + 2 * ps] = bf16_bits(d2);
-    planes[base + 3 * ps] = bf16_bits(d3);
+    const long long base = digit_offset(RT, katoms, r, k, 0, nd);
+    const long long ps = (long long)RT * 16;  // next plane of the same (tile, atom) block
+    for (int i = nd - 1; i >= 1; --i) {
+        const int d = (int)(((Y + 128) & 255) - 128);
+        planes[base + i * ps] = bf16_bits(d);
+        Y = (Y - d) >> 8;
+    }
+    planes[base] = bf16_bits((int)Y);
 }
 // BF16 bit pattern of a small integer digit (|d| <= 256, exact: at most 8 significant bits)
 __device__ __forceinline__ uint32_t bf16_of_digit(int d) { return __float_as_uint((float)d) >> 16; }
 
-// round((v.x + v.y) 2^s) for |.| <= 2^32 as H 2^16 + L with 32-bit H, L (|L| <= 2^15 + 1)
+// round((v.x + v.y) 2^s) for |.| <= 2^40 as H 2^16 + L with 32-bit H (|H| <= 2^24), L
+// (|L| <= 2^16)
 __device__ __forceinline__ void df_to_HL(float2 v, int s, int& H, int& L) {
     const float xs = ldexpf(v.x, s), ys = ldexpf(v.y, s);
     const float h = rintf(xs * (1.0f / 65536.0f));
@@ -106,27 +107,40 @@ __device__ __forceinline__ void split_digits_HL(int H, int L, int& d0, int& d1, 
     d1 = ((Y + 128) & 255) - 128;
     d0 = (Y - d1) >> 8;
 }
-// Eight consecutive K elements (k0 % 8 == 0) of one row from double-floats scaled by 2^s.
-__device__ __forceinline__ void put8_df(uint16_t* planes, int RT, int katoms, long long r, long long k0,
+// digits of Y = H 2^16 + L (|Y| <= 2^40) with 64-bit shifts (5 digits)
+__device__ __forceinline__ void split_digits5_HL(int H, int L, int* d) {
+    long long Y = ((long long)H << 16) + L;
+#pragma unroll
+    for (int i = 4; i >= 1; --i) {
+        d[i] = (int)(((Y + 128) & 255) - 128);
+        Y = (Y - d[i]) >> 8;
+    }
+    d[0] = (int)Y;
+}
+// Eight consecutive K elements (k0 % 8 == 0) of one row from double-floats scaled by 2^s, as nd
+// (4 or 5) digits: one 16-byte store per plane.
+__device__ __forceinline__ void put8_df(uint16_t* planes, int RT, int katoms, int nd, long long r, long long k0,
                                         const float2* v, const int* s) {
-    uint32_t w[4][4];
+    uint32_t w[5][4];
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
-        int H, L, a0, a1, a2, a3, b0, b1, b2, b3;
+        int H, L, a[5], b[5];
         df_to_HL(v[j], s[j], H, L);
-        split_digits_HL(H, L, a0, a1, a2, a3);
+        if (nd == 4) split_digits_HL(H, L, a[0], a[1], a[2], a[3]);
+        else split_digits5_HL(H, L, a);
         df_to_HL(v[j + 1], s[j + 1], H, L);
-        split_digits_HL(H, L, b0, b1, b2, b3);
-        w[0][j / 2] = bf16_of_digit(a0) | (bf16_of_digit(b0) << 16);
-        w[1][j / 2] = bf16_of_digit(a1) | (bf16_of_digit(b1) << 16);
-        w[2][j / 2] = bf16_of_digit(a2) | (bf16_of_digit(b2) << 16);
-        w[3][j / 2] = bf16_of_digit(a3) | (bf16_of_digit(b3) << 16);
+        if (nd == 4) split_digits_HL(H, L, b[0], b[1], b[2], b[3]);
+        else split_digits5_HL(H, L, b);
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+            if (i < nd) w[i][j / 2] = bf16_of_digit(a[i]) | (bf16_of_digit(b[i]) << 16);
     }
-    const long long base = digit_offset(RT, katoms, r, k0, 0);
+    const long long base = digit_offset(RT, katoms, r, k0, 0, nd);
     const long long ps = (long long)RT * 16;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<uint4*>(planes + base + i * ps) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+    for (int i = 0; i < 5; ++i)
+        if (i < nd)
+            *reinterpret_cast<uint4*>(planes + base + i * ps) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
 }
 
 __device__ __forceinline__ int exp_of(float mx) {
@@ -135,10 +149,11 @@ __device__ __forceinline__ int exp_of(float mx) {
     return e;  // mx < 2^e
 }
 
+
 // Digits of an FP64 matrix, one row per warp, scale per row over `ncols` entries:
-// element (row, k) = src[row * s_row + k * s_col].
-__global__ void k_digits_f64(const double* src, long long s_row, long long s_col, int nrows, int ncols,
-                             int RT, int katoms, uint16_t* planes, int* exps) {
+// element (row, k) = src[row * s_row + k * s_col]; written in one or two tile layouts.
+__global__ void k_digits_f64(const double* src, long long s_row, long long s_col, int nrows, int ncols, int nd,
+                             int RT, int katoms, uint16_t* planes, int* exps, int RT2, uint16_t* planes2) {
     int w = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (w >= nrows) return;
     double mx = 0.0;
@@ -148,22 +163,23 @@ __global__ void k_digits_f64(const double* src, long long s_row, long long s_col
     if (mx > 0.0) frexp(mx, &e);
     if (lane == 0) exps[w] = e;
     for (int k = lane; k < ncols; k += 32) {
-        long long Y = __double2ll_rn(ldexp(src[w * s_row + k * s_col], 32 - e));
-        put_digits(planes, RT, katoms, w, k, Y);
+        long long Y = __double2ll_rn(ldexp(src[w * s_row + k * s_col], 8 * nd - e));
+        put_digits(planes, RT, katoms, nd, w, k, Y);
+        if (planes2) put_digits(planes2, RT2, katoms, nd, w, k, Y);
     }
 }
 
 // Reconstruct FP64 rows from digit planes (nof_get_B under the split precision).
-__global__ void k_undigit_rows(const uint16_t* planes, const int* exps, int RT, int katoms, long long rows,
+__global__ void k_undigit_rows(const uint16_t* planes, const int* exps, int RT, int katoms, int nd, long long rows,
                                int ncols, double* out) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= rows * ncols) return;
     long long r = idx / ncols;
     int k = (int)(idx % ncols);
-    long long base = digit_offset(RT, katoms, r, k, 0);
+    long long base = digit_offset(RT, katoms, r, k, 0, nd);
     long long ps = (long long)RT * 16;
     double v = 0.0;
-    for (int i = 3; i >= 0; --i) {
+    for (int i = nd - 1; i >= 0; --i) {
         uint16_t u = planes[base + i * ps];
         __nv_bfloat16 b = *reinterpret_cast<__nv_bfloat16*>(&u);
         v = (v + (double)__bfloat162float(b)) / 256.0;
@@ -171,80 +187,64 @@ __global__ void k_undigit_rows(const uint16_t* planes, const int* exps, int RT, 
     out[idx] = ldexp(v, exps[r]);
 }
 
-// Block per aux index P (blockDim = (32, 32)): per-(P,p) scale over mu and digits for GEMM2
-// (rows (P, p), K = mu), plus running per-mu maxima for GEMM3's operand. T^P is read twice; the
-// second read hits L2 (GEMM1 has just written it).
-__global__ void __launch_bounds__(1024) k_T2_digits(const float2* Tdf, int n, int ap, int katK, uint16_t* Td2,
-                                                    int* e2, unsigned* maxT3) {
-    __shared__ float colpart[32][129];  // [ty][p]
-    __shared__ int ecol[128];
-    const int P = blockIdx.x;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const float2* T = Tdf + (long long)P * n * ap;
-    float cm[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int mu = ty; mu < n; mu += 32) {  // pass 1: warp ty rows mu, lane tx columns p
-        float rm = 0.f;
-        for (int j = 0; j < 4; ++j) {
-            int p = tx + 32 * j;
-            if (p >= ap) break;
-            float f = fabsf(T[(long long)mu * ap + p].x);
-            cm[j] = fmaxf(cm[j], f);
-            rm = fmaxf(rm, f);
-        }
-        for (int o = 16; o; o >>= 1) rm = fmaxf(rm, __shfl_xor_sync(0xffffffffu, rm, o));
-        if (tx == 0) atomicMax(&maxT3[mu], __float_as_uint(rm));
-    }
-    for (int j = 0; j < 4; ++j)
-        if (tx + 32 * j < ap) colpart[ty][tx + 32 * j] = cm[j];
-    __syncthreads();
-    for (int p = ty * 32 + tx; p < ap; p += 1024) {
-        float m = 0.f;
-        for (int t = 0; t < 32; ++t) m = fmaxf(m, colpart[t][p]);
-        const int e = exp_of(m);
-        ecol[p] = e;
-        e2[(long long)P * ap + p] = e;
-    }
-    __syncthreads();
-    // pass 2: a thread takes 8 consecutive mu of one p (lanes over p: coalesced loads, one
-    // 16-byte store per plane)
+// GEMM2's A operand: rows (P, p), K = mu, scale per (P, p) from GEMM1's column maxima. A thread
+// takes 8 consecutive mu of one (P, p); lanes run along p (coalesced loads, one 16-byte store per
+// plane). The thread with mu block 0 also stores the exponent.
+__global__ void k_T2_digits(const float2* Tdf, const unsigned* colT, int X, int n, int ap, int katK, int nd,
+                            uint16_t* Td2, int* e2) {
     const int nb8 = (n + 7) / 8;
-    for (int t = ty * 32 + tx; t < nb8 * ap; t += 1024) {
-        const int mb = t / ap, p = t - mb * ap;
-        float2 v[8];
-        int sh[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int mu = mb * 8 + j;
-            v[j] = mu < n ? T[(long long)mu * ap + p] : make_float2(0.f, 0.f);
-            sh[j] = 32 - ecol[p];
-        }
-        put8_df(Td2, 128, katK, (long long)P * ap + p, (long long)mb * 8, v, sh);
-    }
-}
-
-// GEMM3's A operand: rows mu, K = (P, r); scale per mu over all (P, r). A thread takes 8
-// consecutive r of one row (P, mu).
-__global__ void k_T3_digits(const float2* Tdf, const unsigned* maxT3, int X, int n, int ap, uint16_t* Td3) {
-    const int g8 = ap / 8;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= X * n * g8) return;
-    const int row = t / g8, rg = t - row * g8;  // row = P n + mu
-    const int P = row / n, mu = row - P * n;
-    const int s = 32 - exp_of(__uint_as_float(maxT3[mu]));
-    const float2* src = Tdf + (long long)row * ap + rg * 8;
+    if (t >= X * nb8 * ap) return;
+    const int p = t % ap, rest = t / ap;
+    const int mb = rest % nb8, P = rest / nb8;
+    const int e = exp_of(__uint_as_float(colT[P * ap + p]));
+    if (mb == 0) e2[P * ap + p] = e;
+    const float2* T = Tdf + (long long)P * n * ap + p;
     float2 v[8];
     int sh[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        v[j] = src[j];
-        sh[j] = s;
+        const int mu = mb * 8 + j;
+        v[j] = mu < n ? T[(long long)mu * ap] : make_float2(0.f, 0.f);
+        sh[j] = 8 * nd - e;
     }
-    put8_df(Td3, 128, (int)((long long)X * ap / 16), mu, (long long)P * ap + rg * 8, v, sh);
+    put8_df(Td2, 128, katK, nd, (long long)P * ap + p, (long long)mb * 8, v, sh);
 }
 
-__global__ void k_exps_from_max(const unsigned* mx, int cnt, int* e) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < cnt) e[i] = exp_of(__uint_as_float(mx[i]));
+// GEMM3's A operand: rows mu, K = (P, r) padded to nkp parts of 128, a scale per (part, mu). A
+// thread takes 8 consecutive K of one row; the 16 threads of a part form one half-warp (maximum by
+// shuffles), so every thread of the grid takes part in the shuffles and only live ones store.
+__global__ void k_T3_digits(const float2* Tdf, int X, int n, int ap, int nkp, int nd, uint16_t* Td3, int* epT) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int kgs = nkp * 16;  // groups of 8 K elements per row
+    const bool live = t < (long long)n * kgs;
+    int mu = 0, kg = 0;
+    float2 v[8];
+    float m = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = make_float2(0.f, 0.f);
+    if (live) {
+        mu = (int)(t / kgs);
+        kg = (int)(t - (long long)mu * kgs);
+        const long long K = (long long)kg * 8;
+        if (K < (long long)X * ap) {
+            const int P = (int)(K / ap), r0 = (int)(K - (long long)P * ap);
+            const float2* src = Tdf + ((long long)P * n + mu) * ap + r0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                v[j] = src[j];
+                m = fmaxf(m, fabsf(v[j].x));
+            }
+        }
+    }
+    for (int o = 8; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (!live) return;
+    const int e = exp_of(m);
+    if ((threadIdx.x & 15) == 0) epT[(long long)(kg >> 4) * n + mu] = e;
+    int sh[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sh[j] = 8 * nd - e;
+    put8_df(Td3, 128, nkp * kPartAtoms, nd, mu, (long long)kg * 8, v, sh);
 }
 
 // b^P_pq as a double-float (GEMM2's scaled output)
@@ -260,16 +260,16 @@ __global__ void k_diag_df(const float2* bdf, int X, int a, int ap, float2* d) {
     d[i] = b_val(bdf, ap, P, p, p);
 }
 
-// Partial sums over a chunk of kJKChunk aux indices: J_pq += d_p d_q, K_pq += (b_pq)^2 (double-
-// float); grid (ceil(a*a/256), ceil(X/kJKChunk)); partials [chunk][a*a] as FP64.
-constexpr int kJKChunk = 8;
+// Partial sums over one chunk of aux indices: J_pq += d_p d_q, K_pq += (b_pq)^2 (double-float);
+// grid (ceil(a*a/256), nchunk); partials [chunk][a*a] as FP64.
 __global__ void __launch_bounds__(256) k_JK_partial(const float2* bdf, const float2* d, int X, int a, int ap,
-                                                    double* Jpart, double* Kpart) {
+                                                    int nchunk, double* Jpart, double* Kpart) {
     const int idx = blockIdx.x * 256 + threadIdx.x;
     const int aa = a * a;
     if (idx >= aa) return;
     const int p = idx / a, q = idx - p * a;
-    const int P0 = blockIdx.y * kJKChunk, P1 = min(X, P0 + kJKChunk);
+    const int len = (X + nchunk - 1) / nchunk;
+    const int P0 = blockIdx.y * len, P1 = min(X, P0 + len);
     float2 jacc = make_float2(0.f, 0.f), kacc = make_float2(0.f, 0.f);
     for (int P = P0; P < P1; ++P) {
         float2 b = b_val(bdf, ap, P, p, q);
@@ -298,71 +298,71 @@ __global__ void k_to_df(const double* src, int cnt, float2* dst) {
     dst[i] = make_float2(hi, (float)(v - (double)hi));
 }
 
-// Persistent blocks over P: D^P = A d^P, W^P_rp = delta_rp D^P_p - B_pr b^P_rp (double-float),
-// stored at (P, p, r); per-p maxima for the digit scale of GEMM3's B operand.
-__global__ void __launch_bounds__(256) k_perP_W(const float2* bdf, const float2* Adf, const float2* Bcdf, int X,
-                                                int a, int ap, float2* Wdf, unsigned* maxW) {
-    __shared__ float2 ds[128], Ds[128];
-    __shared__ unsigned wmax[128];
-    for (int p = threadIdx.x; p < ap; p += blockDim.x) wmax[p] = 0u;
-    const int aa = ap * ap;
-    for (int P = blockIdx.x; P < X; P += gridDim.x) {
-        __syncthreads();
-        for (int p = threadIdx.x; p < a; p += blockDim.x) ds[p] = b_val(bdf, ap, P, p, p);
-        __syncthreads();
-        for (int p = threadIdx.x; p < a; p += blockDim.x) {
-            float2 s = make_float2(0.f, 0.f);  // D^P_p = sum_r A_pr d_r
-            for (int r = 0; r < a; ++r) s = df_add(s, df_mul(Adf[p * a + r], ds[r]));
-            Ds[p] = s;
-        }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < aa; idx += blockDim.x) {
-            int p = idx / ap, r = idx - p * ap;  // stored at (P, p, r)
-            float2 w = make_float2(0.f, 0.f);
-            if (r < a && p < a) {
-                w = df_neg(df_mul(Bcdf[p * a + r], b_val(bdf, ap, P, r, p)));
-                if (r == p) w = df_add(w, Ds[p]);
-            }
-            Wdf[(long long)P * aa + idx] = w;
-            unsigned wb = __float_as_uint(fabsf(w.x));
-            if ((ap & 31) == 0) {  // the whole warp shares p
-                for (int o = 16; o; o >>= 1) wb = max(wb, __shfl_xor_sync(0xffffffffu, wb, o));
-                if ((threadIdx.x & 31) == 0) atomicMax(&wmax[p], wb);
-            } else {
-                atomicMax(&wmax[p], wb);
+// D^P_p = sum_r A_pr d^P_r for four aux indices P per thread (A is symmetric, so the lanes read
+// its rows r along p: coalesced).
+constexpr int kDP = 4;
+__global__ void k_D_df(const float2* Adf, const float2* d, int X, int a, float2* D) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pg = (X + kDP - 1) / kDP;
+    if (t >= pg * a) return;
+    const int p = t % a, P0 = (t / a) * kDP;
+    float2 s[kDP];
+#pragma unroll
+    for (int i = 0; i < kDP; ++i) s[i] = make_float2(0.f, 0.f);
+    for (int r = 0; r < a; ++r) {
+        const float2 A = Adf[(long long)r * a + p];
+#pragma unroll
+        for (int i = 0; i < kDP; ++i)
+            if (P0 + i < X) s[i] = df_add(s[i], df_mul(A, d[(long long)(P0 + i) * a + r]));
+    }
+#pragma unroll
+    for (int i = 0; i < kDP; ++i)
+        if (P0 + i < X) D[(long long)(P0 + i) * a + p] = s[i];
+}
+
+// W^P_rp = delta_rp D^P_p - B_pr b^P_rp for p, r < a (zero in the padding); b^P is symmetric, so
+// the element is read at (P, p, r) and W is laid out like it: rows p, K = (P, r).
+__device__ __forceinline__ float2 w_val(const float2* bdf, const float2* Bcdf, const float2* D, int a, int ap,
+                                        int P, int p, int r) {
+    if (p >= a || r >= a) return make_float2(0.f, 0.f);
+    float2 w = df_neg(df_mul(Bcdf[p * a + r], b_val(bdf, ap, P, p, r)));
+    if (r == p) w = df_add(w, D[(long long)P * a + p]);
+    return w;
+}
+
+// GEMM3's B operand: rows p < a (tiles of RT), K = (P, r) padded to nkp parts of 128, a scale per
+// (part, p); W is recomputed from b and D (no W array). Thread and half-warp layout as k_T3_digits.
+__global__ void k_W_digits(const float2* bdf, const float2* Bcdf, const float2* D, int X, int a, int ap, int nkp,
+                           int nd, int RT, uint16_t* Wd3, int* epW) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int kgs = nkp * 16;
+    const bool live = t < (long long)a * kgs;
+    int p = 0, kg = 0;
+    float2 v[8];
+    float m = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = make_float2(0.f, 0.f);
+    if (live) {
+        p = (int)(t / kgs);
+        kg = (int)(t - (long long)p * kgs);
+        const long long K = (long long)kg * 8;
+        if (K < (long long)X * ap) {
+            const int P = (int)(K / ap), r0 = (int)(K - (long long)P * ap);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                v[j] = w_val(bdf, Bcdf, D, a, ap, P, p, r0 + j);
+                m = fmaxf(m, fabsf(v[j].x));
             }
         }
     }
-    __syncthreads();
-    for (int p = threadIdx.x; p < ap; p += blockDim.x) atomicMax(&maxW[p], wmax[p]);
-}
-
-// GEMM3's B operand: rows p, K = (P, r); scale per p over all (P, r). A thread takes 8
-// consecutive r of one (P, p).
-__global__ void k_W_digits(const float2* Wdf, const int* eW3, int X, int ap, uint16_t* Wd3) {
-    const int g8 = ap / 8;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= X * ap * g8) return;
-    const int Pp = t / g8, rg = t - Pp * g8;  // Pp = P ap + p
-    const int P = Pp / ap, p = Pp - P * ap;
-    const int s = 32 - eW3[p];
-    const float2* src = Wdf + (long long)Pp * ap + rg * 8;
-    float2 v[8];
+    for (int o = 8; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (!live) return;
+    const int e = exp_of(m);
+    if ((threadIdx.x & 15) == 0) epW[(long long)(kg >> 4) * a + p] = e;
     int sh[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        v[j] = src[j];
-        sh[j] = s;
-    }
-    put8_df(Wd3, ap, (int)((long long)X * ap / 16), p, (long long)P * ap + rg * 8, v, sh);
-}
-
-__global__ void k_lambda_from_fix(const long long* Lfix, const int* eT3, const int* eW3, int n, int a, int ap,
-                                  double* Lam) {
-    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= (long long)n * a) return;
-    int mu = (int)(idx / a), p = (int)(idx - (long long)mu * a);
-    Lam[idx] = ldexp((double)Lfix[(long long)mu * ap + p], eT3[mu] + eW3[p] - 40);
+    for (int j = 0; j < 8; ++j) sh[j] = 8 * nd - e;
+    put8_df(Wd3, RT, nkp * kPartAtoms, nd, p, (long long)kg * 8, v, sh);
 }
 
 template <class T>
@@ -380,15 +380,42 @@ void ffree(T*& p) {
     p = nullptr;
 }
 
+// Tile widths worth trying for an N of `ap` columns with nd digits (a tile much wider than the
+// matrix only multiplies zeros).
+int bn_candidates(int ap, int nd, int* out) {
+    int k = 0;
+    for (int bn : kDigitBN)
+        if (digit_bn_ok(bn, nd) && (bn < 2 * ap || bn == 16)) out[k++] = bn;
+    return k;
+}
+
+// out[i] = sum_b part[b][i] in a fixed order: a block takes 32 consecutive outputs (coalesced) and
+// eight interleaved slices of the parts, then adds the slices in order.
+__global__ void __launch_bounds__(256) k_sum_parts(const double* part, int nparts, long long cnt, double* out) {
+    __shared__ double acc[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const long long i = blockIdx.x * 32LL + tx;
+    double s = 0.0;
+    if (i < cnt)
+        for (int b = ty; b < nparts; b += 8) s += part[(long long)b * cnt + i];
+    acc[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && i < cnt) {
+        double t = acc[0][tx];
+        for (int k = 1; k < 8; ++k) t += acc[k][tx];
+        out[i] = t;
+    }
+}
+
 }  // namespace
 
 int fast_release(nof_ctx* c) {
     FastState* f = c->fast;
     if (!f) return NOF_OK;
-    ffree(f->Bd); ffree(f->eB); ffree(f->Cd); ffree(f->eC); ffree(f->Tdf); ffree(f->Td2); ffree(f->e2);
-    ffree(f->maxT3); ffree(f->eT3); ffree(f->Td3); ffree(f->bdf); ffree(f->Wdf); ffree(f->maxW);
-    ffree(f->eW3); ffree(f->Wd3); ffree(f->Lfix); ffree(f->Adf); ffree(f->Bcdf); ffree(f->Jpart);
-    ffree(f->Kpart); ffree(f->ddf);
+    ffree(f->Bd); ffree(f->eB); ffree(f->Cd1); ffree(f->Cd2); ffree(f->eC); ffree(f->Tdf); ffree(f->colT);
+    ffree(f->Td2); ffree(f->e2); ffree(f->Td3); ffree(f->epT); ffree(f->bdf); ffree(f->ddf); ffree(f->Ddf);
+    ffree(f->Wd3); ffree(f->epW); ffree(f->Adf); ffree(f->Bcdf); ffree(f->Jpart); ffree(f->Lpart);
+    ffree(f->Kpart);
     delete f;
     c->fast = nullptr;
     return NOF_OK;
@@ -396,8 +423,11 @@ int fast_release(nof_ctx* c) {
 
 int fast_prepare(nof_ctx* c) {
     const int n = c->nbf, X = c->naux, a = c->nact;
-    if (n > 320 || a > 64) {
-        nof_set_error("NOF_PREC_SPLIT_BF16 supports nbf <= 320 and nact <= 64 in this build");
+    const int ap = (a + 15) / 16 * 16, katK = (n + 15) / 16;
+    // 32-bit row and K indices of every digit tensor and an exact int64 GEMM3 sum
+    if ((long long)X * n > (1LL << 30) || (long long)X * ap * n / 8 > (1LL << 30) ||
+        (long long)X * ap * ap / 8 > (1LL << 30)) {
+        nof_set_error("NOF_PREC_SPLIT_BF16: system too large for 32-bit tile indices");
         return NOF_EINVAL;
     }
     FastState* f = new (std::nothrow) FastState();
@@ -406,49 +436,120 @@ int fast_prepare(nof_ctx* c) {
         return NOF_ENOMEM;
     }
     c->fast = f;
-    f->n = n; f->X = X; f->a = a;
-    f->ap = (a + 15) / 16 * 16;
-    f->katK = (n + 15) / 16;
-    f->nblk = X < 304 ? X : 304;
-    const int ap = f->ap, katK = f->katK;
-    const long long rowsB = (long long)X * n, rows2 = (long long)X * ap, kat3 = (long long)X * ap / 16;
-    int k3 = 10;
-    while (kat3 % k3) --k3;
-    f->katoms3 = k3;
-    const long long nBd = digit_elems(128, rowsB, katK), nCd = digit_elems(ap, ap, katK),
-                    nTd2 = digit_elems(128, rows2, katK), nTd3 = digit_elems(128, n, (int)kat3),
-                    nWd3 = digit_elems(ap, ap, (int)kat3);
+    f->n = n; f->X = X; f->a = a; f->ap = ap; f->katK = katK;
+    // digits per element: 5 where the 4-digit truncation error, accumulated over the X a terms of
+    // the Lagrangian contraction, would approach the 1e-6 accuracy target (X a > 80000)
+    const int nd = c->opt.digits ? c->opt.digits : ((long long)X * a > 80000 ? 5 : 4);
+    f->nd = nd;
+    const long long rowsB = (long long)X * n, rows2 = (long long)X * ap;
+    const int nkp = (int)((rows2 / 16 + kPartAtoms - 1) / kPartAtoms);  // parts of GEMM3's K = (P, r)
+    const int kat3 = nkp * kPartAtoms;
+    f->nkp = nkp;
+    const long long nBd = digit_elems(128, rowsB, katK, nd), nCd = digit_elems(64, ap, katK, nd),
+                    nTd2 = digit_elems(128, rows2, katK, nd), nTd3 = digit_elems(128, n, kat3, nd),
+                    nWd3 = digit_elems(64, ap, kat3, nd);
+    {   // J/K chunks: enough blocks for a few waves, never more than one chunk per 8 aux indices
+        const int per = (int)nblk((long long)a * a);
+        int nc = (4 * 152 + per - 1) / per;
+        const int cap = (X + 7) / 8;
+        f->nchunkJK = nc < 1 ? 1 : (nc > cap ? cap : nc);
+    }
     NOF_TRY(falloc(&f->Bd, nBd)); NOF_TRY(falloc(&f->eB, rowsB));
-    NOF_TRY(falloc(&f->Cd, nCd)); NOF_TRY(falloc(&f->eC, ap));
+    NOF_TRY(falloc(&f->Cd1, nCd)); NOF_TRY(falloc(&f->Cd2, nCd)); NOF_TRY(falloc(&f->eC, ap));
     NOF_TRY(falloc(&f->Tdf, rowsB * ap));
+    NOF_TRY(falloc(&f->colT, rows2));
     NOF_TRY(falloc(&f->Td2, nTd2)); NOF_TRY(falloc(&f->e2, rows2));
-    NOF_TRY(falloc(&f->maxT3, n)); NOF_TRY(falloc(&f->eT3, n));
-    NOF_TRY(falloc(&f->Td3, nTd3));
+    NOF_TRY(falloc(&f->Td3, nTd3)); NOF_TRY(falloc(&f->epT, (size_t)nkp * n));
     NOF_TRY(falloc(&f->bdf, rows2 * ap));
-    NOF_TRY(falloc(&f->Wdf, rows2 * ap)); NOF_TRY(falloc(&f->maxW, ap)); NOF_TRY(falloc(&f->eW3, ap));
-    NOF_TRY(falloc(&f->Wd3, nWd3));
-    NOF_TRY(falloc(&f->Lfix, (size_t)n * ap));
+    NOF_TRY(falloc(&f->ddf, (size_t)X * a)); NOF_TRY(falloc(&f->Ddf, (size_t)X * a));
+    NOF_TRY(falloc(&f->Wd3, nWd3)); NOF_TRY(falloc(&f->epW, (size_t)nkp * a));
     NOF_TRY(falloc(&f->Adf, (size_t)a * a)); NOF_TRY(falloc(&f->Bcdf, (size_t)a * a));
-    const size_t nchunk = (size_t)(X + 7) / 8;
-    NOF_TRY(falloc(&f->Jpart, nchunk * a * a)); NOF_TRY(falloc(&f->Kpart, nchunk * a * a));
-    NOF_TRY(falloc(&f->ddf, (size_t)X * a));
+    NOF_TRY(falloc(&f->Jpart, (size_t)f->nchunkJK * a * a)); NOF_TRY(falloc(&f->Kpart, (size_t)f->nchunkJK * a * a));
     cudaStream_t st = c->stream;
     // digit planes start zeroed: padding rows (p >= nact) and padding K (k >= n) stay zero
     NOF_CUDA(cudaMemsetAsync(f->Bd, 0, 2ull * nBd, st));
-    NOF_CUDA(cudaMemsetAsync(f->Cd, 0, 2ull * nCd, st));
+    NOF_CUDA(cudaMemsetAsync(f->Cd1, 0, 2ull * nCd, st));
+    NOF_CUDA(cudaMemsetAsync(f->Cd2, 0, 2ull * nCd, st));
     NOF_CUDA(cudaMemsetAsync(f->Td2, 0, 2ull * nTd2, st));
     NOF_CUDA(cudaMemsetAsync(f->Td3, 0, 2ull * nTd3, st));
     NOF_CUDA(cudaMemsetAsync(f->Wd3, 0, 2ull * nWd3, st));
     NOF_CUDA(cudaMemsetAsync(f->eC, 0, sizeof(int) * ap, st));
     NOF_CUDA(cudaMemsetAsync(f->e2, 0, sizeof(int) * rows2, st));
+    NOF_CUDA(cudaMemsetAsync(f->epT, 0, sizeof(int) * nkp * n, st));
+    NOF_CUDA(cudaMemsetAsync(f->epW, 0, sizeof(int) * nkp * a, st));
     // B digits, one scale per row (P, mu)
-    k_digits_f64<<<nblk(rowsB * 32), 256, 0, st>>>(c->B, n, 1, (int)rowsB, n, 128, katK, f->Bd, f->eB);
+    k_digits_f64<<<nblk(rowsB * 32), 256, 0, st>>>(c->B, n, 1, (int)rowsB, n, nd, 128, katK, f->Bd, f->eB, 0,
+                                                   nullptr);
     NOF_LAUNCH_CHECK();
-    NOF_TRY(digit_gemm_plan_scaled(&f->g1, f->Bd, f->Cd, ap, katK, (int)rowsB, ap, f->Tdf, ap, f->eB, f->eC,
-                                   c->status));
-    NOF_TRY(digit_gemm_plan_scaled(&f->g2, f->Td2, f->Cd, ap, katK, (int)rows2, ap, f->bdf, ap, f->e2, f->eC,
-                                   c->status));
-    NOF_TRY(digit_gemm_plan(&f->g3, f->Td3, f->Wd3, ap, (int)kat3, k3, n, ap, f->Lfix, ap, true, c->status));
+
+    // ---- autotuned plans ----------------------------------------------------------------
+    int bns[3];
+    const int nbn = bn_candidates(ap, nd, bns);
+    DigitGemmPlan cand[16];
+    int best = 0;
+    {   // GEMM1: T = B C, scaled double-float output with the maxima of |T|
+        DigitGemmOut o;
+        o.outf = f->Tdf; o.ldo = ap; o.erow = f->eB; o.ecol = f->eC;
+        o.colmax = f->colT; o.group_rows = n;
+        for (int i = 0; i < nbn; ++i)
+            NOF_TRY(digit_gemm_plan(&cand[i], f->Bd, f->Cd1, (int)rowsB, ap, bns[i], nd, katK, katK, 0, o,
+                                    c->status));
+        NOF_TRY(digit_gemm_pick({1, (int)rowsB, ap, katK, n * 8 + nd}, cand, nbn, st, &best));
+        f->g1 = cand[best];
+        f->bn1 = bns[best];
+    }
+    {   // GEMM2: b = C^T T, scaled double-float output
+        DigitGemmOut o;
+        o.outf = f->bdf; o.ldo = ap; o.erow = f->e2; o.ecol = f->eC;
+        for (int i = 0; i < nbn; ++i)
+            NOF_TRY(digit_gemm_plan(&cand[i], f->Td2, f->Cd2, (int)rows2, ap, bns[i], nd, katK, katK, 0, o,
+                                    c->status));
+        NOF_TRY(digit_gemm_pick({2, (int)rows2, ap, katK, nd}, cand, nbn, st, &best));
+        f->g2 = cand[best];
+        f->bn2 = bns[best];
+    }
+    {   // GEMM3: Lambda' = sum_{P,r} T W with per-part scales; each K chunk stores its FP64 partial
+        // (summed afterwards in a fixed order, so results do not depend on scheduling)
+        const long long na = (long long)n * a;
+        const long long max_chunks = ((long long)1 << 31) / 8 / na;  // at most 2 GiB of partials
+        int k = 0, bnk[16], chk[16];
+        for (int i = 0; i < nbn; ++i) {
+            // per tile width, the three longest chunks (8 * 2^i atoms, or all of K) that still
+            // give one wave of tiles
+            const long long tmn = (long long)((n + 127) / 128) * ((a + bns[i] - 1) / bns[i]);
+            int all[24], na2 = 0;
+            for (long long ch = kPartAtoms; na2 < 24; ch *= 2) {
+                all[na2++] = (int)(ch < kat3 ? ch : kat3);
+                if (ch >= kat3) break;
+            }
+            int nch = 0;
+            for (int j = na2 - 1; j >= 0 && nch < 3; --j) {
+                const long long kch = (kat3 + all[j] - 1) / all[j];
+                if (kch > max_chunks) break;
+                if (tmn * kch < 152 && j > 0) continue;
+                chk[k] = all[j];
+                bnk[k++] = bns[i];
+                ++nch;
+            }
+        }
+        if (k == 0) {
+            nof_set_error("NOF_PREC_SPLIT_BF16: no Lagrangian contraction plan fits the partial buffer");
+            return NOF_EINVAL;
+        }
+        long long maxch = 0;
+        for (int i = 0; i < k; ++i) {
+            const long long kch = (kat3 + chk[i] - 1) / chk[i];
+            maxch = kch > maxch ? kch : maxch;
+        }
+        NOF_TRY(falloc(&f->Lpart, (size_t)(maxch * na)));
+        DigitGemmOut o;
+        o.outd = f->Lpart; o.ldo = a; o.chunk_stride = na; o.epA = f->epT; o.epB = f->epW;
+        for (int i = 0; i < k; ++i)
+            NOF_TRY(digit_gemm_plan(&cand[i], f->Td3, f->Wd3, n, a, bnk[i], nd, kat3, chk[i], 0, o, c->status));
+        NOF_TRY(digit_gemm_pick({3, n, a, kat3, nd}, cand, k, st, &best));
+        f->g3 = cand[best];
+        f->bn3 = bnk[best];
+    }
     NOF_CUDA(cudaStreamSynchronize(st));
     return NOF_OK;
 }
@@ -456,8 +557,17 @@ int fast_prepare(nof_ctx* c) {
 int fast_get_B(nof_ctx* c, double* B) {
     FastState* f = c->fast;
     long long rows = (long long)f->X * f->n;
-    k_undigit_rows<<<nblk(rows * f->n), 256, 0, c->stream>>>(f->Bd, f->eB, 128, f->katK, rows, f->n, B);
+    k_undigit_rows<<<nblk(rows * f->n), 256, 0, c->stream>>>(f->Bd, f->eB, 128, f->katK, f->nd, rows, f->n, B);
     NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+int fast_tiles(nof_ctx* c, int* out) {
+    FastState* f = c->fast;
+    out[0] = f->bn1;
+    out[1] = f->bn2;
+    out[2] = f->bn3;
+    out[3] = f->g3.g.katoms;
     return NOF_OK;
 }
 
@@ -465,20 +575,23 @@ int fast_jk(nof_ctx* c, const double* C) {
     FastState* f = c->fast;
     const int n = f->n, X = f->X, a = f->a, ap = f->ap;
     cudaStream_t st = c->stream;
-    // C digits: row p over nu (element C[nu][p])
-    k_digits_f64<<<nblk((long long)a * 32), 256, 0, st>>>(C, 1, n, a, n, ap, f->katK, f->Cd, f->eC);
+    // C digits: row p over nu (element C[nu][p]), in GEMM1's and GEMM2's tile widths
+    k_digits_f64<<<nblk((long long)a * 32), 256, 0, st>>>(C, 1, n, a, n, f->nd, f->bn1, f->katK, f->Cd1, f->eC,
+                                                          f->bn2, f->Cd2);
     NOF_LAUNCH_CHECK();
+    NOF_CUDA(cudaMemsetAsync(f->colT, 0, sizeof(unsigned) * X * ap, st));
     NOF_TRY(prof_begin(c, "k_digit_gemm (half transform T = B C, tcgen05)"));
     NOF_TRY(digit_gemm_run(f->g1, st));
     NOF_TRY(prof_end(c));
-    NOF_CUDA(cudaMemsetAsync(f->maxT3, 0, sizeof(unsigned) * n, st));
-    k_T2_digits<<<X, dim3(32, 32), 0, st>>>(f->Tdf, n, ap, f->katK, f->Td2, f->e2, f->maxT3);
+    const int nb8 = (n + 7) / 8;
+    k_T2_digits<<<nblk((long long)X * nb8 * ap), 256, 0, st>>>(f->Tdf, f->colT, X, n, ap, f->katK, f->nd, f->Td2,
+                                                               f->e2);
     NOF_LAUNCH_CHECK();
     NOF_TRY(digit_gemm_run(f->g2, st));
     k_diag_df<<<nblk((long long)X * a), 256, 0, st>>>(f->bdf, X, a, ap, f->ddf);
     NOF_LAUNCH_CHECK();
-    const int nchunk = (X + kJKChunk - 1) / kJKChunk;
-    k_JK_partial<<<dim3(nblk((long long)a * a), nchunk), 256, 0, st>>>(f->bdf, f->ddf, X, a, ap, f->Jpart,
+    const int nchunk = f->nchunkJK;
+    k_JK_partial<<<dim3(nblk((long long)a * a), nchunk), 256, 0, st>>>(f->bdf, f->ddf, X, a, ap, nchunk, f->Jpart,
                                                                       f->Kpart);
     NOF_LAUNCH_CHECK();
     k_reduce_parts<<<nblk((long long)a * a * 32), 256, 0, st>>>(f->Jpart, nchunk, a * a, c->J);
@@ -499,20 +612,17 @@ int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad) 
     NOF_LAUNCH_CHECK();
     k_to_df<<<nblk(a * a), 256, 0, st>>>(c->Bc, a * a, f->Bcdf);
     NOF_LAUNCH_CHECK();
-    NOF_CUDA(cudaMemsetAsync(f->maxW, 0, sizeof(unsigned) * ap, st));
-    k_perP_W<<<X, 256, 0, st>>>(f->bdf, f->Adf, f->Bcdf, X, a, ap, f->Wdf, f->maxW);
+    k_D_df<<<nblk((long long)((X + kDP - 1) / kDP) * a), 256, 0, st>>>(f->Adf, f->ddf, X, a, f->Ddf);
     NOF_LAUNCH_CHECK();
-    k_exps_from_max<<<1, 128, 0, st>>>(f->maxW, ap, f->eW3);
+    const long long nkg = (long long)f->nkp * 16;
+    k_W_digits<<<nblk((long long)a * nkg), 256, 0, st>>>(f->bdf, f->Bcdf, f->Ddf, X, a, ap, f->nkp, f->nd, f->bn3,
+                                                        f->Wd3, f->epW);
     NOF_LAUNCH_CHECK();
-    k_W_digits<<<nblk((long long)X * ap * (ap / 8)), 256, 0, st>>>(f->Wdf, f->eW3, X, ap, f->Wd3);
+    k_T3_digits<<<nblk((long long)n * nkg), 256, 0, st>>>(f->Tdf, X, n, ap, f->nkp, f->nd, f->Td3, f->epT);
     NOF_LAUNCH_CHECK();
-    k_exps_from_max<<<nblk(n, 128), 128, 0, st>>>(f->maxT3, n, f->eT3);
-    NOF_LAUNCH_CHECK();
-    k_T3_digits<<<nblk((long long)X * n * (ap / 8)), 256, 0, st>>>(f->Tdf, f->maxT3, X, n, ap, f->Td3);
-    NOF_LAUNCH_CHECK();
-    NOF_CUDA(cudaMemsetAsync(f->Lfix, 0, sizeof(long long) * n * ap, st));
     NOF_TRY(digit_gemm_run(f->g3, st));
-    k_lambda_from_fix<<<nblk((long long)n * a), 256, 0, st>>>(f->Lfix, f->eT3, f->eW3, n, a, ap, c->Lam);
+    const long long na = (long long)n * a;
+    k_sum_parts<<<(unsigned)((na + 31) / 32), 256, 0, st>>>(f->Lpart, f->g3.g.kchunks, na, c->Lam);
     NOF_LAUNCH_CHECK();
     NOF_TRY(pnof_lambda_and_g(c, C, c->gorb));
     return pnof_gamma_grad(c, c->ggam);

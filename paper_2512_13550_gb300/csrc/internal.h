@@ -134,3 +134,4 @@ int fast_release(nof_ctx* c);
 int fast_jk(nof_ctx* c, const double* C);
 int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad);
 int fast_get_B(nof_ctx* c, double* B);
+int fast_tiles(nof_ctx* c, int* out);

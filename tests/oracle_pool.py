@@ -1,0 +1,39 @@
+"""Process pool for the oracle's slice-by-slice orbital-basis route (test infrastructure).
+
+Workers are started with `spawn` (safe after CUDA is initialised in the parent) and run with
+single-threaded BLAS; each computes (P|q p) for one slice of aux functions."""
+from __future__ import annotations
+
+import multiprocessing as mp
+import os
+from concurrent.futures import ProcessPoolExecutor
+
+import numpy as np
+
+from oracle import integrals, large
+
+
+def _slice(args):
+    orb, aux, xyz, C, nact, lo, hi = args
+    return large.mo_three_center(orb, aux, xyz, C, nact, slice(lo, hi))
+
+
+def fitted_mo(orb, aux, xyz, C, nact, workers=None):
+    """b^P_{qp} [X][n][nact] of the oracle, (P|q p) computed in parallel slices."""
+    X = integrals.naux(aux, xyz)
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    step = max(1, -(-X // (4 * workers)))
+    jobs = [(orb, aux, xyz, C, nact, lo, min(X, lo + step)) for lo in range(0, X, step)]
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            Q3 = np.concatenate(list(ex.map(_slice, jobs)))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return large.fitted_mo(Q3, integrals.two_center(aux, xyz))

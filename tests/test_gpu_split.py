@@ -23,9 +23,9 @@ def _n(x):
     return x.detach().cpu().numpy()
 
 
-def _ctx(sysm, ipnof=7):
+def _ctx(sysm, ipnof=7, digits=0):
     import paper_2512_13550_gb300 as nof
-    ctx = nof.Context(precision=nof.PREC_SPLIT_BF16, ncwo=sysm.ncwo, ipnof=ipnof)
+    ctx = nof.Context(precision=nof.PREC_SPLIT_BF16, ncwo=sysm.ncwo, ipnof=ipnof, digits=digits)
     ctx.build_B(sysm.xyz, sysm.orb, sysm.aux)
     return ctx
 
@@ -37,6 +37,7 @@ CASES = {
     "H8_ncwo2": lambda: systems.chain3s(8, ncwo=2),  # two weak orbitals per pair
     "H50": lambda: systems.h50(),                  # the benchmark workload (n = 150, a = 50)
     "H64": lambda: systems.chain3s(64, seed=5),    # n = 192 > 160: two exact K accumulations
+    "H66": lambda: systems.chain3s(66, seed=6),    # a = 66: several N tiles, the last one ragged
 }
 
 
@@ -48,11 +49,13 @@ def test_digit_storage_reproduces_fitted_eri():
     assert np.max(np.abs(ri.fitted_eri(B) - ref)) < 1e-8 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("name", list(CASES))
-def test_split_jk_energy_gradients(name):
+@pytest.mark.parametrize("name,digits", [(k, 0) for k in CASES] + [("H10", 5), ("H22", 5), ("H66", 5),
+                                                                   ("H8_ncwo2", 5)])
+def test_split_jk_energy_gradients(name, digits):
+    """digits 0 = automatic (4 for all of these sizes); 5 forces five BF16 digits per element."""
     sysm = CASES[name]()
     o = sysm.oracle
-    ctx = _ctx(sysm)
+    ctx = _ctx(sysm, digits=digits)
     C, gam = sysm.orbitals(), sysm.gamma()
     Ct, gt = _t(C), _t(gam)
     J, K = ctx.jk(Ct)
@@ -96,10 +99,14 @@ def test_split_step_energy_matches_oracle_step():
     np.testing.assert_allclose(Cn.T @ S @ Cn, np.eye(n), atol=1e-10)
 
 
-def test_split_rejects_unsupported_sizes():
-    import paper_2512_13550_gb300 as nof
-    orb, aux = inputs.basis_3s_10aux()
-    ctx = nof.Context(precision=nof.PREC_SPLIT_BF16)
-    with pytest.raises(nof.NofError) as e:   # nact = 66 > 64
-        ctx.build_B(inputs.chain(66), orb, aux)
-    assert e.value.code == nof.NOF_EINVAL
+def test_split_chooses_tiles_per_shape():
+    """Different shapes get independent autotuned plans and still agree with the oracle."""
+    for name in ("H10", "H22"):
+        sysm = CASES[name]()
+        o = sysm.oracle
+        ctx = _ctx(sysm)
+        C, gam = sysm.orbitals(2), sysm.gamma(3)
+        E, g, gg = ctx.energy_grad(_t(C), _t(gam))
+        ref = pnof.energy_and_gradients(o["B"], o["H"], C, gam, o["pm"], o["vnn"])
+        assert abs(_n(E)[0] - ref["E"]) < GATE
+        assert np.max(np.abs(_n(g) - ref["g"])) < GATE
