@@ -16,11 +16,11 @@
 // (kPartAtoms atoms), the sum over parts of 2^{e_m,part + f_n,part - 8 (nd + 1)} V_part as FP64
 // (added atomically, or stored per K chunk for a fixed-order reduction).
 //
-// Storage: digit_gemm.h's tile-major core-matrix layout, so one pipeline stage (2 K atoms x 4
+// Storage: digit_gemm.h's tile-major swizzled layout, so one pipeline stage (2 K atoms x 4
 // planes) of a 128-row tile of A, or of a BN-row tile of B, is one contiguous block that a single
-// bulk copy (cp.async.bulk) places in shared memory in the no-swizzle K-major canonical layout
-// (core matrices of 8 rows x 16 bytes; 128 bytes between K-adjacent, 256 bytes between
-// row-adjacent core matrices).
+// bulk copy (cp.async.bulk) places in shared memory in the 32-byte-swizzled K-major canonical
+// layout (rows of 32 bytes, 16-byte halves swapped on rows with bit 2 set, 8-row groups 256
+// bytes apart).
 //
 // Every mbarrier wait is bounded; on timeout the kernel sets NOF_DEV_TIMEOUT in the status word,
 // lets what it issued land and exits.
@@ -87,16 +87,17 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
         "l"(src), "r"(bytes), "r"(mbar)
         : "memory");
 }
-// Shared-memory matrix descriptor: K-major, no swizzle; core matrices of 8 rows x 16 bytes,
-// 128 bytes between K-adjacent (leading byte offset) and 256 bytes between row-adjacent
-// (stride byte offset) core matrices.
+// Shared-memory matrix descriptor: K-major with 32-byte swizzling (layout type 6); rows of
+// 32 bytes (one K atom), 8-row groups 256 bytes apart (stride byte offset); the leading byte
+// offset is unused for swizzled K-major operands (1 by convention).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(128 >> 4) << 16;   // leading byte offset: next core matrix along K
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused)
     d |= (uint64_t)(256 >> 4) << 32;   // stride byte offset: next 8-row group
     d |= (uint64_t)1 << 46;            // descriptor version for tcgen05
-    return d;                          // swizzle mode 0 (none)
+    d |= (uint64_t)6 << 61;            // swizzle: 32 bytes
+    return d;
 }
 // Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int N) {
@@ -239,6 +240,7 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                     const uint32_t abytes = (uint32_t)atoms * ND * kBM * 32u;
                     const uint32_t bbytes = (uint32_t)atoms * ND * (uint32_t)BN * 32u;
                     mbar_expect_tx(full0 + 8 * s, abytes + bbytes);
+                    // each operand's stage block is one contiguous run of bytes
                     bulk_load(smem_u32(sA + s * a_stage_bytes),
                               A + digit_offset(kBM, g.katoms_total, (long long)tm * kBM, (long long)ka * 16, 0, ND),
                               abytes, full0 + 8 * s);
@@ -251,6 +253,11 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
             const uint32_t idesc = idesc_bf16(BN);
+            // descriptors of the ring's slot 0; a slot, atom or plane offset is added in 16-byte
+            // units straight to the 14-bit address field (shared addresses stay below 2^18)
+            const uint64_t adesc0 = sdesc(smem_u32(sA)), bdesc0 = sdesc(smem_u32(sB));
+            const uint32_t a_slot16 = a_stage_bytes >> 4, b_slot16 = b_stage_bytes >> 4;
+            const uint32_t b_plane16 = (uint32_t)BN * 2u;  // BN rows x 32 bytes
             int it = 0, unit = 0;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
                 const int kc = tile / (g.tiles_n * g.tiles_m);
@@ -261,28 +268,36 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                     if (use > 0) ok = mbar_wait(tempty0 + 8 * b, (use - 1) & 1, g.status);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t acc = tmem + (uint32_t)(b * ND * BN);
+                    uint32_t accl[ND];  // TMEM column of each level of this set
+#pragma unroll
+                    for (int l = 0; l < ND; ++l) accl[l] = tmem + (uint32_t)((b * ND + l) * BN);
                     const int pa = min(g.apart, tk - part * g.apart);
                     const int nst = (pa + kStageAtoms - 1) / kStageAtoms;
-                    uint32_t started = 0u;  // bit l: level l already initialised in this part
                     for (int st = 0; st < nst && ok; ++st, ++it) {
                         const int s = it % S;
                         ok = mbar_wait(full0 + 8 * s, (it / S) & 1, g.status);
                         if (!ok) break;
                         tc_fence_after();
                         const int atoms = min(kStageAtoms, pa - st * kStageAtoms);
-                        const uint32_t aBase = smem_u32(sA + s * a_stage_bytes), bBase = smem_u32(sB + s * b_stage_bytes);
-                        for (int t = 0; t < atoms; ++t) {
+                        const uint64_t ad = adesc0 + (uint64_t)(s * a_slot16);
+                        const uint64_t bd = bdesc0 + (uint64_t)(s * b_slot16);
+                        // the first product of each level in a part starts its accumulator
+                        const uint32_t acc0 = st > 0 ? 1u : 0u;
 #pragma unroll
-                            for (int i = 0; i < ND; ++i) {
+                        for (int t = 0; t < kStageAtoms; ++t) {
+                            if (t < atoms) {
+                                // stage block order [atom][plane][rows x 16]: plane offsets 256 (A)
+                                // and b_plane16 (B) units
+                                const uint64_t adt = ad + (uint64_t)(t * ND * 256);
+                                const uint64_t bdt = bd + (uint64_t)(t * ND) * b_plane16;
 #pragma unroll
-                                for (int j = 0; j < ND - i; ++j) {
-                                    const int l = i + j;
-                                    // stage block order [atom][plane][rows x 16]
-                                    uint64_t ad = sdesc(aBase + (uint32_t)((t * ND + i) * kBM * 32));
-                                    uint64_t bd = sdesc(bBase + (uint32_t)((t * ND + j) * BN * 32));
-                                    mma_bf16(acc + (uint32_t)(l * BN), ad, bd, idesc, (started >> l) & 1u);
-                                    started |= 1u << l;
+                                for (int i = 0; i < ND; ++i) {
+#pragma unroll
+                                    for (int j = 0; j < ND - i; ++j) {
+                                        const uint32_t accf = (t > 0 || i > 0) ? 1u : acc0;
+                                        mma_bf16(accl[i + j], adt + (uint64_t)(i * 256), bdt + (uint64_t)j * b_plane16,
+                                                 idesc, accf);
+                                    }
                                 }
                             }
                         }
@@ -400,8 +415,7 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                             *dst = x0;
                         }
                     }
-                    // column maxima per group: most candidates are below the running maximum,
-                    // so read before the atomic (a stale read only costs an extra atomic)
+                    // column maxima per group (atomics without a return value: nothing waits on them)
                     if (g.colmax && lane < ncol && rbase < g.M) {  // lane = column: runs of rows of a group
                         int grp = rbase / g.group_rows;
                         int next = (grp + 1) * g.group_rows;  // first row of the next group
@@ -409,16 +423,14 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                         float m = 0.f;
                         for (int rr = 0; rr < rend; ++rr) {
                             if (rbase + rr == next) {
-                                unsigned* dst = g.colmax + (long long)grp * g.Nvalid + col0 + lane;
-                                if (__float_as_uint(m) > __ldcg(dst)) atomicMax(dst, __float_as_uint(m));
+                                atomicMax(g.colmax + (long long)grp * g.Nvalid + col0 + lane, __float_as_uint(m));
                                 m = 0.f;
                                 ++grp;
                                 next += g.group_rows;
                             }
                             m = fmaxf(m, fabsf(st[rr * SP + lane].x));
                         }
-                        unsigned* dst = g.colmax + (long long)grp * g.Nvalid + col0 + lane;
-                        if (__float_as_uint(m) > __ldcg(dst)) atomicMax(dst, __float_as_uint(m));
+                        atomicMax(g.colmax + (long long)grp * g.Nvalid + col0 + lane, __float_as_uint(m));
                     }
                 }
             }

@@ -49,12 +49,14 @@ struct DigitGemmArgs {
     int kchunks;       // K chunks (split-K); tile order: N tile fastest, then row block, then chunk
 };
 
-// Digit-plane storage ("tile-major core-matrix" layout). An operand with R rows is cut into tiles
-// of RT rows (RT = 128 for the M side, RT = BN for the N side; R padded to a multiple of RT with
-// zero rows) and K atoms of 16. Tile rt, atom t, plane i (of nd) is one contiguous block of
-// RT x 16 BF16 in the order the tensor core reads without swizzling: 8-row x 8-element core
-// matrices (128 bytes) ordered [row group r/8][k half kk/8][row r%8][element kk%8]. The two atoms
-// and nd planes of one pipeline stage are therefore one contiguous RT * 64 nd-byte block.
+// Digit-plane storage ("tile-major, 32-byte swizzled" layout). An operand with R rows is cut
+// into tiles of RT rows (RT = 128 for the M side, RT = BN for the N side; R padded to a multiple
+// of RT with zero rows) and K atoms of 16. Tile rt, atom t, plane i (of nd) is one contiguous
+// block of RT x 16 BF16 in the K-major layout the tensor core reads with 32-byte swizzling: row r
+// at r * 32 bytes, its two 16-byte halves swapped when bit 2 of r is set (bit 4 of the byte
+// address XOR bit 7). Four rows then fill all 32 banks, so the MMA reads its operands without
+// bank conflicts. The two atoms and nd planes of one pipeline stage are one contiguous
+// RT * 64 nd-byte block, copied to shared memory as is.
 __host__ __device__ __forceinline__ long long digit_offset(int RT, int katoms, long long row, long long k,
                                                            int plane, int nd) {
     // 32-bit index arithmetic (rows and K stay below 2^31; 64-bit division is emulated)
@@ -74,7 +76,7 @@ __host__ __device__ __forceinline__ long long digit_offset(int RT, int katoms, l
     }
     const unsigned t = uk >> 4, kk = uk & 15u;
     const long long block = (((long long)tile * katoms + t) * nd + plane) * (long long)(RT * 16);
-    return block + (long long)(((r >> 3) * 2 + (kk >> 3)) * 64 + (r & 7) * 8 + (kk & 7));
+    return block + (long long)(r * 16 + ((((kk >> 3) ^ (r >> 2)) & 1u) << 3) + (kk & 7));
 }
 // elements of a digit tensor with R rows (padded to RT), katoms atoms and nd planes
 __host__ __device__ __forceinline__ long long digit_elems(int RT, long long R, int katoms, int nd) {

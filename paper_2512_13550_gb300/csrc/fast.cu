@@ -188,63 +188,68 @@ __global__ void k_undigit_rows(const uint16_t* planes, const int* exps, int RT, 
 }
 
 // GEMM2's A operand: rows (P, p), K = mu, scale per (P, p) from GEMM1's column maxima. A thread
-// takes 8 consecutive mu of one (P, p); lanes run along p (coalesced loads, one 16-byte store per
-// plane). The thread with mu block 0 also stores the exponent.
+// takes 8 consecutive mu (one half of a K atom) of one (P, p); the two halves of a row are
+// neighbouring threads and lanes run along p, so a warp reads runs of 16 columns of T and writes
+// 16 whole swizzled rows (512 bytes) per plane. The thread with mu block 0 stores the exponent.
 __global__ void k_T2_digits(const float2* Tdf, const unsigned* colT, int X, int n, int ap, int katK, int nd,
                             uint16_t* Td2, int* e2) {
-    const int nb8 = (n + 7) / 8;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= X * nb8 * ap) return;
-    const int p = t % ap, rest = t / ap;
-    const int mb = rest % nb8, P = rest / nb8;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)X * katK * ap * 2) return;
+    const int half = (int)(t & 1);
+    const long long u = t >> 1;
+    const int p = (int)(u % ap);
+    const long long w = u / ap;
+    const int atom = (int)(w % katK), P = (int)(w / katK);
     const int e = exp_of(__uint_as_float(colT[P * ap + p]));
-    if (mb == 0) e2[P * ap + p] = e;
+    if (atom == 0 && half == 0) e2[P * ap + p] = e;
+    const int mu0 = atom * 16 + half * 8;
     const float2* T = Tdf + (long long)P * n * ap + p;
     float2 v[8];
     int sh[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const int mu = mb * 8 + j;
+        const int mu = mu0 + j;
         v[j] = mu < n ? T[(long long)mu * ap] : make_float2(0.f, 0.f);
         sh[j] = 8 * nd - e;
     }
-    put8_df(Td2, 128, katK, nd, (long long)P * ap + p, (long long)mb * 8, v, sh);
+    put8_df(Td2, 128, katK, nd, (long long)P * ap + p, (long long)mu0, v, sh);
 }
 
 // GEMM3's A operand: rows mu, K = (P, r) padded to nkp parts of 128, a scale per (part, mu). A
-// thread takes 8 consecutive K of one row; the 16 threads of a part form one half-warp (maximum by
-// shuffles), so every thread of the grid takes part in the shuffles and only live ones store.
-__global__ void k_T3_digits(const float2* Tdf, int X, int n, int ap, int nkp, int nd, uint16_t* Td3, int* epT) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int kgs = nkp * 16;  // groups of 8 K elements per row
-    const bool live = t < (long long)n * kgs;
-    int mu = 0, kg = 0;
+// block of 128 threads takes 8 rows (mu0..mu0+7) and one part: thread (g, i), i = row, g = group of
+// 8 K elements. The 16 threads of a row combine their maxima in shared memory; the 16 threads of
+// one K atom write its 8 rows as one contiguous 256-byte swizzled block per plane.
+__global__ void __launch_bounds__(128) k_T3_digits(const float2* Tdf, int X, int n, int ap, int nkp, int nd,
+                                                   uint16_t* Td3, int* epT) {
+    __shared__ float mx[16][9];
+    const int part = blockIdx.x, i = threadIdx.x & 7, g = threadIdx.x >> 3;
+    const int mu = blockIdx.y * 8 + i;
+    const long long K = (long long)part * 128 + g * 8;
     float2 v[8];
     float m = 0.f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = make_float2(0.f, 0.f);
-    if (live) {
-        mu = (int)(t / kgs);
-        kg = (int)(t - (long long)mu * kgs);
-        const long long K = (long long)kg * 8;
-        if (K < (long long)X * ap) {
-            const int P = (int)(K / ap), r0 = (int)(K - (long long)P * ap);
-            const float2* src = Tdf + ((long long)P * n + mu) * ap + r0;
+    if (mu < n && K < (long long)X * ap) {
+        const int P = (int)(K / ap), r0 = (int)(K - (long long)P * ap);
+        const float2* src = Tdf + ((long long)P * n + mu) * ap + r0;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                v[j] = src[j];
-                m = fmaxf(m, fabsf(v[j].x));
-            }
+        for (int j = 0; j < 8; ++j) {
+            v[j] = src[j];
+            m = fmaxf(m, fabsf(v[j].x));
         }
     }
-    for (int o = 8; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (!live) return;
-    const int e = exp_of(m);
-    if ((threadIdx.x & 15) == 0) epT[(long long)(kg >> 4) * n + mu] = e;
+    mx[g][i] = m;
+    __syncthreads();
+    float mr = 0.f;
+#pragma unroll
+    for (int gg = 0; gg < 16; ++gg) mr = fmaxf(mr, mx[gg][i]);
+    if (mu >= n) return;
+    const int e = exp_of(mr);
+    if (g == 0) epT[(long long)part * n + mu] = e;
     int sh[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) sh[j] = 8 * nd - e;
-    put8_df(Td3, 128, nkp * kPartAtoms, nd, mu, (long long)kg * 8, v, sh);
+    put8_df(Td3, 128, nkp * kPartAtoms, nd, mu, K, v, sh);
 }
 
 // b^P_pq as a double-float (GEMM2's scaled output)
@@ -298,26 +303,44 @@ __global__ void k_to_df(const double* src, int cnt, float2* dst) {
     dst[i] = make_float2(hi, (float)(v - (double)hi));
 }
 
-// D^P_p = sum_r A_pr d^P_r for four aux indices P per thread (A is symmetric, so the lanes read
-// its rows r along p: coalesced).
-constexpr int kDP = 4;
-__global__ void k_D_df(const float2* Adf, const float2* d, int X, int a, float2* D) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int pg = (X + kDP - 1) / kDP;
-    if (t >= pg * a) return;
-    const int p = t % a, P0 = (t / a) * kDP;
-    float2 s[kDP];
+// D^P_p = sum_r d^P_r A_rp (A symmetric): a double-float GEMM D [X][a] = d [X][a] A [a][a] in
+// 32 x 32 output tiles, 2 x 2 outputs per thread, K = r staged through shared memory 16 at a time.
+__global__ void __launch_bounds__(256) k_D_df(const float2* Adf, const float2* d, int X, int a, float2* D) {
+    __shared__ float2 ds[32][17];  // [P][r]
+    __shared__ float2 as[16][33];  // [r][p]
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int P0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
+    float2 acc[2][2];
 #pragma unroll
-    for (int i = 0; i < kDP; ++i) s[i] = make_float2(0.f, 0.f);
-    for (int r = 0; r < a; ++r) {
-        const float2 A = Adf[(long long)r * a + p];
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int i = 0; i < kDP; ++i)
-            if (P0 + i < X) s[i] = df_add(s[i], df_mul(A, d[(long long)(P0 + i) * a + r]));
+        for (int j = 0; j < 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int r0 = 0; r0 < a; r0 += 16) {
+        for (int e = threadIdx.x; e < 32 * 16; e += 256) {
+            const int i = e >> 4, k = e & 15;  // d tile: row P0 + i, column r0 + k
+            ds[i][k] = (P0 + i < X && r0 + k < a) ? d[(long long)(P0 + i) * a + r0 + k] : make_float2(0.f, 0.f);
+            const int kk = e >> 5, j = e & 31;  // A tile: row r0 + kk, column p0 + j
+            as[kk][j] = (r0 + kk < a && p0 + j < a) ? Adf[(long long)(r0 + kk) * a + p0 + j] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float2 d0 = ds[ty][k], d1 = ds[ty + 16][k];
+            const float2 a0 = as[k][tx], a1 = as[k][tx + 16];
+            acc[0][0] = df_add(acc[0][0], df_mul(d0, a0));
+            acc[0][1] = df_add(acc[0][1], df_mul(d0, a1));
+            acc[1][0] = df_add(acc[1][0], df_mul(d1, a0));
+            acc[1][1] = df_add(acc[1][1], df_mul(d1, a1));
+        }
+        __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < kDP; ++i)
-        if (P0 + i < X) D[(long long)(P0 + i) * a + p] = s[i];
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int P = P0 + ty + 16 * i, q = p0 + tx + 16 * j;
+            if (P < X && q < a) D[(long long)P * a + q] = acc[i][j];
+        }
 }
 
 // W^P_rp = delta_rp D^P_p - B_pr b^P_rp for p, r < a (zero in the padding); b^P is symmetric, so
@@ -331,38 +354,37 @@ __device__ __forceinline__ float2 w_val(const float2* bdf, const float2* Bcdf, c
 }
 
 // GEMM3's B operand: rows p < a (tiles of RT), K = (P, r) padded to nkp parts of 128, a scale per
-// (part, p); W is recomputed from b and D (no W array). Thread and half-warp layout as k_T3_digits.
-__global__ void k_W_digits(const float2* bdf, const float2* Bcdf, const float2* D, int X, int a, int ap, int nkp,
-                           int nd, int RT, uint16_t* Wd3, int* epW) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int kgs = nkp * 16;
-    const bool live = t < (long long)a * kgs;
-    int p = 0, kg = 0;
+// (part, p); W is recomputed from b and D (no W array). Block and thread layout as k_T3_digits.
+__global__ void __launch_bounds__(128) k_W_digits(const float2* bdf, const float2* Bcdf, const float2* D, int X,
+                                                  int a, int ap, int nkp, int nd, int RT, uint16_t* Wd3, int* epW) {
+    __shared__ float mx[16][9];
+    const int part = blockIdx.x, i = threadIdx.x & 7, g = threadIdx.x >> 3;
+    const int p = blockIdx.y * 8 + i;
+    const long long K = (long long)part * 128 + g * 8;
     float2 v[8];
     float m = 0.f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = make_float2(0.f, 0.f);
-    if (live) {
-        p = (int)(t / kgs);
-        kg = (int)(t - (long long)p * kgs);
-        const long long K = (long long)kg * 8;
-        if (K < (long long)X * ap) {
-            const int P = (int)(K / ap), r0 = (int)(K - (long long)P * ap);
+    if (p < a && K < (long long)X * ap) {
+        const int P = (int)(K / ap), r0 = (int)(K - (long long)P * ap);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                v[j] = w_val(bdf, Bcdf, D, a, ap, P, p, r0 + j);
-                m = fmaxf(m, fabsf(v[j].x));
-            }
+        for (int j = 0; j < 8; ++j) {
+            v[j] = w_val(bdf, Bcdf, D, a, ap, P, p, r0 + j);
+            m = fmaxf(m, fabsf(v[j].x));
         }
     }
-    for (int o = 8; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (!live) return;
-    const int e = exp_of(m);
-    if ((threadIdx.x & 15) == 0) epW[(long long)(kg >> 4) * a + p] = e;
+    mx[g][i] = m;
+    __syncthreads();
+    float mr = 0.f;
+#pragma unroll
+    for (int gg = 0; gg < 16; ++gg) mr = fmaxf(mr, mx[gg][i]);
+    if (p >= a) return;
+    const int e = exp_of(mr);
+    if (g == 0) epW[(long long)part * a + p] = e;
     int sh[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) sh[j] = 8 * nd - e;
-    put8_df(Wd3, RT, nkp * kPartAtoms, nd, p, (long long)kg * 8, v, sh);
+    put8_df(Wd3, RT, nkp * kPartAtoms, nd, p, K, v, sh);
 }
 
 template <class T>
@@ -583,9 +605,8 @@ int fast_jk(nof_ctx* c, const double* C) {
     NOF_TRY(prof_begin(c, "k_digit_gemm (half transform T = B C, tcgen05)"));
     NOF_TRY(digit_gemm_run(f->g1, st));
     NOF_TRY(prof_end(c));
-    const int nb8 = (n + 7) / 8;
-    k_T2_digits<<<nblk((long long)X * nb8 * ap), 256, 0, st>>>(f->Tdf, f->colT, X, n, ap, f->katK, f->nd, f->Td2,
-                                                               f->e2);
+    k_T2_digits<<<nblk((long long)X * f->katK * ap * 2), 256, 0, st>>>(f->Tdf, f->colT, X, n, ap, f->katK, f->nd,
+                                                                       f->Td2, f->e2);
     NOF_LAUNCH_CHECK();
     NOF_TRY(digit_gemm_run(f->g2, st));
     k_diag_df<<<nblk((long long)X * a), 256, 0, st>>>(f->bdf, X, a, ap, f->ddf);
@@ -612,13 +633,12 @@ int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad) 
     NOF_LAUNCH_CHECK();
     k_to_df<<<nblk(a * a), 256, 0, st>>>(c->Bc, a * a, f->Bcdf);
     NOF_LAUNCH_CHECK();
-    k_D_df<<<nblk((long long)((X + kDP - 1) / kDP) * a), 256, 0, st>>>(f->Adf, f->ddf, X, a, f->Ddf);
+    k_D_df<<<dim3((a + 31) / 32, (X + 31) / 32), 256, 0, st>>>(f->Adf, f->ddf, X, a, f->Ddf);
     NOF_LAUNCH_CHECK();
-    const long long nkg = (long long)f->nkp * 16;
-    k_W_digits<<<nblk((long long)a * nkg), 256, 0, st>>>(f->bdf, f->Bcdf, f->Ddf, X, a, ap, f->nkp, f->nd, f->bn3,
-                                                        f->Wd3, f->epW);
+    k_W_digits<<<dim3(f->nkp, (a + 7) / 8), 128, 0, st>>>(f->bdf, f->Bcdf, f->Ddf, X, a, ap, f->nkp, f->nd, f->bn3,
+                                                          f->Wd3, f->epW);
     NOF_LAUNCH_CHECK();
-    k_T3_digits<<<nblk((long long)n * nkg), 256, 0, st>>>(f->Tdf, X, n, ap, f->nkp, f->nd, f->Td3, f->epT);
+    k_T3_digits<<<dim3(f->nkp, (n + 7) / 8), 128, 0, st>>>(f->Tdf, X, n, ap, f->nkp, f->nd, f->Td3, f->epT);
     NOF_LAUNCH_CHECK();
     NOF_TRY(digit_gemm_run(f->g3, st));
     const long long na = (long long)n * a;
