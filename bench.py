@@ -49,8 +49,8 @@ def parse():
                     help="h50: the single-geometry benchmark; h200: the 10 x 20 lattice (nbf 600, "
                          "naux 2000, nact 200); batch: many uneven H-chain frames evaluated "
                          "concurrently as one CUDA-graph launch")
-    ap.add_argument("--batch-count", type=int, default=64)
-    ap.add_argument("--batch-max", type=int, default=32, help="largest chain length in the batch")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-max", type=int, default=64, help="largest chain length in the batch")
     ap.add_argument("--no-graph", action="store_true",
                     help="time plain API calls instead of CUDA-graph replays of one evaluation")
     ap.add_argument("--profile-evals", type=int, default=0,
@@ -472,7 +472,7 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
 # DRAM bytes (read + write) of one GEMM1 launch on the H50 workload from an ncu capture of the
 # current kernel (profiles/), or None when the kernel has changed since the counters were taken.
-TRAFFIC_GEMM1_BYTES = None
+TRAFFIC_GEMM1_BYTES = 96610816 + 3343616  # profiles/digit_gemm_h50_ncu.md
 
 
 def roofline(prec, s, ms_per_launch, name, traffic=None):

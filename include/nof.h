@@ -196,6 +196,15 @@ int nof_profile_read(nof_ctx* ctx, double* ms, int* launches, const char** name)
 int nof_selftest_digit_gemm(int M, int N, int bn, int nd, int katoms, int chunk_atoms, unsigned int seed,
                             long long* max_abs_diff);
 
+/* Device time of one launch of the digit GEMM on zero operands (no paper counterpart;
+ * measurement only): M x N output, N tiles of bn, nd digits, K = 16 katoms in chunks of
+ * chunk_atoms. mode 0: exact int64 output (split-K atomics when chunk_atoms < katoms);
+ * 1: scaled double-float output (one chunk); 2: per-part scales with an FP64 partial per K chunk
+ * (chunk_atoms a multiple of 8). One warm-up, then the mean of `reps` launches timed with CUDA
+ * events on the default stream into *us_per_launch (host). Allocates and frees its own buffers. */
+int nof_bench_digit_gemm(int M, int N, int bn, int nd, int katoms, int chunk_atoms, int mode, int reps,
+                         double* us_per_launch);
+
 /* J and K exactly as nof_jk computes them in FP64, without a context and without allocating
  * any device memory (the paper has no counterpart; this is a deployment variant).
  * Some callers cannot call cudaMalloc: an application whose device memory is owned by another

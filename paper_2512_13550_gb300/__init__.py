@@ -73,6 +73,7 @@ SIGNATURES = {
     "nof_profile_read": (ctypes.c_int, [_P, _P, _P, _P]),
     "nof_selftest_digit_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_uint, _P]),
+    "nof_bench_digit_gemm": (ctypes.c_int, [ctypes.c_int] * 8 + [_P]),
     "nof_jk_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]),
     "nof_mlp_param_count": (ctypes.c_longlong, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "nof_mlp_work_size": (ctypes.c_longlong, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -114,6 +115,15 @@ def selftest_digit_gemm(M: int, N: int, bn: int, katoms: int, chunk_atoms: int =
     chunk = chunk_atoms if chunk_atoms > 0 else katoms
     _check(load_library().nof_selftest_digit_gemm(M, N, bn, nd, katoms, chunk, seed, ctypes.byref(out)))
     return out.value
+
+
+def bench_digit_gemm(M: int, N: int, bn: int, nd: int, katoms: int, chunk_atoms: int = 0, mode: int = 0,
+                     reps: int = 10) -> float:
+    """Microseconds per launch of the digit GEMM on zero operands (see nof_bench_digit_gemm)."""
+    us = ctypes.c_double(-1.0)
+    chunk = chunk_atoms if chunk_atoms > 0 else katoms
+    _check(load_library().nof_bench_digit_gemm(M, N, bn, nd, katoms, chunk, mode, reps, ctypes.byref(us)))
+    return us.value
 
 
 def energy_grad_batch(contexts, Cs, gammas, Es, gs=None, ggs=None, stream=None):

@@ -373,7 +373,7 @@ int nof_build_B(nof_ctx* c, int natom, const double* xyz, const double* Z, int c
     NOF_TRY(dalloc(&c->lam, nn)); NOF_TRY(dalloc(&c->gorb, nn));
     NOF_TRY(dalloc(&c->hpp, a)); NOF_TRY(dalloc(&c->s, a)); NOF_TRY(dalloc(&c->t, a)); NOF_TRY(dalloc(&c->occ, a));
     NOF_TRY(dalloc(&c->ds, (size_t)a * ncwo)); NOF_TRY(dalloc(&c->dt, (size_t)a * ncwo));
-    NOF_TRY(dalloc(&c->E, 1)); NOF_TRY(dalloc(&c->part, 3 * (size_t)a)); NOF_TRY(dalloc(&c->ggam, c->ngamma));
+    NOF_TRY(dalloc(&c->E, 1)); NOF_TRY(dalloc(&c->part, 4 * (size_t)a)); NOF_TRY(dalloc(&c->ggam, c->ngamma));
     NOF_TRY(dalloc(&c->y, nn)); NOF_TRY(dalloc(&c->U, nn)); NOF_TRY(dalloc(&c->U2, nn)); NOF_TRY(dalloc(&c->tmpn, nn));
     {   // split-K scratch for the small FP64 GEMMs (n x n, n x a, a x a, X x a outputs)
         size_t big = nn > (size_t)X * a ? nn : (size_t)X * a;

@@ -727,3 +727,81 @@ extern "C" int nof_selftest_digit_gemm(int M, int N, int bn, int nd, int katoms,
     cudaFree(A); cudaFree(B); cudaFree(C1); cudaFree(C2); cudaFree(dmax); cudaFree(status);
     return r;
 }
+
+// ---------------------------------------------------------------------------------------
+// Timing of one GEMM shape and output mode on zero operands (measurement only; the tensor
+// cores and copies do the same work whatever the digits are).
+// ---------------------------------------------------------------------------------------
+extern "C" int nof_bench_digit_gemm(int M, int N, int bn, int nd, int katoms, int chunk_atoms, int mode, int reps,
+                                    double* us_per_launch) {
+    if (!us_per_launch || M <= 0 || N <= 0 || (nd != 4 && nd != 5) || !digit_bn_ok(bn, nd) || katoms <= 0 ||
+        chunk_atoms <= 0 || mode < 0 || mode > 2 || reps <= 0 ||
+        (mode == 2 && chunk_atoms % kPartAtoms) || (mode != 0 && mode != 2 && chunk_atoms < katoms)) {
+        nof_set_error("nof_bench_digit_gemm: bad arguments");
+        return NOF_EINVAL;
+    }
+    const long long na = digit_elems(128, M, katoms, nd), nb = digit_elems(bn, N, katoms, nd);
+    const long long nkp = (katoms + kPartAtoms - 1) / kPartAtoms, kch = (katoms + chunk_atoms - 1) / chunk_atoms;
+    const long long nout = (long long)M * N * (mode == 2 ? kch : 1);
+    uint16_t *A = nullptr, *B = nullptr;
+    void* out = nullptr;
+    int *erow = nullptr, *ecol = nullptr, *status = nullptr;
+    int r = NOF_OK;
+    auto fail = [&](cudaError_t e, const char* w) { r = nof_cuda_fail(e, w, __FILE__, __LINE__); };
+    cudaError_t e;
+    if ((e = cudaMalloc(&A, 2ull * na)) != cudaSuccess) fail(e, "malloc A");
+    if (r == NOF_OK && (e = cudaMalloc(&B, 2ull * nb)) != cudaSuccess) fail(e, "malloc B");
+    if (r == NOF_OK && (e = cudaMalloc(&out, 8ull * nout)) != cudaSuccess) fail(e, "malloc out");
+    if (r == NOF_OK && (e = cudaMalloc(&erow, 4ull * (M > N ? M : N) * nkp)) != cudaSuccess) fail(e, "malloc exps");
+    if (r == NOF_OK && (e = cudaMalloc(&ecol, 4ull * (M > N ? M : N) * nkp)) != cudaSuccess) fail(e, "malloc exps");
+    if (r == NOF_OK && (e = cudaMalloc(&status, 4)) != cudaSuccess) fail(e, "malloc status");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (r == NOF_OK) {
+        cudaMemset(A, 0, 2ull * na);
+        cudaMemset(B, 0, 2ull * nb);
+        cudaMemset(erow, 0, 4ull * (M > N ? M : N) * nkp);
+        cudaMemset(ecol, 0, 4ull * (M > N ? M : N) * nkp);
+        cudaMemset(status, 0, 4);
+        DigitGemmOut o;
+        o.ldo = N;
+        if (mode == 0) {  // exact int64, split-K atomics when chunked
+            o.out = (long long*)out;
+            o.atomic = chunk_atoms < katoms;
+        } else if (mode == 1) {  // scaled double-float
+            o.outf = (float2*)out;
+            o.erow = erow;
+            o.ecol = ecol;
+        } else {  // per-part scales, FP64 partial per K chunk
+            o.outd = (double*)out;
+            o.chunk_stride = (long long)M * N;
+            o.epA = erow;
+            o.epB = ecol;
+        }
+        DigitGemmPlan p;
+        r = digit_gemm_plan(&p, A, B, M, N, bn, nd, katoms, chunk_atoms, 0, o, status);
+        if (r == NOF_OK) r = digit_gemm_run(p, 0);  // warm-up
+        if (r == NOF_OK) {
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, 0);
+            for (int i = 0; i < reps && r == NOF_OK; ++i) r = digit_gemm_run(p, 0);
+            cudaEventRecord(e1, 0);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) fail(e, "event sync");
+        }
+        if (r == NOF_OK) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            *us_per_launch = 1000.0 * ms / reps;
+            int hs = 0;
+            if ((e = cudaMemcpy(&hs, status, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) fail(e, "copy status");
+            else if (hs & NOF_DEV_TIMEOUT) {
+                nof_set_error("digit GEMM benchmark: a bounded wait timed out");
+                r = NOF_ETIMEOUT;
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(A); cudaFree(B); cudaFree(out); cudaFree(erow); cudaFree(ecol); cudaFree(status);
+    return r;
+}

@@ -33,7 +33,6 @@ struct FastState {
     uint16_t* Td2; int* e2;     // [4][katK][X ap][16], per (P, p)
     uint16_t* Td3; int* epT;    // [4][8 nkp][n][16] (K = (P, r) padded to nkp parts), scale per (part, mu)
     float2* bdf;                // [X ap][ap] b^P_{p q} as double-floats
-    float2* ddf;                // [X][a] diagonals d^P_p
     float2* Ddf;                // [X][a] D^P_p = sum_r A_pr d^P_r
     uint16_t* Wd3; int* epW;    // rows p (tiles of bn3), K = (P, r); scale per (part, p)
     float2 *Adf, *Bcdf;         // [a][a]
@@ -257,18 +256,10 @@ __device__ __forceinline__ float2 b_val(const float2* bdf, int ap, int P, int p,
     return bdf[((long long)P * ap + p) * ap + q];
 }
 
-// d^P_p = b^P_pp as double-floats
-__global__ void k_diag_df(const float2* bdf, int X, int a, int ap, float2* d) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= X * a) return;
-    int P = i / a, p = i - P * a;
-    d[i] = b_val(bdf, ap, P, p, p);
-}
-
-// Partial sums over one chunk of aux indices: J_pq += d_p d_q, K_pq += (b_pq)^2 (double-float);
-// grid (ceil(a*a/256), nchunk); partials [chunk][a*a] as FP64.
-__global__ void __launch_bounds__(256) k_JK_partial(const float2* bdf, const float2* d, int X, int a, int ap,
-                                                    int nchunk, double* Jpart, double* Kpart) {
+// Partial sums over one chunk of aux indices: J_pq += d_p d_q, K_pq += (b_pq)^2 (double-float),
+// with d^P_p = b^P_pp read from b; grid (ceil(a*a/256), nchunk); partials [chunk][a*a] as FP64.
+__global__ void __launch_bounds__(256) k_JK_partial(const float2* bdf, int X, int a, int ap, int nchunk,
+                                                    double* Jpart, double* Kpart) {
     const int idx = blockIdx.x * 256 + threadIdx.x;
     const int aa = a * a;
     if (idx >= aa) return;
@@ -279,33 +270,30 @@ __global__ void __launch_bounds__(256) k_JK_partial(const float2* bdf, const flo
     for (int P = P0; P < P1; ++P) {
         float2 b = b_val(bdf, ap, P, p, q);
         kacc = df_add(kacc, df_mul(b, b));
-        jacc = df_add(jacc, df_mul(d[P * a + p], d[P * a + q]));
+        jacc = df_add(jacc, df_mul(b_val(bdf, ap, P, p, p), b_val(bdf, ap, P, q, q)));
     }
     Jpart[(long long)blockIdx.y * aa + idx] = df_to_double(jacc);
     Kpart[(long long)blockIdx.y * aa + idx] = df_to_double(kacc);
 }
 
-// out[i] = sum_b part[b][i], one warp per output, fixed order (lane-strided then a fixed tree)
-__global__ void k_reduce_parts(const double* part, int nparts, int cnt, double* out) {
+// out[i] = sum_b part[b][i], one warp per output, fixed order (lane-strided then a fixed tree);
+// blockIdx.y selects one of two (part, out) pairs.
+__global__ void k_reduce_parts(const double* part0, double* out0, const double* part1, double* out1, int nparts,
+                               int cnt) {
     int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (i >= cnt) return;
+    const double* part = blockIdx.y ? part1 : part0;
+    double* out = blockIdx.y ? out1 : out0;
     double s = 0.0;
     for (int b = lane; b < nparts; b += 32) s += part[(long long)b * cnt + i];
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[i] = s;
 }
 
-__global__ void k_to_df(const double* src, int cnt, float2* dst) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= cnt) return;
-    double v = src[i];
-    float hi = (float)v;
-    dst[i] = make_float2(hi, (float)(v - (double)hi));
-}
-
-// D^P_p = sum_r d^P_r A_rp (A symmetric): a double-float GEMM D [X][a] = d [X][a] A [a][a] in
+// D^P_p = sum_r d^P_r A_rp (A symmetric, d^P_r = b^P_rr): a double-float GEMM D [X][a] = d A in
 // 32 x 32 output tiles, 2 x 2 outputs per thread, K = r staged through shared memory 16 at a time.
-__global__ void __launch_bounds__(256) k_D_df(const float2* Adf, const float2* d, int X, int a, float2* D) {
+__global__ void __launch_bounds__(256) k_D_df(const float2* Adf, const float2* bdf, int X, int a, int ap,
+                                              float2* D) {
     __shared__ float2 ds[32][17];  // [P][r]
     __shared__ float2 as[16][33];  // [r][p]
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -318,7 +306,7 @@ __global__ void __launch_bounds__(256) k_D_df(const float2* Adf, const float2* d
     for (int r0 = 0; r0 < a; r0 += 16) {
         for (int e = threadIdx.x; e < 32 * 16; e += 256) {
             const int i = e >> 4, k = e & 15;  // d tile: row P0 + i, column r0 + k
-            ds[i][k] = (P0 + i < X && r0 + k < a) ? d[(long long)(P0 + i) * a + r0 + k] : make_float2(0.f, 0.f);
+            ds[i][k] = (P0 + i < X && r0 + k < a) ? b_val(bdf, ap, P0 + i, r0 + k, r0 + k) : make_float2(0.f, 0.f);
             const int kk = e >> 5, j = e & 31;  // A tile: row r0 + kk, column p0 + j
             as[kk][j] = (r0 + kk < a && p0 + j < a) ? Adf[(long long)(r0 + kk) * a + p0 + j] : make_float2(0.f, 0.f);
         }
@@ -411,9 +399,12 @@ int bn_candidates(int ap, int nd, int* out) {
     return k;
 }
 
-// out[i] = sum_b part[b][i] in a fixed order: a block takes 32 consecutive outputs (coalesced) and
-// eight interleaved slices of the parts, then adds the slices in order.
-__global__ void __launch_bounds__(256) k_sum_parts(const double* part, int nparts, long long cnt, double* out) {
+// Lambda[mu][p] = n_p (HC)[mu][p] + sum_b part[b][mu][p] (the K-chunk partials of GEMM3) in a
+// fixed order: a block takes 32 consecutive outputs (coalesced) and eight interleaved slices of the
+// parts, then adds the slices in order.
+__global__ void __launch_bounds__(256) k_lambda_from_parts(const double* part, int nparts, long long cnt,
+                                                           const double* HC, const double* occ, int a,
+                                                           double* out) {
     __shared__ double acc[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const long long i = blockIdx.x * 32LL + tx;
@@ -425,7 +416,7 @@ __global__ void __launch_bounds__(256) k_sum_parts(const double* part, int npart
     if (ty == 0 && i < cnt) {
         double t = acc[0][tx];
         for (int k = 1; k < 8; ++k) t += acc[k][tx];
-        out[i] = t;
+        out[i] = t + occ[i % a] * HC[i];
     }
 }
 
@@ -435,7 +426,7 @@ int fast_release(nof_ctx* c) {
     FastState* f = c->fast;
     if (!f) return NOF_OK;
     ffree(f->Bd); ffree(f->eB); ffree(f->Cd1); ffree(f->Cd2); ffree(f->eC); ffree(f->Tdf); ffree(f->colT);
-    ffree(f->Td2); ffree(f->e2); ffree(f->Td3); ffree(f->epT); ffree(f->bdf); ffree(f->ddf); ffree(f->Ddf);
+    ffree(f->Td2); ffree(f->e2); ffree(f->Td3); ffree(f->epT); ffree(f->bdf); ffree(f->Ddf);
     ffree(f->Wd3); ffree(f->epW); ffree(f->Adf); ffree(f->Bcdf); ffree(f->Jpart); ffree(f->Lpart);
     ffree(f->Kpart);
     delete f;
@@ -483,7 +474,7 @@ int fast_prepare(nof_ctx* c) {
     NOF_TRY(falloc(&f->Td2, nTd2)); NOF_TRY(falloc(&f->e2, rows2));
     NOF_TRY(falloc(&f->Td3, nTd3)); NOF_TRY(falloc(&f->epT, (size_t)nkp * n));
     NOF_TRY(falloc(&f->bdf, rows2 * ap));
-    NOF_TRY(falloc(&f->ddf, (size_t)X * a)); NOF_TRY(falloc(&f->Ddf, (size_t)X * a));
+    NOF_TRY(falloc(&f->Ddf, (size_t)X * a));
     NOF_TRY(falloc(&f->Wd3, nWd3)); NOF_TRY(falloc(&f->epW, (size_t)nkp * a));
     NOF_TRY(falloc(&f->Adf, (size_t)a * a)); NOF_TRY(falloc(&f->Bcdf, (size_t)a * a));
     NOF_TRY(falloc(&f->Jpart, (size_t)f->nchunkJK * a * a)); NOF_TRY(falloc(&f->Kpart, (size_t)f->nchunkJK * a * a));
@@ -534,10 +525,10 @@ int fast_prepare(nof_ctx* c) {
         // (summed afterwards in a fixed order, so results do not depend on scheduling)
         const long long na = (long long)n * a;
         const long long max_chunks = ((long long)1 << 31) / 8 / na;  // at most 2 GiB of partials
-        int k = 0, bnk[16], chk[16];
+        int k = 0, bnk[16], chk[16];  // at most 3 widths x 4 chunks
         for (int i = 0; i < nbn; ++i) {
-            // per tile width, the three longest chunks (8 * 2^i atoms, or all of K) that still
-            // give one wave of tiles
+            // per tile width, the four longest chunks (8 * 2^i atoms, or all of K) that still give
+            // half a wave of tiles (longer chunks mean fewer partials and less per-tile overhead)
             const long long tmn = (long long)((n + 127) / 128) * ((a + bns[i] - 1) / bns[i]);
             int all[24], na2 = 0;
             for (long long ch = kPartAtoms; na2 < 24; ch *= 2) {
@@ -545,10 +536,10 @@ int fast_prepare(nof_ctx* c) {
                 if (ch >= kat3) break;
             }
             int nch = 0;
-            for (int j = na2 - 1; j >= 0 && nch < 3; --j) {
+            for (int j = na2 - 1; j >= 0 && nch < 4; --j) {
                 const long long kch = (kat3 + all[j] - 1) / all[j];
                 if (kch > max_chunks) break;
-                if (tmn * kch < 152 && j > 0) continue;
+                if (tmn * kch < 76 && j > 0) continue;
                 chk[k] = all[j];
                 bnk[k++] = bns[i];
                 ++nch;
@@ -584,6 +575,11 @@ int fast_get_B(nof_ctx* c, double* B) {
     return NOF_OK;
 }
 
+void fast_coefficient_buffers(nof_ctx* c, float2** Adf, float2** Bcdf) {
+    *Adf = c->fast ? c->fast->Adf : nullptr;
+    *Bcdf = c->fast ? c->fast->Bcdf : nullptr;
+}
+
 int fast_tiles(nof_ctx* c, int* out) {
     FastState* f = c->fast;
     out[0] = f->bn1;
@@ -609,15 +605,11 @@ int fast_jk(nof_ctx* c, const double* C) {
                                                                        f->Td2, f->e2);
     NOF_LAUNCH_CHECK();
     NOF_TRY(digit_gemm_run(f->g2, st));
-    k_diag_df<<<nblk((long long)X * a), 256, 0, st>>>(f->bdf, X, a, ap, f->ddf);
-    NOF_LAUNCH_CHECK();
     const int nchunk = f->nchunkJK;
-    k_JK_partial<<<dim3(nblk((long long)a * a), nchunk), 256, 0, st>>>(f->bdf, f->ddf, X, a, ap, nchunk, f->Jpart,
-                                                                      f->Kpart);
+    k_JK_partial<<<dim3(nblk((long long)a * a), nchunk), 256, 0, st>>>(f->bdf, X, a, ap, nchunk, f->Jpart, f->Kpart);
     NOF_LAUNCH_CHECK();
-    k_reduce_parts<<<nblk((long long)a * a * 32), 256, 0, st>>>(f->Jpart, nchunk, a * a, c->J);
-    NOF_LAUNCH_CHECK();
-    k_reduce_parts<<<nblk((long long)a * a * 32), 256, 0, st>>>(f->Kpart, nchunk, a * a, c->K);
+    k_reduce_parts<<<dim3(nblk((long long)a * a * 32), 2), 256, 0, st>>>(f->Jpart, c->J, f->Kpart, c->K, nchunk,
+                                                                        a * a);
     NOF_LAUNCH_CHECK();
     return pnof_hpp(c, C);
 }
@@ -626,14 +618,10 @@ int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad) 
     FastState* f = c->fast;
     const int n = f->n, X = f->X, a = f->a, ap = f->ap;
     cudaStream_t st = c->stream;
-    NOF_TRY(pnof_occupations(c, gamma));
-    NOF_TRY(pnof_energy(c));
+    NOF_TRY(pnof_occupations(c, gamma));  // also A and B as double-floats
+    NOF_TRY(pnof_energy(c));              // E and dE/dgamma
     if (!want_grad) return NOF_OK;
-    k_to_df<<<nblk(a * a), 256, 0, st>>>(c->A, a * a, f->Adf);
-    NOF_LAUNCH_CHECK();
-    k_to_df<<<nblk(a * a), 256, 0, st>>>(c->Bc, a * a, f->Bcdf);
-    NOF_LAUNCH_CHECK();
-    k_D_df<<<dim3((a + 31) / 32, (X + 31) / 32), 256, 0, st>>>(f->Adf, f->ddf, X, a, f->Ddf);
+    k_D_df<<<dim3((a + 31) / 32, (X + 31) / 32), 256, 0, st>>>(f->Adf, f->bdf, X, a, ap, f->Ddf);
     NOF_LAUNCH_CHECK();
     k_W_digits<<<dim3(f->nkp, (a + 7) / 8), 128, 0, st>>>(f->bdf, f->Bcdf, f->Ddf, X, a, ap, f->nkp, f->nd, f->bn3,
                                                           f->Wd3, f->epW);
@@ -642,8 +630,8 @@ int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad) 
     NOF_LAUNCH_CHECK();
     NOF_TRY(digit_gemm_run(f->g3, st));
     const long long na = (long long)n * a;
-    k_sum_parts<<<(unsigned)((na + 31) / 32), 256, 0, st>>>(f->Lpart, f->g3.g.kchunks, na, c->Lam);
+    k_lambda_from_parts<<<(unsigned)((na + 31) / 32), 256, 0, st>>>(f->Lpart, f->g3.g.kchunks, na, c->HC, c->occ, a,
+                                                                   c->Lam);
     NOF_LAUNCH_CHECK();
-    NOF_TRY(pnof_lambda_and_g(c, C, c->gorb));
-    return pnof_gamma_grad(c, c->ggam);
+    return pnof_lambda_and_g(c, C, c->gorb, true);
 }

@@ -122,7 +122,7 @@ int pnof_occupations(nof_ctx* c, const double* gamma);
 int pnof_energy(nof_ctx* c);
 int pnof_gamma_grad(nof_ctx* c, double* out);
 int pnof_hpp(nof_ctx* c, const double* C);
-int pnof_lambda_and_g(nof_ctx* c, const double* C, double* g_out);
+int pnof_lambda_and_g(nof_ctx* c, const double* C, double* g_out, bool assembled);
 int pnof_jk_from_b(nof_ctx* c);
 int pnof_build_W(nof_ctx* c);
 int pnof_on_update(nof_ctx* c, double* gamma);
@@ -135,3 +135,5 @@ int fast_jk(nof_ctx* c, const double* C);
 int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad);
 int fast_get_B(nof_ctx* c, double* B);
 int fast_tiles(nof_ctx* c, int* out);
+// split path: double-float copies of A and B for k_coefficients (null outside the split path)
+void fast_coefficient_buffers(nof_ctx* c, float2** Adf, float2** Bcdf);

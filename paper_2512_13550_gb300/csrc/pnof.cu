@@ -78,8 +78,11 @@ __global__ void k_occupations(const double* gamma, int npair, int ncwo, double* 
     }
 }
 
+// A and B of Eq. PNOF for every active pair (p, q); optionally also as double-floats (hi, lo) for
+// the split path (Adf, Bcdf may be null).
 __global__ void k_coefficients(const double* s, const double* t, const int* pair, const int* slot,
-                               int a, int ipnof, double* occ, double* A, double* Bc) {
+                               int a, int ipnof, double* occ, double* A, double* Bc, float2* Adf,
+                               float2* Bcdf) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= (long long)a * a) return;
     int p = (int)(idx / a), q = (int)(idx % a);
@@ -101,6 +104,11 @@ __global__ void k_coefficients(const double* s, const double* t, const int* pair
     }
     A[idx] = av;
     Bc[idx] = bv;
+    if (Adf) {
+        const float ah = (float)av, bh = (float)bv;
+        Adf[idx] = make_float2(ah, (float)(av - (double)ah));
+        Bcdf[idx] = make_float2(bh, (float)(bv - (double)bh));
+    }
 }
 
 // hpp_p = sum_mu C_mu,p (H C)_mu,p, one warp per p
@@ -111,22 +119,6 @@ __global__ void k_hpp(const double* C, const double* HC, int n, int a, double* h
     for (int mu = lane; mu < n; mu += 32) s = fma(C[(long long)mu * n + p], HC[(long long)mu * a + p], s);
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) hpp[p] = s;
-}
-
-// Single-block energy reduction in a fixed order.
-__global__ void k_energy(const double* occ, const double* hpp, const double* A, const double* Bc,
-                         const double* J, const double* K, const double* vnn, int a, double* E) {
-    __shared__ double red[1024];
-    double s = 0.0;
-    for (int p = threadIdx.x; p < a; p += blockDim.x) s += 2.0 * occ[p] * hpp[p];
-    for (long long i = threadIdx.x; i < (long long)a * a; i += blockDim.x) s += A[i] * J[i] - Bc[i] * K[i];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *E = red[0] + *vnn;
 }
 
 // d^P_p = b^P_pp
@@ -173,28 +165,29 @@ __global__ void k_lambda_assemble(const double* HC, const double* occ, int n, in
     Lam[idx] += occ[p] * HC[idx];
 }
 
-__global__ void k_orbital_gradient(const double* lam, int n, double* g) {
+// g = 4 (lambda - lambda^T); lambda holds columns p < a (the others are zero and never stored).
+__global__ void k_orbital_gradient(const double* lam, int n, int a, double* g) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= (long long)n * n) return;
     int p = (int)(idx / n), q = (int)(idx % n);
-    g[idx] = 4.0 * (lam[idx] - lam[(long long)q * n + p]);
+    const double lpq = q < a ? lam[idx] : 0.0, lqp = p < a ? lam[(long long)q * n + p] : 0.0;
+    g[idx] = 4.0 * (lpq - lqp);
 }
 
-__global__ void k_zero(double* x, long long n) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) x[i] = 0.0;
-}
-
-// Partial derivatives of E with respect to n_p, c_p and Phi_p (one warp per active orbital p).
+// Partial derivatives of E with respect to n_p, c_p and Phi_p, and the energy row
+// E_p = 2 n_p h_pp + sum_q (A_pq J_pq - B_pq K_pq), one warp per active orbital p
+// (out [4][a]: dE/dn, dE/dc, dE/dPhi, E_p).
 __global__ void k_dE_parts(const double* s, const double* t, const int* pair, const int* slot,
-                           const double* hpp, const double* J, const double* K, int a, int ipnof,
-                           double* out /* [3][a] */) {
+                           const double* hpp, const double* J, const double* K, const double* A,
+                           const double* Bc, int a, int ipnof, double* out) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= a) return;
     int p = warp;
-    double sn = 0.0, sc = 0.0, sf = 0.0;
+    double sn = 0.0, sc = 0.0, sf = 0.0, se = 0.0;
     for (int q = lane; q < a; q += 32) {
-        double Jpq = J[(long long)p * a + q], Kpq = K[(long long)p * a + q];
+        const long long pq = (long long)p * a + q;
+        double Jpq = J[pq], Kpq = K[pq];
+        se += A[pq] * Jpq - Bc[pq] * Kpq;
         if (pair[q] != pair[p]) {
             double nq = s[q] * s[q];
             sn += nq * (2.0 * Jpq - Kpq);
@@ -208,18 +201,27 @@ __global__ void k_dE_parts(const double* s, const double* t, const int* pair, co
         sn += __shfl_xor_sync(0xffffffffu, sn, o);
         sc += __shfl_xor_sync(0xffffffffu, sc, o);
         sf += __shfl_xor_sync(0xffffffffu, sf, o);
+        se += __shfl_xor_sync(0xffffffffu, se, o);
     }
     if (lane == 0) {
         out[p] = 2.0 * hpp[p] + J[(long long)p * a + p] + 2.0 * sn;
         out[a + p] = 2.0 * sc;
         out[2 * a + p] = (ipnof == 7) ? -2.0 * sf : 0.0;
+        out[3 * a + p] = 2.0 * s[p] * s[p] * hpp[p] + se;
     }
 }
 
-// dE/dgamma for gamma index k = i * npair + g: sum over the orbitals of subspace g.
+// dE/dgamma for gamma index k = i * npair + g: sum over the orbitals of subspace g. Warp 0 of
+// block 0 also forms E = V_nn + sum_p E_p in a fixed order.
 __global__ void k_gamma_chain(const double* s, const double* t, const double* ds, const double* dt,
                               const int* slot, const double* parts, int npair, int ncwo, int a,
-                              double* out) {
+                              const double* vnn, double* E, double* out) {
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        double e = 0.0;
+        for (int p = threadIdx.x; p < a; p += 32) e += parts[3 * a + p];
+        for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (threadIdx.x == 0) *E = e + *vnn;
+    }
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= npair * ncwo) return;
     int i = k / npair, g = k % npair;
@@ -253,14 +255,15 @@ __global__ void k_adam(const double* g, double* m, double* v, double* y, long lo
 }
 
 // out[0] = E, out[1] = ||g||_F, out[2] = max |lambda - lambda^T|
-__global__ void k_step_stats(const double* E, const double* g, const double* lam, int n,
+__global__ void k_step_stats(const double* E, const double* g, const double* lam, int n, int a,
                              double* out) {
     __shared__ double r1[256], r2[256];
     double s = 0.0, mx = 0.0;
     for (long long i = threadIdx.x; i < (long long)n * n; i += blockDim.x) {
         s = fma(g[i], g[i], s);
         int p = (int)(i / n), q = (int)(i % n);
-        mx = fmax(mx, fabs(lam[i] - lam[(long long)q * n + p]));
+        const double lpq = q < a ? lam[i] : 0.0, lqp = p < a ? lam[(long long)q * n + p] : 0.0;
+        mx = fmax(mx, fabs(lpq - lqp));
     }
     r1[threadIdx.x] = s;
     r2[threadIdx.x] = mx;
@@ -287,8 +290,10 @@ int pnof_occupations(nof_ctx* c, const double* gamma) {
                                                                c->t, c->ds, c->dt);
     NOF_LAUNCH_CHECK();
     long long aa = (long long)c->nact * c->nact;
+    float2 *Adf = nullptr, *Bcdf = nullptr;
+    fast_coefficient_buffers(c, &Adf, &Bcdf);
     k_coefficients<<<nblk(aa), 256, 0, c->stream>>>(c->s, c->t, c->pair, c->slot, c->nact,
-                                                    c->opt.ipnof, c->occ, c->A, c->Bc);
+                                                    c->opt.ipnof, c->occ, c->A, c->Bc, Adf, Bcdf);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
@@ -307,22 +312,21 @@ int pnof_hpp(nof_ctx* c, const double* C) {
     return NOF_OK;
 }
 
-int pnof_energy(nof_ctx* c) {
-    k_energy<<<1, 1024, 0, c->stream>>>(c->occ, c->hpp, c->A, c->Bc, c->J, c->K, c->vnn, c->nact, c->E);
+// E (into c->E) and dE/dgamma (into out) from J, K, h_pp and the occupations of pnof_occupations.
+int pnof_gamma_grad(nof_ctx* c, double* out) {
+    const int a = c->nact;
+    k_dE_parts<<<nblk((long long)a * 32), 256, 0, c->stream>>>(c->s, c->t, c->pair, c->slot, c->hpp,
+                                                               c->J, c->K, c->A, c->Bc, a, c->opt.ipnof,
+                                                               c->part);
+    NOF_LAUNCH_CHECK();
+    k_gamma_chain<<<nblk(c->ngamma, 128), 128, 0, c->stream>>>(c->s, c->t, c->ds, c->dt, c->slot,
+                                                                c->part, c->npair, c->opt.ncwo, a, c->vnn,
+                                                                c->E, out);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
 
-int pnof_gamma_grad(nof_ctx* c, double* out) {
-    const int a = c->nact;
-    k_dE_parts<<<nblk((long long)a * 32), 256, 0, c->stream>>>(c->s, c->t, c->pair, c->slot, c->hpp,
-                                                               c->J, c->K, a, c->opt.ipnof, c->part);
-    NOF_LAUNCH_CHECK();
-    k_gamma_chain<<<nblk(c->ngamma, 128), 128, 0, c->stream>>>(c->s, c->t, c->ds, c->dt, c->slot,
-                                                                c->part, c->npair, c->opt.ncwo, a, out);
-    NOF_LAUNCH_CHECK();
-    return NOF_OK;
-}
+int pnof_energy(nof_ctx* c) { return pnof_gamma_grad(c, c->ggam); }
 
 int pnof_jk_from_b(nof_ctx* c) {
     const int X = c->naux, a = c->nact;
@@ -354,13 +358,14 @@ int pnof_build_W(nof_ctx* c) {
     return NOF_OK;
 }
 
-// Lam currently holds sum_P T^P W^P; finish Lambda, lambda = C^T Lambda and g.
-int pnof_lambda_and_g(nof_ctx* c, const double* C, double* g_out) {
+// Lam holds sum_P T^P W^P (assembled = false) or already Lambda (assembled = true); finish
+// Lambda, lambda = C^T Lambda (columns p < a) and g.
+int pnof_lambda_and_g(nof_ctx* c, const double* C, double* g_out, bool assembled) {
     const int n = c->nbf, a = c->nact;
-    k_lambda_assemble<<<nblk((long long)n * a), 256, 0, c->stream>>>(c->HC, c->occ, n, a, c->Lam);
-    NOF_LAUNCH_CHECK();
-    k_zero<<<nblk((long long)n * n), 256, 0, c->stream>>>(c->lam, (long long)n * n);
-    NOF_LAUNCH_CHECK();
+    if (!assembled) {
+        k_lambda_assemble<<<nblk((long long)n * a), 256, 0, c->stream>>>(c->HC, c->occ, n, a, c->Lam);
+        NOF_LAUNCH_CHECK();
+    }
     Gemm64 g;  // lam[q][p] = sum_mu C[mu][q] Lam[mu][p], p < a
     g.M = n; g.N = a; g.K = n;
     g.A = C; g.sAm = 1; g.sAk0 = n;
@@ -368,7 +373,7 @@ int pnof_lambda_and_g(nof_ctx* c, const double* C, double* g_out) {
     g.C = c->lam; g.sCm = n; g.sCn = 1;
     g.work = c->gwork; g.work_cap = c->gwork_cap;
     NOF_TRY(gemm64(g, c->stream));
-    k_orbital_gradient<<<nblk((long long)n * n), 256, 0, c->stream>>>(c->lam, n, g_out);
+    k_orbital_gradient<<<nblk((long long)n * n), 256, 0, c->stream>>>(c->lam, n, a, g_out);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
@@ -424,9 +429,7 @@ int plain_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad)
         if (splits < 1) splits = 1;
         NOF_TRY(gemm64_splitk(g, splits, c->W + (long long)X * a * a, st));
     }
-    NOF_TRY(pnof_lambda_and_g(c, C, c->gorb));
-    NOF_TRY(pnof_gamma_grad(c, c->ggam));
-    return NOF_OK;
+    return pnof_lambda_and_g(c, C, c->gorb, false);
 }
 
 // ON update of an alternating step (see nof.h): on_iters steepest-descent steps on gamma with
@@ -452,7 +455,7 @@ int pnof_adam_rotate(nof_ctx* c, double* C, double* m, double* v, int* t, double
     k_adam<<<nblk(nn), 256, 0, st>>>(c->gorb, m, v, c->y, nn, c->opt.b1, c->opt.b2, c1, c2,
                                      c->opt.lr, c->opt.eps);
     NOF_LAUNCH_CHECK();
-    k_step_stats<<<1, 256, 0, st>>>(c->E, c->gorb, c->lam, n, out);
+    k_step_stats<<<1, 256, 0, st>>>(c->E, c->gorb, c->lam, n, c->nact, out);
     NOF_LAUNCH_CHECK();
     NOF_TRY(expm_antisym_device(c->y, c->U, c->U2, c->tmpn, n, st, c->gwork, c->gwork_cap));
     Gemm64 g;  // tmp = C U
