@@ -173,22 +173,33 @@ def generate(sizes, orb, aux, seed=11, precision=1, on_iters=300, gamma0=0.3):
     return np.concatenate(feats), np.concatenate(targs)
 
 
-def evaluate(net: MLP, sizes, orb, aux, steps=60, seed=13, precision=1, gamma0=0.3):
+def evaluate(net: MLP, sizes, orb, aux, steps=60, seed=13, precision=1, gamma0=0.3, straight=False):
     """Energies along the optimisation from the core guess with learned vs constant starting
-    angles, for held-out geometries: list of (N, E_learned[steps], E_constant[steps])."""
+    angles, for held-out geometries (displaced chains, or straight 1.8-bohr chains): list of
+    (N, E_learned[steps], E_constant[steps], seconds: set-up, core guess, per step)."""
+    import time
+
+    import torch
+
     from . import Context
     out = []
     for i, N in enumerate(sizes):
-        xyz = inputs.displaced_chain(int(N), seed=seed * 100003 + i)
+        xyz = inputs.chain(int(N), 1.8) if straight else inputs.displaced_chain(int(N), seed=seed * 100003 + i)
+        t0 = time.perf_counter()
         ctx = Context(precision=precision)
         ctx.build_B(xyz, orb, aux)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         C0, eps = ctx.core_guess()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
         ng = ctx.sizes["ngamma"]
         g_learn = np.full(ng, gamma0)
         g_learn[: int(N) // 2] = angles(predict(net, pair_features(xyz, eps.cpu().numpy(), int(N))))
         E1, _, _ = optimise(ctx, g_learn, steps, C0=C0)
+        t3 = time.perf_counter()
         E2, _, _ = optimise(ctx, np.full(ng, gamma0), steps, C0=C0)
-        out.append((int(N), E1[:, 0], E2[:, 0]))
+        out.append((int(N), E1[:, 0], E2[:, 0], (t1 - t0, t2 - t1, (t3 - t2) / steps)))
         ctx.close()
     return out
 
@@ -207,12 +218,17 @@ def main(argv=None):
     ap.add_argument("--eval-sizes", type=int, nargs="*", default=[40, 48, 64])
     ap.add_argument("--eval-steps", type=int, default=40)
     ap.add_argument("--iters", type=int, default=1500)
+    ap.add_argument("--min-len", type=int, default=6)
+    ap.add_argument("--basis", choices=["3s10aux", "h1000"], default="3s10aux",
+                    help="3s10aux: 3 s + 10 aux s per H; h1000: 1 contracted s + 3 aux s per H")
+    ap.add_argument("--straight-eval", action="store_true", help="evaluate on straight 1.8-bohr chains")
     args = ap.parse_args(argv)
-    orb, aux = inputs.basis_3s_10aux()
+    orb, aux = inputs.basis_h1000() if args.basis == "h1000" else inputs.basis_3s_10aux()
     t0 = time.perf_counter()
-    X, y = generate(inputs.batch_sizes(args.train_chains, seed=21, lo=6, hi=args.max_len), orb, aux, seed=11)
-    Xv, yv = generate(inputs.batch_sizes(max(8, args.train_chains // 8), seed=22, lo=6, hi=args.max_len), orb, aux,
-                      seed=12)
+    X, y = generate(inputs.batch_sizes(args.train_chains, seed=21, lo=args.min_len, hi=args.max_len), orb, aux,
+                    seed=11)
+    Xv, yv = generate(inputs.batch_sizes(max(8, args.train_chains // 8), seed=22, lo=args.min_len, hi=args.max_len),
+                      orb, aux, seed=12)
     t_data = time.perf_counter() - t0
     net = MLP(NFEAT, 256, 1, seed=0)
     t0 = time.perf_counter()
@@ -220,17 +236,20 @@ def main(argv=None):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     pv = predict(net, Xv)
-    res = evaluate(net, args.eval_sizes, orb, aux, steps=args.eval_steps)
+    res = evaluate(net, args.eval_sizes, orb, aux, steps=args.eval_steps, straight=args.straight_eval)
     rows = []
-    for N, El, Ec in res:
+    for N, El, Ec, secs in res:
         Emin = min(El.min(), Ec.min())
         def first(E, tol):
             idx = np.nonzero(E - Emin <= tol)[0]
             return int(idx[0]) + 1 if idx.size else None
         rows.append({"N": N, "E_first_learned": float(El[0]), "E_first_constant": float(Ec[0]),
                      "E_end_learned": float(El[-1]), "E_end_constant": float(Ec[-1]),
-                     "steps_to_1e-3_learned": first(El, 1e-3), "steps_to_1e-3_constant": first(Ec, 1e-3)})
-    print(json.dumps({"train_pairs": int(X.shape[0]), "data_s": round(t_data, 1), "train_s": round(t_train, 2),
+                     "steps_to_1e-3_learned": first(El, 1e-3), "steps_to_1e-3_constant": first(Ec, 1e-3),
+                     "setup_s": round(secs[0], 2), "core_guess_s": round(secs[1], 2), "step_s": round(secs[2], 4),
+                     "E_learned_every_5": [float(x) for x in El[4::5]],
+                     "E_constant_every_5": [float(x) for x in Ec[4::5]]})
+    print(json.dumps({"basis": args.basis, "train_pairs": int(X.shape[0]), "data_s": round(t_data, 1), "train_s": round(t_train, 2),
                       "loss_first": hist[0], "loss_last": hist[-1],
                       "val_rmse": float(np.sqrt(np.mean((pv - yv) ** 2))),
                       "val_rmse_mean_predictor": float(np.sqrt(np.mean((y.mean() - yv) ** 2))),
