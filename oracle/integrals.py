@@ -69,6 +69,21 @@ def nbf(basis, xyz) -> int:
     return basis.per_atom * xyz.shape[0]
 
 
+def overlap(basis, xyz):
+    """S alone (the first matrix of one_electron) for systems where the nuclear-attraction sum
+    over all nuclei is too slow: S_ab = (pi/p)^{3/2} exp(-ab/p |AB|^2) per primitive pair."""
+    fi, cen, ex, co = _prim_table(basis, xyz)
+    n = nbf(basis, xyz)
+    a = ex[:, None]
+    b = ex[None, :]
+    p = a + b
+    AB2 = np.sum((cen[:, None, :] - cen[None, :, :]) ** 2, axis=-1)
+    Sp = (np.pi / p) ** 1.5 * np.exp(-a * b / p * AB2)
+    S = np.zeros((n, n))
+    np.add.at(S, (fi[:, None], fi[None, :]), co[:, None] * co[None, :] * Sp)
+    return S
+
+
 def one_electron(basis, xyz, Z=None):
     """S, T and V (nuclear attraction of all nuclei) as n x n FP64 matrices."""
     natom = xyz.shape[0]

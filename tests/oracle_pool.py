@@ -10,7 +10,7 @@ from concurrent.futures import ProcessPoolExecutor
 
 import numpy as np
 
-from oracle import integrals, large
+from oracle import integrals, large, ri
 
 
 def _slice(args):
@@ -37,3 +37,32 @@ def fitted_mo(orb, aux, xyz, C, nact, workers=None):
             else:
                 os.environ[k] = v
     return large.fitted_mo(Q3, integrals.two_center(aux, xyz))
+
+
+def _slice_cols(args):
+    orb, aux, xyz, Cs, lo, hi = args
+    M = integrals.three_center(orb, aux, xyz, slice(lo, hi))
+    return np.matmul(Cs.T[None, :, :], np.matmul(M, Cs))
+
+
+def fitted_columns(orb, aux, xyz, Cs, workers=None):
+    """b^P_{ij} = sum_Q (V^{-1/2})_{PQ} (Q|i j) for the orbitals given as the columns of Cs only
+    ([X][k][k]); the three-centre integrals are generated in parallel slices of aux functions."""
+    X = integrals.naux(aux, xyz)
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    step = max(1, -(-X // (4 * workers)))
+    jobs = [(orb, aux, xyz, Cs, lo, min(X, lo + step)) for lo in range(0, X, step)]
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            Q3 = np.concatenate(list(ex.map(_slice_cols, jobs)))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    k = Q3.shape[1]
+    return (ri.inverse_sqrt_metric(integrals.two_center(aux, xyz)) @ Q3.reshape(X, k * k)).reshape(X, k, k)

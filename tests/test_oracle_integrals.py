@@ -141,3 +141,8 @@ def test_ri_ill_conditioned_metric_is_refused():
     xyz = np.zeros((1, 3))
     with pytest.raises(ri.IllConditioned):
         ri.inverse_sqrt_metric(integrals.two_center(aux, xyz))
+
+
+def test_overlap_alone_equals_one_electron_overlap():
+    for orb, xyz in [(inputs.basis_h4()[0], inputs.chain(4, 1.8)), (inputs.basis_3s_10aux()[0], inputs.chain(6, 1.8))]:
+        np.testing.assert_allclose(integrals.overlap(orb, xyz), integrals.one_electron(orb, xyz)[0], atol=1e-15)
