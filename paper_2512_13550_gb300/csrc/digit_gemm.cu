@@ -125,6 +125,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -339,16 +347,23 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                 const int erp = (partsc && row < g.M) ? g.epA[gp * g.M + row] - kOff : er;
                 const uint32_t acc = tmem + lane_base + (uint32_t)(b * ND * BN);
                 for (int c0 = 0; c0 < cw; c0 += 16) {
+                    const int w = min(16, cw - c0);  // 16, or 8 for the last chunk of a 24-column half
                     float v[ND][16];
                     const uint32_t col = (uint32_t)(cbeg + c0);
+                    if (w == 16) {
 #pragma unroll
-                    for (int l = 0; l < ND; ++l) tmem_ld16(acc + (uint32_t)(l * BN) + col, v[l]);
+                        for (int l = 0; l < ND; ++l) tmem_ld16(acc + (uint32_t)(l * BN) + col, v[l]);
+                    } else {
+#pragma unroll
+                        for (int l = 0; l < ND; ++l) tmem_ld8(acc + (uint32_t)(l * BN) + col, v[l]);
+                    }
                     tmem_wait_ld();
                     if (ints) {
                         // level sums are exact integers below 2^24: 32-bit conversions and a 64-bit
                         // integer sum (64-bit int <-> float conversions run at the FP64 rate here)
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
+                            if (j >= w) break;
                             long long Vp = 0;
 #pragma unroll
                             for (int l = 0; l < ND; ++l) Vp += (long long)__float2int_rn(v[l][j]) << (8 * (ND - 1 - l));
@@ -359,6 +374,7 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                         const int* ec = partsc ? g.epB + gp * g.Nvalid : g.ecol;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
+                            if (j >= w) break;
                             const int e = erp + ec[min(col0 + c0 + j, g.Nvalid - 1)];
                             float S[ND];
 #pragma unroll
@@ -501,7 +517,7 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
     g.katoms = chunk_atoms < katoms_total ? chunk_atoms : katoms_total;
     g.katoms_total = katoms_total;
     g.apart = (partsc || nd == 5) ? kPartAtoms : 10;
-    g.nbuf = 2;
+    g.nbuf = digit_nbuf(BN, nd);
     int cols = 32;
     while (cols < g.nbuf * nd * BN) cols *= 2;
     g.tmem_cols = cols;

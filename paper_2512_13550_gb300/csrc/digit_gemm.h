@@ -4,11 +4,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-// Tile widths along N the kernel supports (two TMEM accumulator sets of nd levels x BN columns
-// must fit the 512 TMEM columns, and the epilogue splits BN >= 32 into two column halves):
-// 16, 32, 64 with 4 digits, 16, 32 with 5 digits.
-constexpr int kDigitBN[3] = {16, 32, 64};
-inline bool digit_bn_ok(int BN, int nd) { return (BN == 16 || BN == 32 || BN == 64) && 2 * nd * BN <= 512; }
+// Tile widths along N the kernel supports: 16, 32, 48, 64 (the epilogue splits BN >= 32 into two
+// column halves, read from TMEM in chunks of 16 columns and, for 48, one of 8). The TMEM accumulators (nd levels x BN columns per set) take two sets when
+// 2 nd BN <= 512 columns (the drain of one set overlaps the MMAs into the other) and one set
+// otherwise (5 digits with BN = 64).
+constexpr int kDigitBN[4] = {16, 32, 48, 64};
+inline bool digit_bn_ok(int BN, int nd) {
+    return (BN == 16 || BN == 32 || BN == 48 || BN == 64) && nd * BN <= 512;
+}
+inline int digit_nbuf(int BN, int nd) { return 2 * nd * BN <= 512 ? 2 : 1; }
 
 struct DigitGemmArgs {
     int nd;            // digits per element (4 or 5): nd (nd + 1) / 2 plane products per K atom

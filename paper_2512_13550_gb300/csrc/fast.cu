@@ -18,6 +18,7 @@
 // Tile widths, pipeline depth and the split-K chunk of each GEMM come from the autotuner.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "digit_gemm.h"
@@ -458,9 +459,12 @@ int fast_prepare(nof_ctx* c) {
     const int nkp = (int)((rows2 / 16 + kPartAtoms - 1) / kPartAtoms);  // parts of GEMM3's K = (P, r)
     const int kat3 = nkp * kPartAtoms;
     f->nkp = nkp;
-    const long long nBd = digit_elems(128, rowsB, katK, nd), nCd = digit_elems(64, ap, katK, nd),
+    // N-side operands (C digits, W digits) hold whole tiles of every candidate width BN
+    long long npad = ap;
+    for (int bn : kDigitBN) npad = std::max(npad, (long long)(ap + bn - 1) / bn * bn);
+    const long long nBd = digit_elems(128, rowsB, katK, nd), nCd = digit_elems(16, npad, katK, nd),
                     nTd2 = digit_elems(128, rows2, katK, nd), nTd3 = digit_elems(128, n, kat3, nd),
-                    nWd3 = digit_elems(64, ap, kat3, nd);
+                    nWd3 = digit_elems(16, npad, kat3, nd);
     {   // J/K chunks: enough blocks for a few waves, never more than one chunk per 8 aux indices
         const int per = (int)nblk((long long)a * a);
         int nc = (4 * 152 + per - 1) / per;
@@ -496,9 +500,9 @@ int fast_prepare(nof_ctx* c) {
     NOF_LAUNCH_CHECK();
 
     // ---- autotuned plans ----------------------------------------------------------------
-    int bns[3];
+    int bns[4];
     const int nbn = bn_candidates(ap, nd, bns);
-    DigitGemmPlan cand[16];
+    DigitGemmPlan cand[20];
     int best = 0;
     {   // GEMM1: T = B C, scaled double-float output with the maxima of |T|
         DigitGemmOut o;
@@ -525,7 +529,7 @@ int fast_prepare(nof_ctx* c) {
         // (summed afterwards in a fixed order, so results do not depend on scheduling)
         const long long na = (long long)n * a;
         const long long max_chunks = ((long long)1 << 31) / 8 / na;  // at most 2 GiB of partials
-        int k = 0, bnk[16], chk[16];  // at most 3 widths x 4 chunks
+        int k = 0, bnk[20], chk[20];  // at most 4 widths x 4 chunks
         for (int i = 0; i < nbn; ++i) {
             // per tile width, the four longest chunks (8 * 2^i atoms, or all of K) that still give
             // half a wave of tiles (longer chunks mean fewer partials and less per-tile overhead)

@@ -24,6 +24,9 @@ CASES = [
     ("stream 600000 x 64 x 640, BN 16", 600000, 64, 16, 4, 40, 40, 0),
     ("stream 600000 x 64 x 640, 5 digits, BN 32", 600000, 64, 32, 5, 40, 40, 0),
     ("H200 half transform, 5 digits, BN 32", 1200000, 208, 32, 5, 38, 38, 1),
+    ("H200 half transform, 5 digits, BN 48", 1200000, 208, 48, 5, 38, 38, 1),
+    ("H200 half transform, 5 digits, BN 64 (one TMEM set)", 1200000, 208, 64, 5, 38, 38, 1),
+    ("stream 600000 x 64 x 640, 5 digits, BN 64 (one TMEM set)", 600000, 64, 64, 5, 40, 40, 0),
     ("H200 half transform, 4 digits, BN 64", 1200000, 208, 64, 4, 38, 38, 1),
 ]
 

@@ -21,6 +21,10 @@ pytestmark = pytest.mark.gpu
     (300, 80, 16, 38, 38, 5),    # 5 digits, five parts (8 + 8 + 8 + 8 + 6), five N tiles
     (257, 64, 32, 24, 9, 5),     # 5 digits, split-K with ragged chunks (9, 9, 6) and two N tiles
     (130, 208, 32, 63, 63, 5),   # 5 digits, K = 1008 (eight parts), seven N tiles
+    (300, 208, 64, 38, 38, 5),   # 5 digits, BN 64 with one TMEM set (five parts drained in turn)
+    (256, 64, 64, 24, 10, 5),    # 5 digits, BN 64, one TMEM set, split-K (chunks 10, 10, 4)
+    (300, 208, 48, 38, 38, 5),   # 5 digits, BN 48 (24-column halves: chunks of 16 and 8), five tiles
+    (257, 100, 48, 12, 12, 4),   # 4 digits, BN 48, ragged last tile (100 = 2 x 48 + 4)
 ])
 def test_digit_gemm_exact(M, N, bn, katoms, chunk, nd):
     import paper_2512_13550_gb300 as nof
