@@ -44,3 +44,33 @@ def test_null_arguments_rejected_without_device_work(lib):
     assert lib.nof_query(None, None, None, None, None, None) == nof.NOF_EINVAL
     assert lib.nof_destroy(None) == nof.NOF_OK
     assert b"null" in lib.nof_last_error()
+
+
+def test_argument_checks_of_measurement_and_deployment_entry_points(lib):
+    """Invalid arguments are refused on the host, before any device work (no GPU needed)."""
+    d = ctypes.c_double(0.0)
+    ll = ctypes.c_longlong(0)
+    # tile width 24 is not a supported N tile; 5 digits with BN 64 and 4 digits are fine shapes
+    assert lib.nof_bench_digit_gemm(128, 64, 24, 4, 10, 10, 0, 1, ctypes.byref(d)) == nof.NOF_EINVAL
+    assert lib.nof_bench_digit_gemm(128, 64, 64, 6, 10, 10, 0, 1, ctypes.byref(d)) == nof.NOF_EINVAL
+    assert lib.nof_bench_digit_gemm(128, 64, 64, 4, 10, 3, 2, 1, ctypes.byref(d)) == nof.NOF_EINVAL  # chunk % 8
+    assert lib.nof_bench_digit_gemm(128, 64, 64, 4, 10, 10, 0, 1, None) == nof.NOF_EINVAL
+    assert lib.nof_selftest_digit_gemm(128, 64, 24, 4, 10, 10, 1, ctypes.byref(ll)) == nof.NOF_EINVAL
+    assert lib.nof_selftest_digit_gemm(0, 64, 64, 4, 10, 10, 1, ctypes.byref(ll)) == nof.NOF_EINVAL
+    assert lib.nof_tuned_tiles(None, (ctypes.c_int * 4)()) == nof.NOF_EINVAL
+    # the allocation-free JK refuses sizes beyond its fixed scratch before touching the device
+    p = ctypes.c_void_p(16)
+    assert lib.nof_jk_static(2000, 600, 200, p, p, p, p, None) == nof.NOF_EINVAL
+    assert b"exceeds" in lib.nof_last_error()
+    assert lib.nof_jk_static(10, 4, 5, p, p, p, p, None) == nof.NOF_EINVAL  # nact > nbf
+
+
+def test_bad_options_rejected(lib):
+    o = nof.Options()
+    lib.nof_default_options(ctypes.byref(o))
+    assert o.digits == 0
+    o.precision, o.digits = 1, 3
+    h = ctypes.c_void_p()
+    assert lib.nof_create(ctypes.byref(h), ctypes.byref(o), None) == nof.NOF_EINVAL
+    o.digits, o.ipnof = 0, 6
+    assert lib.nof_create(ctypes.byref(h), ctypes.byref(o), None) == nof.NOF_EINVAL
