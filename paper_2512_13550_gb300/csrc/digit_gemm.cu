@@ -346,10 +346,16 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                 const long long gp = (long long)(kc * g.katoms) / g.apart + part;  // part index along K
                 const int erp = (partsc && row < g.M) ? g.epA[gp * g.M + row] - kOff : er;
                 const uint32_t acc = tmem + lane_base + (uint32_t)(b * ND * BN);
+                const int* ec = partsc ? g.epB + gp * g.Nvalid : g.ecol;
                 for (int c0 = 0; c0 < cw; c0 += 16) {
                     const int w = min(16, cw - c0);  // 16, or 8 for the last chunk of a 24-column half
                     float v[ND][16];
                     const uint32_t col = (uint32_t)(cbeg + c0);
+                    int ecj[16];  // column exponents, fetched before the TMEM reads to overlap them
+                    if (!ints) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) ecj[j] = ec[min(col0 + c0 + j, g.Nvalid - 1)];
+                    }
                     if (w == 16) {
 #pragma unroll
                         for (int l = 0; l < ND; ++l) tmem_ld16(acc + (uint32_t)(l * BN) + col, v[l]);
@@ -371,11 +377,10 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                             s = part ? s + Vp : Vp;
                         }
                     } else {
-                        const int* ec = partsc ? g.epB + gp * g.Nvalid : g.ecol;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             if (j >= w) break;
-                            const int e = erp + ec[min(col0 + c0 + j, g.Nvalid - 1)];
+                            const int e = erp + ecj[j];
                             float S[ND];
 #pragma unroll
                             for (int l = 0; l < ND; ++l) S[l] = v[l][j];
@@ -393,10 +398,12 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
             if (!ok) break;
             __syncwarp();
             const int ncol = min(cw, g.Nvalid - col0);  // valid staged columns
+            // lanes cover whole rows of the staging tile: row lane / L, column lane % L, with L the
+            // number of lanes per row (cw elements, or cw / 2 pairs) and 32 / L rows per pass
             if (ncol > 0) {
                 if (g.out) {
-                    for (int idx = lane; idx < 32 * cw; idx += 32) {
-                        const int rr = idx / cw, cc = idx - rr * cw;
+                    const int rpp = 32 / cw, lr = lane / cw, cc = lane - lr * cw;
+                    for (int rr = lr; lr < rpp && rr < 32; rr += rpp) {
                         const int grow = rbase + rr;
                         if (grow >= g.M || cc >= ncol) continue;
                         long long* dst = g.out + (long long)grow * g.ldo + col0 + cc;
@@ -405,8 +412,8 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                         else *dst = V;
                     }
                 } else if (g.outd) {
-                    for (int idx = lane; idx < 32 * cw; idx += 32) {
-                        const int rr = idx / cw, cc = idx - rr * cw;
+                    const int rpp = 32 / cw, lr = lane / cw, cc = lane - lr * cw;
+                    for (int rr = lr; lr < rpp && rr < 32; rr += rpp) {
                         const int grow = rbase + rr;
                         if (grow >= g.M || cc >= ncol) continue;
                         double* dst = g.outd + (long long)kc * g.chunk_stride + (long long)grow * g.ldo + col0 + cc;
@@ -418,8 +425,8 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                 } else {
                     // pairs of columns as 16-byte stores, consecutive lanes along a row
                     const int hp = cw / 2;
-                    for (int idx = lane; idx < 32 * hp; idx += 32) {
-                        const int rr = idx / hp, cc = 2 * (idx - rr * hp);
+                    const int rpp = 32 / hp, lr = lane / hp, cc = 2 * (lane - lr * hp);
+                    for (int rr = lr; lr < rpp && rr < 32; rr += rpp) {
                         const int grow = rbase + rr;
                         if (grow >= g.M || cc >= ncol) continue;
                         float2* dst = g.outf + (long long)grow * g.ldo + col0 + cc;

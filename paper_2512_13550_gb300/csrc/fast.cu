@@ -34,6 +34,7 @@ struct FastState {
     uint16_t* Td2; int* e2;     // [4][katK][X ap][16], per (P, p)
     uint16_t* Td3; int* epT;    // [4][8 nkp][n][16] (K = (P, r) padded to nkp parts), scale per (part, mu)
     float2* bdf;                // [X ap][ap] b^P_{p q} as double-floats
+    float2* ddf;                // [X][a] d^P_p = b^P_pp (written by the J/K partial sums)
     float2* Ddf;                // [X][a] D^P_p = sum_r A_pr d^P_r
     uint16_t* Wd3; int* epW;    // rows p (tiles of bn3), K = (P, r); scale per (part, p)
     float2 *Adf, *Bcdf;         // [a][a]
@@ -258,9 +259,10 @@ __device__ __forceinline__ float2 b_val(const float2* bdf, int ap, int P, int p,
 }
 
 // Partial sums over one chunk of aux indices: J_pq += d_p d_q, K_pq += (b_pq)^2 (double-float),
-// with d^P_p = b^P_pp read from b; grid (ceil(a*a/256), nchunk); partials [chunk][a*a] as FP64.
+// with d^P_p = b^P_pp read from b (and stored contiguously in d); grid (ceil(a*a/256), nchunk);
+// partials [chunk][a*a] as FP64.
 __global__ void __launch_bounds__(256) k_JK_partial(const float2* bdf, int X, int a, int ap, int nchunk,
-                                                    double* Jpart, double* Kpart) {
+                                                    double* Jpart, double* Kpart, float2* d) {
     const int idx = blockIdx.x * 256 + threadIdx.x;
     const int aa = a * a;
     if (idx >= aa) return;
@@ -272,6 +274,7 @@ __global__ void __launch_bounds__(256) k_JK_partial(const float2* bdf, int X, in
         float2 b = b_val(bdf, ap, P, p, q);
         kacc = df_add(kacc, df_mul(b, b));
         jacc = df_add(jacc, df_mul(b_val(bdf, ap, P, p, p), b_val(bdf, ap, P, q, q)));
+        if (p == q) d[(long long)P * a + p] = b;  // the diagonal, contiguous for D = d A
     }
     Jpart[(long long)blockIdx.y * aa + idx] = df_to_double(jacc);
     Kpart[(long long)blockIdx.y * aa + idx] = df_to_double(kacc);
@@ -291,45 +294,23 @@ __global__ void k_reduce_parts(const double* part0, double* out0, const double* 
     if (lane == 0) out[i] = s;
 }
 
-// D^P_p = sum_r d^P_r A_rp (A symmetric, d^P_r = b^P_rr): a double-float GEMM D [X][a] = d A in
-// 32 x 32 output tiles, 2 x 2 outputs per thread, K = r staged through shared memory 16 at a time.
-__global__ void __launch_bounds__(256) k_D_df(const float2* Adf, const float2* bdf, int X, int a, int ap,
-                                              float2* D) {
-    __shared__ float2 ds[32][17];  // [P][r]
-    __shared__ float2 as[16][33];  // [r][p]
+// D^P_p = sum_r d^P_r A_rp (A symmetric): a double-float GEMM D [X][a] = d [X][a] A [a][a] in
+// 16 x 16 output tiles, one output per thread, K = r staged through shared memory 16 at a time.
+__global__ void __launch_bounds__(256) k_D_df(const float2* Adf, const float2* d, int X, int a, float2* D) {
+    __shared__ float2 ds[16][17];  // [P][r]
+    __shared__ float2 as[16][17];  // [r][p]
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int P0 = blockIdx.y * 32, p0 = blockIdx.x * 32;
-    float2 acc[2][2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    const int P0 = blockIdx.y * 16, p0 = blockIdx.x * 16;
+    float2 acc = make_float2(0.f, 0.f);
     for (int r0 = 0; r0 < a; r0 += 16) {
-        for (int e = threadIdx.x; e < 32 * 16; e += 256) {
-            const int i = e >> 4, k = e & 15;  // d tile: row P0 + i, column r0 + k
-            ds[i][k] = (P0 + i < X && r0 + k < a) ? b_val(bdf, ap, P0 + i, r0 + k, r0 + k) : make_float2(0.f, 0.f);
-            const int kk = e >> 5, j = e & 31;  // A tile: row r0 + kk, column p0 + j
-            as[kk][j] = (r0 + kk < a && p0 + j < a) ? Adf[(long long)(r0 + kk) * a + p0 + j] : make_float2(0.f, 0.f);
-        }
+        ds[ty][tx] = (P0 + ty < X && r0 + tx < a) ? d[(long long)(P0 + ty) * a + r0 + tx] : make_float2(0.f, 0.f);
+        as[ty][tx] = (r0 + ty < a && p0 + tx < a) ? Adf[(long long)(r0 + ty) * a + p0 + tx] : make_float2(0.f, 0.f);
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const float2 d0 = ds[ty][k], d1 = ds[ty + 16][k];
-            const float2 a0 = as[k][tx], a1 = as[k][tx + 16];
-            acc[0][0] = df_add(acc[0][0], df_mul(d0, a0));
-            acc[0][1] = df_add(acc[0][1], df_mul(d0, a1));
-            acc[1][0] = df_add(acc[1][0], df_mul(d1, a0));
-            acc[1][1] = df_add(acc[1][1], df_mul(d1, a1));
-        }
+        for (int k = 0; k < 16; ++k) acc = df_add(acc, df_mul(ds[ty][k], as[k][tx]));
         __syncthreads();
     }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int P = P0 + ty + 16 * i, q = p0 + tx + 16 * j;
-            if (P < X && q < a) D[(long long)P * a + q] = acc[i][j];
-        }
+    if (P0 + ty < X && p0 + tx < a) D[(long long)(P0 + ty) * a + p0 + tx] = acc;
 }
 
 // W^P_rp = delta_rp D^P_p - B_pr b^P_rp for p, r < a (zero in the padding); b^P is symmetric, so
@@ -427,7 +408,7 @@ int fast_release(nof_ctx* c) {
     FastState* f = c->fast;
     if (!f) return NOF_OK;
     ffree(f->Bd); ffree(f->eB); ffree(f->Cd1); ffree(f->Cd2); ffree(f->eC); ffree(f->Tdf); ffree(f->colT);
-    ffree(f->Td2); ffree(f->e2); ffree(f->Td3); ffree(f->epT); ffree(f->bdf); ffree(f->Ddf);
+    ffree(f->Td2); ffree(f->e2); ffree(f->Td3); ffree(f->epT); ffree(f->bdf); ffree(f->ddf); ffree(f->Ddf);
     ffree(f->Wd3); ffree(f->epW); ffree(f->Adf); ffree(f->Bcdf); ffree(f->Jpart); ffree(f->Lpart);
     ffree(f->Kpart);
     delete f;
@@ -478,7 +459,7 @@ int fast_prepare(nof_ctx* c) {
     NOF_TRY(falloc(&f->Td2, nTd2)); NOF_TRY(falloc(&f->e2, rows2));
     NOF_TRY(falloc(&f->Td3, nTd3)); NOF_TRY(falloc(&f->epT, (size_t)nkp * n));
     NOF_TRY(falloc(&f->bdf, rows2 * ap));
-    NOF_TRY(falloc(&f->Ddf, (size_t)X * a));
+    NOF_TRY(falloc(&f->ddf, (size_t)X * a)); NOF_TRY(falloc(&f->Ddf, (size_t)X * a));
     NOF_TRY(falloc(&f->Wd3, nWd3)); NOF_TRY(falloc(&f->epW, (size_t)nkp * a));
     NOF_TRY(falloc(&f->Adf, (size_t)a * a)); NOF_TRY(falloc(&f->Bcdf, (size_t)a * a));
     NOF_TRY(falloc(&f->Jpart, (size_t)f->nchunkJK * a * a)); NOF_TRY(falloc(&f->Kpart, (size_t)f->nchunkJK * a * a));
@@ -610,7 +591,8 @@ int fast_jk(nof_ctx* c, const double* C) {
     NOF_LAUNCH_CHECK();
     NOF_TRY(digit_gemm_run(f->g2, st));
     const int nchunk = f->nchunkJK;
-    k_JK_partial<<<dim3(nblk((long long)a * a), nchunk), 256, 0, st>>>(f->bdf, X, a, ap, nchunk, f->Jpart, f->Kpart);
+    k_JK_partial<<<dim3(nblk((long long)a * a), nchunk), 256, 0, st>>>(f->bdf, X, a, ap, nchunk, f->Jpart, f->Kpart,
+                                                                      f->ddf);
     NOF_LAUNCH_CHECK();
     k_reduce_parts<<<dim3(nblk((long long)a * a * 32), 2), 256, 0, st>>>(f->Jpart, c->J, f->Kpart, c->K, nchunk,
                                                                         a * a);
@@ -625,7 +607,7 @@ int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad) 
     NOF_TRY(pnof_occupations(c, gamma));  // also A and B as double-floats
     NOF_TRY(pnof_energy(c));              // E and dE/dgamma
     if (!want_grad) return NOF_OK;
-    k_D_df<<<dim3((a + 31) / 32, (X + 31) / 32), 256, 0, st>>>(f->Adf, f->bdf, X, a, ap, f->Ddf);
+    k_D_df<<<dim3((a + 15) / 16, (X + 15) / 16), 256, 0, st>>>(f->Adf, f->ddf, X, a, f->Ddf);
     NOF_LAUNCH_CHECK();
     k_W_digits<<<dim3(f->nkp, (a + 7) / 8), 128, 0, st>>>(f->bdf, f->Bcdf, f->Ddf, X, a, ap, f->nkp, f->nd, f->bn3,
                                                           f->Wd3, f->epW);
