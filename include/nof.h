@@ -65,6 +65,13 @@ typedef struct {
                          chooses 5 when naux * nact > 80000 (where the truncation error of 4
                          digits, accumulated over the naux * nact terms of the Lagrangian, nears
                          1e-6), else 4 */
+    int graphs;       /* 1 (default): when nof_energy_grad is called twice in a row with the same
+                         pointers, the second call records its kernels as a CUDA graph on the
+                         context's stream, and later calls with those pointers replay it (one
+                         launch instead of about 30). The graph reads the arrays, so their contents
+                         may change between calls. 0: every call launches its kernels one by one.
+                         No graph is recorded on the legacy default stream (stream 0), while
+                         nof_profile is on, or while the caller is capturing the stream. */
 } nof_options;
 
 /* s-only contracted basis repeated on every atom (host arrays). Shell s has nprim[s]

@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
     _fields_ = [("ipnof", ctypes.c_int), ("isoftmax", ctypes.c_int), ("ncwo", ctypes.c_int),
                 ("precision", ctypes.c_int), ("on_iters", ctypes.c_int), ("on_lr", ctypes.c_double),
                 ("lr", ctypes.c_double), ("b1", ctypes.c_double), ("b2", ctypes.c_double),
-                ("eps", ctypes.c_double), ("digits", ctypes.c_int)]
+                ("eps", ctypes.c_double), ("digits", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 class CBasis(ctypes.Structure):

@@ -81,7 +81,19 @@ void dfree(T*& p) {
     p = nullptr;
 }
 
+// Forget the recorded evaluation graph (its kernels name workspaces that are about to change).
+void drop_eval_graph(nof_ctx* c) {
+    if (c->geval) {
+        cudaStreamSynchronize(c->stream);  // no replay of it still pending
+        cudaGraphExecDestroy(c->geval);
+    }
+    c->geval = nullptr;
+    c->gkernels = 0;
+    for (int i = 0; i < 5; ++i) c->gkey[i] = c->glast[i] = nullptr;
+}
+
 void free_system(nof_ctx* c) {
+    drop_eval_graph(c);
     if (c->fast) fast_release(c);
     dfree(c->fn_atom); dfree(c->fn_first); dfree(c->fn_nprim); dfree(c->pexp); dfree(c->pcoef);
     dfree(c->ax_atom); dfree(c->axexp); dfree(c->xyz); dfree(c->Z);
@@ -158,6 +170,7 @@ void nof_default_options(nof_options* o) {
     o->b2 = 0.999;
     o->eps = 1e-8;
     o->digits = 0;
+    o->graphs = 1;
 }
 
 const char* nof_last_error(void) { return g_last_error.c_str(); }
@@ -181,8 +194,8 @@ int nof_create(nof_ctx** out, const nof_options* opt, void* stream) {
     }
     if (o.ncwo < 1 || o.on_iters < 0 ||
         (o.precision != NOF_PREC_FP64 && o.precision != NOF_PREC_SPLIT_BF16) ||
-        (o.digits != 0 && o.digits != 4 && o.digits != 5)) {
-        nof_set_error("nof_create: bad ncwo, on_iters, precision or digits");
+        (o.digits != 0 && o.digits != 4 && o.digits != 5) || (o.graphs != 0 && o.graphs != 1)) {
+        nof_set_error("nof_create: bad ncwo, on_iters, precision, digits or graphs");
         return NOF_EINVAL;
     }
     nof_ctx* c = new (std::nothrow) nof_ctx;
@@ -496,13 +509,9 @@ int nof_jk(nof_ctx* c, const double* C, double* J, double* K) {
     return NOF_OK;
 }
 
-int nof_energy_grad(nof_ctx* c, const double* C, const double* gamma, double* E, double* g_orb,
-                    double* g_gamma) {
-    NOF_TRY(check_ctx(c, true));
-    if (!C || !gamma) {
-        nof_set_error("nof_energy_grad: null C or gamma");
-        return NOF_EINVAL;
-    }
+// One evaluation, every kernel launched on the context's stream.
+static int energy_grad_body(nof_ctx* c, const double* C, const double* gamma, double* E, double* g_orb,
+                            double* g_gamma) {
     const bool grad = g_orb || g_gamma;
     NOF_TRY(run_jk(c, C));
     NOF_TRY(run_grad(c, C, gamma, grad));
@@ -513,6 +522,55 @@ int nof_energy_grad(nof_ctx* c, const double* C, const double* gamma, double* E,
     if (g_gamma)
         NOF_CUDA(cudaMemcpyAsync(g_gamma, c->ggam, (size_t)c->ngamma * sizeof(double),
                                  cudaMemcpyDeviceToDevice, c->stream));
+    return NOF_OK;
+}
+
+int nof_energy_grad(nof_ctx* c, const double* C, const double* gamma, double* E, double* g_orb,
+                    double* g_gamma) {
+    NOF_TRY(check_ctx(c, true));
+    if (!C || !gamma) {
+        nof_set_error("nof_energy_grad: null C or gamma");
+        return NOF_EINVAL;
+    }
+    if (!c->opt.graphs || !c->stream || c->prof_on || c->gfail)
+        return energy_grad_body(c, C, gamma, E, g_orb, g_gamma);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NOF_CUDA(cudaStreamIsCapturing(c->stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return energy_grad_body(c, C, gamma, E, g_orb, g_gamma);
+    const void* key[5] = {C, gamma, E, g_orb, g_gamma};
+    auto same_as = [&](const void* const* k) {
+        for (int i = 0; i < 5; ++i)
+            if (k[i] != key[i]) return false;
+        return true;
+    };
+    if (!(c->geval && same_as(c->gkey))) {
+        if (!same_as(c->glast)) {  // new pointers: run directly and remember them (the graph stays)
+            for (int i = 0; i < 5; ++i) c->glast[i] = key[i];
+            return energy_grad_body(c, C, gamma, E, g_orb, g_gamma);
+        }
+        // second call in a row with these pointers: record the evaluation, then replay it below
+        drop_eval_graph(c);
+        const long long l0 = g_launches.load();
+        NOF_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int r = energy_grad_body(c, C, gamma, E, g_orb, g_gamma);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        const long long recorded = g_launches.load() - l0;
+        g_launches.fetch_sub(recorded);  // counted again at each replay
+        if (r == NOF_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->geval, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (r != NOF_OK || e != cudaSuccess) {
+            // recording failed: nothing ran, so run directly and keep launching directly from now on
+            c->geval = nullptr;
+            c->gfail = 1;
+            cudaGetLastError();
+            return energy_grad_body(c, C, gamma, E, g_orb, g_gamma);
+        }
+        for (int i = 0; i < 5; ++i) c->gkey[i] = key[i];
+        c->gkernels = recorded;
+    }
+    NOF_CUDA(cudaGraphLaunch(c->geval, c->stream));
+    g_launches.fetch_add(c->gkernels);
     return NOF_OK;
 }
 

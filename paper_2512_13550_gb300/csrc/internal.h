@@ -66,6 +66,14 @@ struct nof_ctx {
     FastState* fast;
     // fork/join events of the batched evaluation
     cudaEvent_t ev_fork, ev_join;
+    // recorded graph of nof_energy_grad (option graphs): the argument pointers it was recorded
+    // with, the kernel launches it holds, the pointers of the last direct call, and a flag set when
+    // recording failed once (the context then launches directly)
+    cudaGraphExec_t geval;
+    const void* gkey[5];
+    const void* glast[5];
+    long long gkernels;
+    int gfail;
     // dominant-kernel timing (nof_profile)
     int prof_on;
     const char* prof_name;

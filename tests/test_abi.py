@@ -74,3 +74,7 @@ def test_bad_options_rejected(lib):
     assert lib.nof_create(ctypes.byref(h), ctypes.byref(o), None) == nof.NOF_EINVAL
     o.digits, o.ipnof = 0, 6
     assert lib.nof_create(ctypes.byref(h), ctypes.byref(o), None) == nof.NOF_EINVAL
+    lib.nof_default_options(ctypes.byref(o))
+    assert o.graphs == 1
+    o.graphs = 2
+    assert lib.nof_create(ctypes.byref(h), ctypes.byref(o), None) == nof.NOF_EINVAL

@@ -1,0 +1,105 @@
+"""Recorded-graph replay of nof_energy_grad (option graphs): the second call in a row with the same
+pointers records the evaluation as a CUDA graph and later calls replay it. Replays must give the
+same bits as direct launches, follow in-place changes of C and gamma, and count the same kernels."""
+import numpy as np
+import pytest
+
+import systems
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GATE = 1e-6
+
+
+def _t(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def _ctx(nof, sysm, precision, graphs):
+    ctx = nof.Context(precision=precision, stream=torch.cuda.Stream(), graphs=graphs)
+    ctx.build_B(sysm.xyz, sysm.orb, sysm.aux)
+    return ctx
+
+
+def _eval(nof, ctx, C, gam, E, g, gg):
+    l0 = nof.kernel_launches()
+    ctx.energy_grad(C, gam, E, g, gg)
+    ctx.stream.synchronize()
+    return nof.kernel_launches() - l0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_matches_direct_launches(precision):
+    import paper_2512_13550_gb300 as nof
+    from oracle import pnof
+    sysm = systems.chain3s(14, seed=7)
+    o = sysm.oracle
+    cg, cd = _ctx(nof, sysm, precision, 1), _ctx(nof, sysm, precision, 0)
+    n, ng = cg.sizes["nbf"], cg.sizes["ngamma"]
+    C, gam = _t(sysm.orbitals(11)), _t(sysm.gamma(12))
+    out = lambda: (torch.empty(1, dtype=torch.float64, device="cuda"),
+                   torch.empty(n, n, dtype=torch.float64, device="cuda"),
+                   torch.empty(ng, dtype=torch.float64, device="cuda"))
+    Eg, gg_, ggg = out()
+    Ed, gd, ggd = out()
+    torch.cuda.synchronize()
+
+    def same():
+        assert Eg.item() == Ed.item()
+        assert torch.equal(gg_, gd) and torch.equal(ggg, ggd)
+
+    # direct, recorded, then replayed calls with unchanged pointers
+    for it in range(4):
+        lg = _eval(nof, cg, C, gam, Eg, gg_, ggg)
+        ld = _eval(nof, cd, C, gam, Ed, gd, ggd)
+        same()
+        assert lg == ld > 0, (it, lg, ld)
+    ref = pnof.energy_and_gradients(o["B"], o["H"], sysm.orbitals(11), sysm.gamma(12), o["pm"], o["vnn"])
+    assert abs(Eg.item() - ref["E"]) < GATE
+    assert np.max(np.abs(gg_.cpu().numpy() - ref["g"])) < GATE
+
+    # the replayed graph reads the arrays: new contents in place, same pointers
+    C2, gam2 = sysm.orbitals(21), sysm.gamma(22)
+    C.copy_(_t(C2))
+    gam.copy_(_t(gam2))
+    torch.cuda.synchronize()
+    for _ in range(2):
+        _eval(nof, cg, C, gam, Eg, gg_, ggg)
+        _eval(nof, cd, C, gam, Ed, gd, ggd)
+        same()
+    ref2 = pnof.energy_and_gradients(o["B"], o["H"], C2, gam2, o["pm"], o["vnn"])
+    assert abs(Eg.item() - ref2["E"]) < GATE
+    assert np.max(np.abs(ggg.cpu().numpy() - ref2["g_gamma"])) < GATE
+
+    # new output pointers: a direct call, then a new recording; the old outputs stay untouched
+    old = Eg.clone()
+    Eg2, gg2, ggg2 = out()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        _eval(nof, cg, C, gam, Eg2, gg2, ggg2)
+        assert Eg2.item() == Ed.item()
+        assert torch.equal(gg2, gd) and torch.equal(ggg2, ggd)
+    assert Eg.item() == old.item()
+
+    # energy only (no gradient outputs), and back to the first pointers
+    E3 = torch.empty(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(3):
+        cg.energy_grad(C, gam, E3, grad=False)
+        cg.stream.synchronize()
+        assert E3.item() == Ed.item()
+    for _ in range(2):
+        _eval(nof, cg, C, gam, Eg, gg_, ggg)
+        same()
+
+    # profiling switches recording off; the results do not change
+    cg.profile(True)
+    for _ in range(3):
+        _eval(nof, cg, C, gam, Eg, gg_, ggg)
+        same()
+    assert cg.profile_read()[1] == 3
+    cg.profile(False)
+    cg.close()
+    cd.close()
+
