@@ -68,7 +68,7 @@ typedef struct {
     int graphs;       /* 1 (default): when nof_energy_grad is called twice in a row with the same
                          pointers, the second call records its kernels as a CUDA graph on the
                          context's stream, and later calls with those pointers replay it (one
-                         launch instead of about 30). The graph reads the arrays, so their contents
+                         launch instead of about 20). The graph reads the arrays, so their contents
                          may change between calls. 0: every call launches its kernels one by one.
                          No graph is recorded on the legacy default stream (stream 0), while
                          nof_profile is on, or while the caller is capturing the stream. */
