@@ -154,11 +154,15 @@ __device__ __forceinline__ float2 levels_to_df(const float* S, int e) {
     }
     const float hi = h + err;
     const float lo = err - (hi - h);
-    if (e >= -126 && e <= 127) {
-        const float sc = __int_as_float((e + 127) << 23);
-        return make_float2(hi * sc, lo * sc);
-    }
-    return make_float2(ldexpf(hi, e), ldexpf(lo, e));
+    // x 2^e as (x 2^{e1}) 2^{e2} with e1 = floor(e / 2), e2 = e - e1: once e is clamped to
+    // [-252, 252] both factors are normal powers of two. The intermediate lies between x and the
+    // result, so every normal result is exact, the same as with ldexpf (only subnormal results
+    // can round twice); beyond the clamp every nonzero result is 0 or infinite either way.
+    // No branch and no library call per element.
+    e = min(max(e, -252), 252);
+    const int e1 = e >> 1, e2 = e - e1;
+    const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
+    return make_float2((hi * s1) * s2, (lo * s1) * s2);
 }
 
 // sum of two double-floats
