@@ -212,10 +212,16 @@ int nof_create(nof_ctx** out, const nof_options* opt, void* stream) {
         return r;
     }
     cudaError_t e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    cudaEvent_t* evs[5] = {&c->ev_fork, &c->ev_join, &c->ev_s0, &c->ev_sT, &c->ev_s1};
+    for (cudaEvent_t* ev : evs)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    int prio_low = 0, prio_high = 0;  // the side stream takes the lowest priority
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_low);
     if (e != cudaSuccess) {
-        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        for (cudaEvent_t* ev : evs)
+            if (*ev) cudaEventDestroy(*ev);
+        if (c->side) cudaStreamDestroy(c->side);
         cudaFree(c->status);
         delete c;
         return nof_cuda_fail(e, "context set-up", __FILE__, __LINE__);
@@ -230,8 +236,10 @@ int nof_destroy(nof_ctx* c) {
     prof_clear(c);
     delete static_cast<EventPairs*>(c->prof_events);
     free_system(c);
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamSynchronize(c->side);
+    for (cudaEvent_t ev : {c->ev_fork, c->ev_join, c->ev_s0, c->ev_sT, c->ev_s1})
+        if (ev) cudaEventDestroy(ev);
+    if (c->side) cudaStreamDestroy(c->side);
     dfree(c->status);
     delete c;
     return NOF_OK;
@@ -513,8 +521,12 @@ int nof_jk(nof_ctx* c, const double* C, double* J, double* K) {
 static int energy_grad_body(nof_ctx* c, const double* C, const double* gamma, double* E, double* g_orb,
                             double* g_gamma) {
     const bool grad = g_orb || g_gamma;
-    NOF_TRY(run_jk(c, C));
-    NOF_TRY(run_grad(c, C, gamma, grad));
+    if (c->opt.precision == NOF_PREC_SPLIT_BF16) {
+        NOF_TRY(fast_eval(c, C, gamma, grad));
+    } else {
+        NOF_TRY(run_jk(c, C));
+        NOF_TRY(run_grad(c, C, gamma, grad));
+    }
     if (E) NOF_CUDA(cudaMemcpyAsync(E, c->E, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     if (g_orb)
         NOF_CUDA(cudaMemcpyAsync(g_orb, c->gorb, (size_t)c->nbf * c->nbf * sizeof(double),

@@ -574,7 +574,11 @@ int fast_tiles(nof_ctx* c, int* out) {
     return NOF_OK;
 }
 
-int fast_jk(nof_ctx* c, const double* C) {
+namespace {
+
+// J/K chain from C on the context's stream: C digits, GEMM1 (T = B C), the digits of T,
+// GEMM2 (b = C^T T), then J and K. When t_written is not null it is recorded once T is written.
+int jk_chain(nof_ctx* c, const double* C, cudaEvent_t t_written) {
     FastState* f = c->fast;
     const int n = f->n, X = f->X, a = f->a, ap = f->ap;
     cudaStream_t st = c->stream;
@@ -586,6 +590,7 @@ int fast_jk(nof_ctx* c, const double* C) {
     NOF_TRY(prof_begin(c, "k_digit_gemm (half transform T = B C, tcgen05)"));
     NOF_TRY(digit_gemm_run(f->g1, st));
     NOF_TRY(prof_end(c));
+    if (t_written) NOF_CUDA(cudaEventRecord(t_written, st));
     k_T2_digits<<<nblk((long long)X * f->katK * ap * 2), 256, 0, st>>>(f->Tdf, f->colT, X, n, ap, f->katK, f->nd,
                                                                        f->Td2, f->e2);
     NOF_LAUNCH_CHECK();
@@ -597,22 +602,28 @@ int fast_jk(nof_ctx* c, const double* C) {
     k_reduce_parts<<<dim3(nblk((long long)a * a * 32), 2), 256, 0, st>>>(f->Jpart, c->J, f->Kpart, c->K, nchunk,
                                                                         a * a);
     NOF_LAUNCH_CHECK();
-    return pnof_hpp(c, C);
+    return NOF_OK;
 }
 
-int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad) {
+// Digits of T for the Lagrangian contraction (GEMM3's M side), on stream s.
+int t3_digits(nof_ctx* c, cudaStream_t s) {
+    FastState* f = c->fast;
+    k_T3_digits<<<dim3(f->nkp, (f->n + 7) / 8), 128, 0, s>>>(f->Tdf, f->X, f->n, f->ap, f->nkp, f->nd, f->Td3,
+                                                             f->epT);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+// The gradient after E: D = A d, the digits of W, GEMM3 (Lambda' = sum_P T^P W^P), Lambda,
+// lambda = C^T Lambda and g. The digits of T (t3_digits) must be written before.
+int grad_tail(nof_ctx* c, const double* C) {
     FastState* f = c->fast;
     const int n = f->n, X = f->X, a = f->a, ap = f->ap;
     cudaStream_t st = c->stream;
-    NOF_TRY(pnof_occupations(c, gamma));  // also A and B as double-floats
-    NOF_TRY(pnof_energy(c));              // E and dE/dgamma
-    if (!want_grad) return NOF_OK;
     k_D_df<<<dim3((a + 15) / 16, (X + 15) / 16), 256, 0, st>>>(f->Adf, f->ddf, X, a, f->Ddf);
     NOF_LAUNCH_CHECK();
     k_W_digits<<<dim3(f->nkp, (a + 7) / 8), 128, 0, st>>>(f->bdf, f->Bcdf, f->Ddf, X, a, ap, f->nkp, f->nd, f->bn3,
                                                           f->Wd3, f->epW);
-    NOF_LAUNCH_CHECK();
-    k_T3_digits<<<dim3(f->nkp, (n + 7) / 8), 128, 0, st>>>(f->Tdf, X, n, ap, f->nkp, f->nd, f->Td3, f->epT);
     NOF_LAUNCH_CHECK();
     NOF_TRY(digit_gemm_run(f->g3, st));
     const long long na = (long long)n * a;
@@ -620,4 +631,43 @@ int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad) 
                                                                    c->Lam);
     NOF_LAUNCH_CHECK();
     return pnof_lambda_and_g(c, C, c->gorb, true);
+}
+
+}  // namespace
+
+int fast_jk(nof_ctx* c, const double* C) {
+    NOF_TRY(jk_chain(c, C, nullptr));
+    return pnof_hpp(c, C);
+}
+
+int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad) {
+    NOF_TRY(pnof_occupations(c, gamma));  // also A and B as double-floats
+    NOF_TRY(pnof_energy(c));              // E and dE/dgamma
+    if (!want_grad) return NOF_OK;
+    NOF_TRY(t3_digits(c, c->stream));
+    return grad_tail(c, C);
+}
+
+// One evaluation (fast_jk + fast_grad) as two streams. The J/K chain runs on the context's
+// stream. A low-priority side stream, forked from it, computes what does not depend on J and K:
+// the occupations and PNOF coefficients from gamma, H C and h_pp from C, and, once GEMM1 has
+// written T, the digits of T for the Lagrangian. The side stream joins before the energy. Every
+// buffer the side stream writes is read only after the join, and the fork orders it after the
+// previous evaluation's reads. No FP64 GEMM shares the split-K scratch with H C during that time.
+int fast_eval(nof_ctx* c, const double* C, const double* gamma, bool want_grad) {
+    cudaStream_t st = c->stream, sd = c->side;
+    NOF_CUDA(cudaEventRecord(c->ev_s0, st));
+    NOF_CUDA(cudaStreamWaitEvent(sd, c->ev_s0, 0));
+    NOF_TRY(pnof_occupations(c, gamma, sd));
+    NOF_TRY(pnof_hpp(c, C, sd));
+    NOF_TRY(jk_chain(c, C, want_grad ? c->ev_sT : nullptr));
+    if (want_grad) {
+        NOF_CUDA(cudaStreamWaitEvent(sd, c->ev_sT, 0));
+        NOF_TRY(t3_digits(c, sd));
+    }
+    NOF_CUDA(cudaEventRecord(c->ev_s1, sd));
+    NOF_CUDA(cudaStreamWaitEvent(st, c->ev_s1, 0));
+    NOF_TRY(pnof_energy(c));
+    if (!want_grad) return NOF_OK;
+    return grad_tail(c, C);
 }

@@ -66,6 +66,10 @@ struct nof_ctx {
     FastState* fast;
     // fork/join events of the batched evaluation
     cudaEvent_t ev_fork, ev_join;
+    // low-priority side stream of a split-precision evaluation (the work that does not depend on
+    // the J/K chain) with its fork, T-written and join events
+    cudaStream_t side;
+    cudaEvent_t ev_s0, ev_sT, ev_s1;
     // recorded graph of nof_energy_grad (option graphs): the argument pointers it was recorded
     // with, the kernel launches it holds, the pointers of the last direct call, and a flag set when
     // recording failed once (the context then launches directly)
@@ -126,10 +130,12 @@ int build_integrals(nof_ctx* c, double* M3 /* [X][n][n] */, double* V2 /* [X][X]
 // PNOF kernels (pnof.cu)
 int plain_jk(nof_ctx* c, const double* C);
 int plain_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad);
-int pnof_occupations(nof_ctx* c, const double* gamma);
+int pnof_occupations(nof_ctx* c, const double* gamma, cudaStream_t st);
+inline int pnof_occupations(nof_ctx* c, const double* gamma) { return pnof_occupations(c, gamma, c->stream); }
 int pnof_energy(nof_ctx* c);
 int pnof_gamma_grad(nof_ctx* c, double* out);
-int pnof_hpp(nof_ctx* c, const double* C);
+int pnof_hpp(nof_ctx* c, const double* C, cudaStream_t st);
+inline int pnof_hpp(nof_ctx* c, const double* C) { return pnof_hpp(c, C, c->stream); }
 int pnof_lambda_and_g(nof_ctx* c, const double* C, double* g_out, bool assembled);
 int pnof_jk_from_b(nof_ctx* c);
 int pnof_build_W(nof_ctx* c);
@@ -141,6 +147,7 @@ int fast_prepare(nof_ctx* c);
 int fast_release(nof_ctx* c);
 int fast_jk(nof_ctx* c, const double* C);
 int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad);
+int fast_eval(nof_ctx* c, const double* C, const double* gamma, bool want_grad);
 int fast_get_B(nof_ctx* c, double* B);
 int fast_tiles(nof_ctx* c, int* out);
 // split path: double-float copies of A and B for k_coefficients (null outside the split path)

@@ -285,20 +285,20 @@ __global__ void k_step_stats(const double* E, const double* g, const double* lam
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
-int pnof_occupations(nof_ctx* c, const double* gamma) {
-    k_occupations<<<nblk(c->npair, 128), 128, 0, c->stream>>>(gamma, c->npair, c->opt.ncwo, c->s,
+int pnof_occupations(nof_ctx* c, const double* gamma, cudaStream_t st) {
+    k_occupations<<<nblk(c->npair, 128), 128, 0, st>>>(gamma, c->npair, c->opt.ncwo, c->s,
                                                                c->t, c->ds, c->dt);
     NOF_LAUNCH_CHECK();
     long long aa = (long long)c->nact * c->nact;
     float2 *Adf = nullptr, *Bcdf = nullptr;
     fast_coefficient_buffers(c, &Adf, &Bcdf);
-    k_coefficients<<<nblk(aa), 256, 0, c->stream>>>(c->s, c->t, c->pair, c->slot, c->nact,
+    k_coefficients<<<nblk(aa), 256, 0, st>>>(c->s, c->t, c->pair, c->slot, c->nact,
                                                     c->opt.ipnof, c->occ, c->A, c->Bc, Adf, Bcdf);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
 
-int pnof_hpp(nof_ctx* c, const double* C) {
+int pnof_hpp(nof_ctx* c, const double* C, cudaStream_t st) {
     const int n = c->nbf, a = c->nact;
     Gemm64 g;  // HC = H C_a
     g.M = n; g.N = a; g.K = n;
@@ -306,8 +306,8 @@ int pnof_hpp(nof_ctx* c, const double* C) {
     g.B = C; g.sBn = 1; g.sBk0 = n;
     g.C = c->HC; g.sCm = a; g.sCn = 1;
     g.work = c->gwork; g.work_cap = c->gwork_cap;
-    NOF_TRY(gemm64(g, c->stream));
-    k_hpp<<<nblk((long long)a * 32), 256, 0, c->stream>>>(C, c->HC, n, a, c->hpp);
+    NOF_TRY(gemm64(g, st));
+    k_hpp<<<nblk((long long)a * 32), 256, 0, st>>>(C, c->HC, n, a, c->hpp);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
