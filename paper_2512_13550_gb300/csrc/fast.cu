@@ -283,7 +283,13 @@ __global__ void __launch_bounds__(256) k_JK_partial(const float2* bdf, int X, in
 // out[i] = sum_b part[b][i], one warp per output, fixed order (lane-strided then a fixed tree);
 // blockIdx.y selects one of two (part, out) pairs.
 __global__ void k_reduce_parts(const double* part0, double* out0, const double* part1, double* out1, int nparts,
-                               int cnt) {
+                               int cnt, unsigned* clear, long long nclear) {
+    // clear[] (GEMM1's column maxima, read for the last time by k_T2_digits) back to zero for
+    // the next evaluation
+    const long long nthr = (long long)gridDim.x * gridDim.y * blockDim.x;
+    for (long long k = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x; k < nclear;
+         k += nthr)
+        clear[k] = 0u;
     int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (i >= cnt) return;
     const double* part = blockIdx.y ? part1 : part0;
@@ -548,6 +554,9 @@ int fast_prepare(nof_ctx* c) {
         f->g3 = cand[best];
         f->bn3 = bnk[best];
     }
+    // GEMM1's column maxima start at zero (the autotuner's launches wrote them); from then on
+    // k_reduce_parts clears them after each use
+    NOF_CUDA(cudaMemsetAsync(f->colT, 0, sizeof(unsigned) * X * ap, st));
     NOF_CUDA(cudaStreamSynchronize(st));
     return NOF_OK;
 }
@@ -586,7 +595,6 @@ int jk_chain(nof_ctx* c, const double* C, cudaEvent_t t_written) {
     k_digits_f64<<<nblk((long long)a * 32), 256, 0, st>>>(C, 1, n, a, n, f->nd, f->bn1, f->katK, f->Cd1, f->eC,
                                                           f->bn2, f->Cd2);
     NOF_LAUNCH_CHECK();
-    NOF_CUDA(cudaMemsetAsync(f->colT, 0, sizeof(unsigned) * X * ap, st));
     NOF_TRY(prof_begin(c, "k_digit_gemm (half transform T = B C, tcgen05)"));
     NOF_TRY(digit_gemm_run(f->g1, st));
     NOF_TRY(prof_end(c));
@@ -600,7 +608,7 @@ int jk_chain(nof_ctx* c, const double* C, cudaEvent_t t_written) {
                                                                       f->ddf);
     NOF_LAUNCH_CHECK();
     k_reduce_parts<<<dim3(nblk((long long)a * a * 32), 2), 256, 0, st>>>(f->Jpart, c->J, f->Kpart, c->K, nchunk,
-                                                                        a * a);
+                                                                        a * a, f->colT, (long long)X * ap);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
@@ -642,18 +650,20 @@ int fast_jk(nof_ctx* c, const double* C) {
 
 int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad) {
     NOF_TRY(pnof_occupations(c, gamma));  // also A and B as double-floats
-    NOF_TRY(pnof_energy(c));              // E and dE/dgamma
+    NOF_TRY(pnof_energy(c, c->stream));   // E and dE/dgamma
     if (!want_grad) return NOF_OK;
     NOF_TRY(t3_digits(c, c->stream));
     return grad_tail(c, C);
 }
 
-// One evaluation (fast_jk + fast_grad) as two streams. The J/K chain runs on the context's
-// stream. A low-priority side stream, forked from it, computes what does not depend on J and K:
-// the occupations and PNOF coefficients from gamma, H C and h_pp from C, and, once GEMM1 has
-// written T, the digits of T for the Lagrangian. The side stream joins before the energy. Every
-// buffer the side stream writes is read only after the join, and the fork orders it after the
-// previous evaluation's reads. No FP64 GEMM shares the split-K scratch with H C during that time.
+// One evaluation (fast_jk + fast_grad) as two streams. The J/K chain and the gradient run on
+// the context's stream. A low-priority side stream, forked from it, computes what the chain does
+// not need: the occupations and PNOF coefficients from gamma, H C and h_pp from C, the digits of
+// T for the Lagrangian once GEMM1 has written T, and, once J and K exist, E and dE/dgamma. The
+// gradient waits for the side stream's inputs before D = A d; the evaluation ends when both
+// streams are done. Every buffer the side stream writes is read only after the matching wait,
+// the fork orders it after the previous evaluation, and no FP64 GEMM shares the split-K scratch
+// with H C.
 int fast_eval(nof_ctx* c, const double* C, const double* gamma, bool want_grad) {
     cudaStream_t st = c->stream, sd = c->side;
     NOF_CUDA(cudaEventRecord(c->ev_s0, st));
@@ -661,13 +671,19 @@ int fast_eval(nof_ctx* c, const double* C, const double* gamma, bool want_grad) 
     NOF_TRY(pnof_occupations(c, gamma, sd));
     NOF_TRY(pnof_hpp(c, C, sd));
     NOF_TRY(jk_chain(c, C, want_grad ? c->ev_sT : nullptr));
+    NOF_CUDA(cudaEventRecord(c->ev_sJ, st));
     if (want_grad) {
         NOF_CUDA(cudaStreamWaitEvent(sd, c->ev_sT, 0));
         NOF_TRY(t3_digits(c, sd));
+        NOF_CUDA(cudaEventRecord(c->ev_s1, sd));
     }
-    NOF_CUDA(cudaEventRecord(c->ev_s1, sd));
-    NOF_CUDA(cudaStreamWaitEvent(st, c->ev_s1, 0));
-    NOF_TRY(pnof_energy(c));
-    if (!want_grad) return NOF_OK;
-    return grad_tail(c, C);
+    NOF_CUDA(cudaStreamWaitEvent(sd, c->ev_sJ, 0));
+    NOF_TRY(pnof_energy(c, sd));
+    NOF_CUDA(cudaEventRecord(c->ev_s2, sd));
+    if (want_grad) {
+        NOF_CUDA(cudaStreamWaitEvent(st, c->ev_s1, 0));
+        NOF_TRY(grad_tail(c, C));
+    }
+    NOF_CUDA(cudaStreamWaitEvent(st, c->ev_s2, 0));
+    return NOF_OK;
 }

@@ -66,10 +66,10 @@ struct nof_ctx {
     FastState* fast;
     // fork/join events of the batched evaluation
     cudaEvent_t ev_fork, ev_join;
-    // low-priority side stream of a split-precision evaluation (the work that does not depend on
-    // the J/K chain) with its fork, T-written and join events
+    // low-priority side stream of a split-precision evaluation (the work off the J/K chain) and
+    // its events: fork, T written, J and K written, side inputs of the gradient ready, energy done
     cudaStream_t side;
-    cudaEvent_t ev_s0, ev_sT, ev_s1;
+    cudaEvent_t ev_s0, ev_sT, ev_sJ, ev_s1, ev_s2;
     // recorded graph of nof_energy_grad (option graphs): the argument pointers it was recorded
     // with, the kernel launches it holds, the pointers of the last direct call, and a flag set when
     // recording failed once (the context then launches directly)
@@ -132,8 +132,8 @@ int plain_jk(nof_ctx* c, const double* C);
 int plain_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad);
 int pnof_occupations(nof_ctx* c, const double* gamma, cudaStream_t st);
 inline int pnof_occupations(nof_ctx* c, const double* gamma) { return pnof_occupations(c, gamma, c->stream); }
-int pnof_energy(nof_ctx* c);
-int pnof_gamma_grad(nof_ctx* c, double* out);
+int pnof_energy(nof_ctx* c, cudaStream_t st);
+int pnof_gamma_grad(nof_ctx* c, double* out, cudaStream_t st);
 int pnof_hpp(nof_ctx* c, const double* C, cudaStream_t st);
 inline int pnof_hpp(nof_ctx* c, const double* C) { return pnof_hpp(c, C, c->stream); }
 int pnof_lambda_and_g(nof_ctx* c, const double* C, double* g_out, bool assembled);

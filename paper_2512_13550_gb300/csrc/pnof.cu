@@ -313,20 +313,20 @@ int pnof_hpp(nof_ctx* c, const double* C, cudaStream_t st) {
 }
 
 // E (into c->E) and dE/dgamma (into out) from J, K, h_pp and the occupations of pnof_occupations.
-int pnof_gamma_grad(nof_ctx* c, double* out) {
+int pnof_gamma_grad(nof_ctx* c, double* out, cudaStream_t st) {
     const int a = c->nact;
-    k_dE_parts<<<nblk((long long)a * 32), 256, 0, c->stream>>>(c->s, c->t, c->pair, c->slot, c->hpp,
+    k_dE_parts<<<nblk((long long)a * 32), 256, 0, st>>>(c->s, c->t, c->pair, c->slot, c->hpp,
                                                                c->J, c->K, c->A, c->Bc, a, c->opt.ipnof,
                                                                c->part);
     NOF_LAUNCH_CHECK();
-    k_gamma_chain<<<nblk(c->ngamma, 128), 128, 0, c->stream>>>(c->s, c->t, c->ds, c->dt, c->slot,
+    k_gamma_chain<<<nblk(c->ngamma, 128), 128, 0, st>>>(c->s, c->t, c->ds, c->dt, c->slot,
                                                                 c->part, c->npair, c->opt.ncwo, a, c->vnn,
                                                                 c->E, out);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
 
-int pnof_energy(nof_ctx* c) { return pnof_gamma_grad(c, c->ggam); }
+int pnof_energy(nof_ctx* c, cudaStream_t st) { return pnof_gamma_grad(c, c->ggam, st); }
 
 int pnof_jk_from_b(nof_ctx* c) {
     const int X = c->naux, a = c->nact;
@@ -411,7 +411,7 @@ int plain_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad)
     const int n = c->nbf, X = c->naux, a = c->nact;
     cudaStream_t st = c->stream;
     NOF_TRY(pnof_occupations(c, gamma));
-    NOF_TRY(pnof_energy(c));
+    NOF_TRY(pnof_energy(c, c->stream));
     if (!want_grad) return NOF_OK;
     NOF_TRY(pnof_build_W(c));
     {   // Lam[mu][p] = sum_{P,r} T[P][mu][r] W[P][r][p]  (composite contraction index)
@@ -438,7 +438,7 @@ int pnof_on_update(nof_ctx* c, double* gamma) {
     cudaStream_t st = c->stream;
     for (int it = 0; it < c->opt.on_iters; ++it) {
         NOF_TRY(pnof_occupations(c, gamma));
-        NOF_TRY(pnof_gamma_grad(c, c->ggam));
+        NOF_TRY(pnof_gamma_grad(c, c->ggam, c->stream));
         k_gamma_descent<<<nblk(c->ngamma, 128), 128, 0, st>>>(gamma, c->ggam, c->opt.on_lr, c->ngamma);
         NOF_LAUNCH_CHECK();
     }
