@@ -344,22 +344,21 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
             const int er = (g.outf && row < g.M) ? g.erow[row] - kOff : 0;
             for (int part = 0; part < nparts && ok; ++part, ++unit) {
                 const int b = unit % NB, use = unit / NB;
+                const long long gp = (long long)(kc * g.katoms) / g.apart + part;  // part index along K
+                // this part's exponents, loaded before the wait so that their latency overlaps it:
+                // the row's, and one column's per lane (column col0 + lane, cw <= 32), handed to the
+                // other lanes by shuffles
+                const int erp = (partsc && row < g.M) ? g.epA[gp * g.M + row] - kOff : er;
+                const int* ec = partsc ? g.epB + gp * g.Nvalid : g.ecol;
+                const int ecl = ints ? 0 : ec[min(col0 + lane, g.Nvalid - 1)];
                 ok = mbar_wait(tfull0 + 8 * b, use & 1, g.status);
                 if (!ok) break;
                 tc_fence_after();
-                const long long gp = (long long)(kc * g.katoms) / g.apart + part;  // part index along K
-                const int erp = (partsc && row < g.M) ? g.epA[gp * g.M + row] - kOff : er;
                 const uint32_t acc = tmem + lane_base + (uint32_t)(b * ND * BN);
-                const int* ec = partsc ? g.epB + gp * g.Nvalid : g.ecol;
                 for (int c0 = 0; c0 < cw; c0 += 16) {
                     const int w = min(16, cw - c0);  // 16, or 8 for the last chunk of a 24-column half
                     float v[ND][16];
                     const uint32_t col = (uint32_t)(cbeg + c0);
-                    int ecj[16];  // column exponents, fetched before the TMEM reads to overlap them
-                    if (!ints) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) ecj[j] = ec[min(col0 + c0 + j, g.Nvalid - 1)];
-                    }
                     if (w == 16) {
 #pragma unroll
                         for (int l = 0; l < ND; ++l) tmem_ld16(acc + (uint32_t)(l * BN) + col, v[l]);
@@ -384,7 +383,7 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             if (j >= w) break;
-                            const int e = erp + ecj[j];
+                            const int e = erp + __shfl_sync(0xffffffffu, ecl, c0 + j);
                             float S[ND];
 #pragma unroll
                             for (int l = 0; l < ND; ++l) S[l] = v[l][j];
