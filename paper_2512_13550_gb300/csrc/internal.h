@@ -114,6 +114,11 @@ int gemm64(const Gemm64& g, cudaStream_t st);
 // Same contraction with the K range split over `splits` CTAs; partial results are written
 // to work[split][M][N] then summed in a fixed order into C (deterministic).
 int gemm64_splitk(const Gemm64& g, int splits, double* work, cudaStream_t st);
+// The small-output route of gemm64 in two steps: the K split it takes (0 when it does not take
+// that route), and the launch that writes the split's partial products to g.work[split][M][N]
+// (summed afterwards in split order, like gemm64 does).
+int gemm64_small_splits(const Gemm64& g);
+int gemm64_small_partials(const Gemm64& g, int splits, cudaStream_t st);
 
 int cholesky_inverse(double* V, double* Linv, int X, int* status, cudaStream_t st);
 int newton_schulz_invsqrt(const double* S, double* Xout, double* w1, double* w2, double* w3,

@@ -372,25 +372,34 @@ int sym_eig(double* A, double* Vwork, double* Vout, double* w, int n, int* sweep
     return NOF_OK;
 }
 
+int gemm64_small_splits(const Gemm64& g) {
+    if (g.M <= 0 || g.N <= 0 || g.batch != 1 || !g.work) return 0;
+    const long long tiles = (long long)((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM);
+    if (tiles >= 304) return 0;
+    // small output: 16x16 tiles and a K split so that about 600 CTAs share the work
+    const long long t16 = (long long)((g.N + 15) / 16) * ((g.M + 15) / 16);
+    long long splits = (608 + t16 - 1) / t16;
+    const long long maxs = (g.K + 15) / 16;
+    if (splits > maxs) splits = maxs;
+    const long long cap = (long long)(g.work_cap / ((size_t)g.M * g.N));
+    if (splits > cap) splits = cap;
+    return splits >= 1 ? (int)splits : 0;
+}
+
+int gemm64_small_partials(const Gemm64& g, int splits, cudaStream_t st) {
+    dim3 grid((g.N + 15) / 16, (g.M + 15) / 16, (unsigned)splits);
+    k_gemm64_small<<<grid, 256, 0, st>>>(g, splits, g.work);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
 int gemm64(const Gemm64& g, cudaStream_t st) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return NOF_OK;
-    long long tiles = (long long)((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM) * g.batch;
-    if (g.work && g.batch == 1 && tiles < 304) {
-        // small output: 16x16 tiles and a K split so that about 600 CTAs share the work
-        long long t16 = (long long)((g.N + 15) / 16) * ((g.M + 15) / 16);
-        long long splits = (608 + t16 - 1) / t16;
-        long long maxs = (g.K + 15) / 16;
-        if (splits > maxs) splits = maxs;
-        long long cap = (long long)(g.work_cap / ((size_t)g.M * g.N));
-        if (splits > cap) splits = cap;
-        if (splits >= 1 && cap >= 1) {
-            dim3 grid((g.N + 15) / 16, (g.M + 15) / 16, (unsigned)splits);
-            k_gemm64_small<<<grid, 256, 0, st>>>(g, (int)splits, g.work);
-            NOF_LAUNCH_CHECK();
-            k_splitk_reduce<<<blocks_for((long long)g.M * g.N), 256, 0, st>>>(g, (int)splits, g.work);
-            NOF_LAUNCH_CHECK();
-            return NOF_OK;
-        }
+    if (const int splits = gemm64_small_splits(g)) {
+        NOF_TRY(gemm64_small_partials(g, splits, st));
+        k_splitk_reduce<<<blocks_for((long long)g.M * g.N), 256, 0, st>>>(g, splits, g.work);
+        NOF_LAUNCH_CHECK();
+        return NOF_OK;
     }
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
     if (grid.y > 65535u || grid.z > 65535u) {

@@ -166,6 +166,24 @@ __global__ void k_lambda_assemble(const double* HC, const double* occ, int n, in
 }
 
 // g = 4 (lambda - lambda^T); lambda holds columns p < a (the others are zero and never stored).
+// lambda = sum over the K split of the partial products work[split][n][a] (in split order, as
+// gemm64 sums them) into lam (columns p < a, leading dimension n), and the orbital gradient
+// g_pq = 4 (lambda_pq - lambda_qp) from the same sums, in one pass.
+__global__ void k_reduce_gradient(const double* work, int splits, int n, int a, double* lam, double* g) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * n) return;
+    const int p = (int)(idx / n), q = (int)(idx % n);
+    const long long MN = (long long)n * a;
+    double lpq = 0.0, lqp = 0.0;
+    if (q < a) {
+        for (int s = 0; s < splits; ++s) lpq += work[s * MN + (long long)p * a + q];
+        lam[idx] = lpq;
+    }
+    if (p < a)
+        for (int s = 0; s < splits; ++s) lqp += work[s * MN + (long long)q * a + p];
+    g[idx] = 4.0 * (lpq - lqp);
+}
+
 __global__ void k_orbital_gradient(const double* lam, int n, int a, double* g) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= (long long)n * n) return;
@@ -372,6 +390,13 @@ int pnof_lambda_and_g(nof_ctx* c, const double* C, double* g_out, bool assembled
     g.B = c->Lam; g.sBn = 1; g.sBk0 = a;
     g.C = c->lam; g.sCm = n; g.sCn = 1;
     g.work = c->gwork; g.work_cap = c->gwork_cap;
+    if (const int splits = gemm64_small_splits(g)) {
+        // split-K partials, then lambda and g from them in one kernel
+        NOF_TRY(gemm64_small_partials(g, splits, c->stream));
+        k_reduce_gradient<<<nblk((long long)n * n), 256, 0, c->stream>>>(c->gwork, splits, n, a, c->lam, g_out);
+        NOF_LAUNCH_CHECK();
+        return NOF_OK;
+    }
     NOF_TRY(gemm64(g, c->stream));
     k_orbital_gradient<<<nblk((long long)n * n), 256, 0, c->stream>>>(c->lam, n, a, g_out);
     NOF_LAUNCH_CHECK();
