@@ -586,7 +586,8 @@ int fast_tiles(nof_ctx* c, int* out) {
 namespace {
 
 // J/K chain from C on the context's stream: C digits, GEMM1 (T = B C), the digits of T,
-// GEMM2 (b = C^T T), then J and K. When t_written is not null it is recorded once T is written.
+// GEMM2 (b = C^T T), then the chunk partials of J and K and the contiguous diagonal d. When
+// t_written is not null it is recorded once T is written. jk_sum adds the partials into J and K.
 int jk_chain(nof_ctx* c, const double* C, cudaEvent_t t_written) {
     FastState* f = c->fast;
     const int n = f->n, X = f->X, a = f->a, ap = f->ap;
@@ -607,8 +608,16 @@ int jk_chain(nof_ctx* c, const double* C, cudaEvent_t t_written) {
     k_JK_partial<<<dim3(nblk((long long)a * a), nchunk), 256, 0, st>>>(f->bdf, X, a, ap, nchunk, f->Jpart, f->Kpart,
                                                                       f->ddf);
     NOF_LAUNCH_CHECK();
-    k_reduce_parts<<<dim3(nblk((long long)a * a * 32), 2), 256, 0, st>>>(f->Jpart, c->J, f->Kpart, c->K, nchunk,
-                                                                        a * a, f->colT, (long long)X * ap);
+    return NOF_OK;
+}
+
+// J and K from the chunk partials of jk_chain (fixed order), on stream s; also clears GEMM1's
+// column maxima for the next evaluation.
+int jk_sum(nof_ctx* c, cudaStream_t s) {
+    FastState* f = c->fast;
+    const int a = f->a;
+    k_reduce_parts<<<dim3(nblk((long long)a * a * 32), 2), 256, 0, s>>>(f->Jpart, c->J, f->Kpart, c->K, f->nchunkJK,
+                                                                       a * a, f->colT, (long long)f->X * f->ap);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
@@ -645,6 +654,7 @@ int grad_tail(nof_ctx* c, const double* C) {
 
 int fast_jk(nof_ctx* c, const double* C) {
     NOF_TRY(jk_chain(c, C, nullptr));
+    NOF_TRY(jk_sum(c, c->stream));
     return pnof_hpp(c, C);
 }
 
@@ -659,7 +669,8 @@ int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad) 
 // One evaluation (fast_jk + fast_grad) as two streams. The J/K chain and the gradient run on
 // the context's stream. A low-priority side stream, forked from it, computes what the chain does
 // not need: the occupations and PNOF coefficients from gamma, H C and h_pp from C, the digits of
-// T for the Lagrangian once GEMM1 has written T, and, once J and K exist, E and dE/dgamma. The
+// T for the Lagrangian once GEMM1 has written T, and, once the J/K partials exist, J and K
+// themselves, E and dE/dgamma. The
 // gradient waits for the side stream's inputs before D = A d; the evaluation ends when both
 // streams are done. Every buffer the side stream writes is read only after the matching wait,
 // the fork orders it after the previous evaluation, and no FP64 GEMM shares the split-K scratch
@@ -678,6 +689,7 @@ int fast_eval(nof_ctx* c, const double* C, const double* gamma, bool want_grad) 
         NOF_CUDA(cudaEventRecord(c->ev_s1, sd));
     }
     NOF_CUDA(cudaStreamWaitEvent(sd, c->ev_sJ, 0));
+    NOF_TRY(jk_sum(c, sd));
     NOF_TRY(pnof_energy(c, sd));
     NOF_CUDA(cudaEventRecord(c->ev_s2, sd));
     if (want_grad) {
