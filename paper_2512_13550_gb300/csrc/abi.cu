@@ -212,7 +212,7 @@ int nof_create(nof_ctx** out, const nof_options* opt, void* stream) {
         return r;
     }
     cudaError_t e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
-    cudaEvent_t* evs[7] = {&c->ev_fork, &c->ev_join, &c->ev_s0, &c->ev_sT, &c->ev_sJ, &c->ev_s1, &c->ev_s2};
+    cudaEvent_t* evs[8] = {&c->ev_fork, &c->ev_join, &c->ev_s0, &c->ev_sO, &c->ev_sT, &c->ev_sJ, &c->ev_s1, &c->ev_s2};
     for (cudaEvent_t* ev : evs)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     int prio_low = 0, prio_high = 0;  // the side stream takes the lowest priority
@@ -237,7 +237,7 @@ int nof_destroy(nof_ctx* c) {
     delete static_cast<EventPairs*>(c->prof_events);
     free_system(c);
     if (c->side) cudaStreamSynchronize(c->side);
-    for (cudaEvent_t ev : {c->ev_fork, c->ev_join, c->ev_s0, c->ev_sT, c->ev_sJ, c->ev_s1, c->ev_s2})
+    for (cudaEvent_t ev : {c->ev_fork, c->ev_join, c->ev_s0, c->ev_sO, c->ev_sT, c->ev_sJ, c->ev_s1, c->ev_s2})
         if (ev) cudaEventDestroy(ev);
     if (c->side) cudaStreamDestroy(c->side);
     dfree(c->status);

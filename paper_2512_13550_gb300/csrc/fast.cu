@@ -34,7 +34,6 @@ struct FastState {
     uint16_t* Td2; int* e2;     // [4][katK][X ap][16], per (P, p)
     uint16_t* Td3; int* epT;    // [4][8 nkp][n][16] (K = (P, r) padded to nkp parts), scale per (part, mu)
     float2* bdf;                // [X ap][ap] b^P_{p q} as double-floats
-    float2* ddf;                // [X][a] d^P_p = b^P_pp (written by the J/K partial sums)
     float2* Ddf;                // [X][a] D^P_p = sum_r A_pr d^P_r
     uint16_t* Wd3; int* epW;    // rows p (tiles of bn3), K = (P, r); scale per (part, p)
     float2 *Adf, *Bcdf;         // [a][a]
@@ -262,7 +261,7 @@ __device__ __forceinline__ float2 b_val(const float2* bdf, int ap, int P, int p,
 // with d^P_p = b^P_pp read from b (and stored contiguously in d); grid (ceil(a*a/256), nchunk);
 // partials [chunk][a*a] as FP64.
 __global__ void __launch_bounds__(256) k_JK_partial(const float2* bdf, int X, int a, int ap, int nchunk,
-                                                    double* Jpart, double* Kpart, float2* d) {
+                                                    double* Jpart, double* Kpart) {
     const int idx = blockIdx.x * 256 + threadIdx.x;
     const int aa = a * a;
     if (idx >= aa) return;
@@ -274,7 +273,6 @@ __global__ void __launch_bounds__(256) k_JK_partial(const float2* bdf, int X, in
         float2 b = b_val(bdf, ap, P, p, q);
         kacc = df_add(kacc, df_mul(b, b));
         jacc = df_add(jacc, df_mul(b_val(bdf, ap, P, p, p), b_val(bdf, ap, P, q, q)));
-        if (p == q) d[(long long)P * a + p] = b;  // the diagonal, contiguous for D = d A
     }
     Jpart[(long long)blockIdx.y * aa + idx] = df_to_double(jacc);
     Kpart[(long long)blockIdx.y * aa + idx] = df_to_double(kacc);
@@ -302,14 +300,14 @@ __global__ void k_reduce_parts(const double* part0, double* out0, const double* 
 
 // D^P_p = sum_r d^P_r A_rp (A symmetric): a double-float GEMM D [X][a] = d [X][a] A [a][a] in
 // 16 x 16 output tiles, one output per thread, K = r staged through shared memory 16 at a time.
-__global__ void __launch_bounds__(256) k_D_df(const float2* Adf, const float2* d, int X, int a, float2* D) {
+__global__ void __launch_bounds__(256) k_D_df(const float2* Adf, const float2* bdf, int X, int a, int ap, float2* D) {
     __shared__ float2 ds[16][17];  // [P][r]
     __shared__ float2 as[16][17];  // [r][p]
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int P0 = blockIdx.y * 16, p0 = blockIdx.x * 16;
     float2 acc = make_float2(0.f, 0.f);
     for (int r0 = 0; r0 < a; r0 += 16) {
-        ds[ty][tx] = (P0 + ty < X && r0 + tx < a) ? d[(long long)(P0 + ty) * a + r0 + tx] : make_float2(0.f, 0.f);
+        ds[ty][tx] = (P0 + ty < X && r0 + tx < a) ? b_val(bdf, ap, P0 + ty, r0 + tx, r0 + tx) : make_float2(0.f, 0.f);
         as[ty][tx] = (r0 + ty < a && p0 + tx < a) ? Adf[(long long)(r0 + ty) * a + p0 + tx] : make_float2(0.f, 0.f);
         __syncthreads();
 #pragma unroll
@@ -414,7 +412,7 @@ int fast_release(nof_ctx* c) {
     FastState* f = c->fast;
     if (!f) return NOF_OK;
     ffree(f->Bd); ffree(f->eB); ffree(f->Cd1); ffree(f->Cd2); ffree(f->eC); ffree(f->Tdf); ffree(f->colT);
-    ffree(f->Td2); ffree(f->e2); ffree(f->Td3); ffree(f->epT); ffree(f->bdf); ffree(f->ddf); ffree(f->Ddf);
+    ffree(f->Td2); ffree(f->e2); ffree(f->Td3); ffree(f->epT); ffree(f->bdf); ffree(f->Ddf);
     ffree(f->Wd3); ffree(f->epW); ffree(f->Adf); ffree(f->Bcdf); ffree(f->Jpart); ffree(f->Lpart);
     ffree(f->Kpart);
     delete f;
@@ -465,7 +463,7 @@ int fast_prepare(nof_ctx* c) {
     NOF_TRY(falloc(&f->Td2, nTd2)); NOF_TRY(falloc(&f->e2, rows2));
     NOF_TRY(falloc(&f->Td3, nTd3)); NOF_TRY(falloc(&f->epT, (size_t)nkp * n));
     NOF_TRY(falloc(&f->bdf, rows2 * ap));
-    NOF_TRY(falloc(&f->ddf, (size_t)X * a)); NOF_TRY(falloc(&f->Ddf, (size_t)X * a));
+    NOF_TRY(falloc(&f->Ddf, (size_t)X * a));
     NOF_TRY(falloc(&f->Wd3, nWd3)); NOF_TRY(falloc(&f->epW, (size_t)nkp * a));
     NOF_TRY(falloc(&f->Adf, (size_t)a * a)); NOF_TRY(falloc(&f->Bcdf, (size_t)a * a));
     NOF_TRY(falloc(&f->Jpart, (size_t)f->nchunkJK * a * a)); NOF_TRY(falloc(&f->Kpart, (size_t)f->nchunkJK * a * a));
@@ -585,10 +583,9 @@ int fast_tiles(nof_ctx* c, int* out) {
 
 namespace {
 
-// J/K chain from C on the context's stream: C digits, GEMM1 (T = B C), the digits of T,
-// GEMM2 (b = C^T T), then the chunk partials of J and K and the contiguous diagonal d. When
-// t_written is not null it is recorded once T is written. jk_sum adds the partials into J and K.
-int jk_chain(nof_ctx* c, const double* C, cudaEvent_t t_written) {
+// b = C^T B C from C on the context's stream: C digits, GEMM1 (T = B C), the digits of T,
+// GEMM2 (b = C^T T). When t_written is not null it is recorded once T is written.
+int b_chain(nof_ctx* c, const double* C, cudaEvent_t t_written) {
     FastState* f = c->fast;
     const int n = f->n, X = f->X, a = f->a, ap = f->ap;
     cudaStream_t st = c->stream;
@@ -603,20 +600,18 @@ int jk_chain(nof_ctx* c, const double* C, cudaEvent_t t_written) {
     k_T2_digits<<<nblk((long long)X * f->katK * ap * 2), 256, 0, st>>>(f->Tdf, f->colT, X, n, ap, f->katK, f->nd,
                                                                        f->Td2, f->e2);
     NOF_LAUNCH_CHECK();
-    NOF_TRY(digit_gemm_run(f->g2, st));
-    const int nchunk = f->nchunkJK;
-    k_JK_partial<<<dim3(nblk((long long)a * a), nchunk), 256, 0, st>>>(f->bdf, X, a, ap, nchunk, f->Jpart, f->Kpart,
-                                                                      f->ddf);
-    NOF_LAUNCH_CHECK();
-    return NOF_OK;
+    return digit_gemm_run(f->g2, st);
 }
 
-// J and K from the chunk partials of jk_chain (fixed order), on stream s; also clears GEMM1's
-// column maxima for the next evaluation.
-int jk_sum(nof_ctx* c, cudaStream_t s) {
+// J and K from b on stream s: chunk partials, then their fixed-order sum. The sum also clears
+// GEMM1's column maxima (last read by the digits of T) for the next evaluation.
+int jk_from_b(nof_ctx* c, cudaStream_t s) {
     FastState* f = c->fast;
-    const int a = f->a;
-    k_reduce_parts<<<dim3(nblk((long long)a * a * 32), 2), 256, 0, s>>>(f->Jpart, c->J, f->Kpart, c->K, f->nchunkJK,
+    const int a = f->a, nchunk = f->nchunkJK;
+    k_JK_partial<<<dim3(nblk((long long)a * a), nchunk), 256, 0, s>>>(f->bdf, f->X, a, f->ap, nchunk, f->Jpart,
+                                                                     f->Kpart);
+    NOF_LAUNCH_CHECK();
+    k_reduce_parts<<<dim3(nblk((long long)a * a * 32), 2), 256, 0, s>>>(f->Jpart, c->J, f->Kpart, c->K, nchunk,
                                                                        a * a, f->colT, (long long)f->X * f->ap);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
@@ -631,21 +626,29 @@ int t3_digits(nof_ctx* c, cudaStream_t s) {
     return NOF_OK;
 }
 
-// The gradient after E: D = A d, the digits of W, GEMM3 (Lambda' = sum_P T^P W^P), Lambda,
-// lambda = C^T Lambda and g. The digits of T (t3_digits) must be written before.
-int grad_tail(nof_ctx* c, const double* C) {
+// D^P = A d^P (d^P the diagonal of b^P) and the digits of W (GEMM3's N side), on the context's
+// stream.
+int w_digits(nof_ctx* c) {
     FastState* f = c->fast;
-    const int n = f->n, X = f->X, a = f->a, ap = f->ap;
+    const int X = f->X, a = f->a, ap = f->ap;
     cudaStream_t st = c->stream;
-    k_D_df<<<dim3((a + 15) / 16, (X + 15) / 16), 256, 0, st>>>(f->Adf, f->ddf, X, a, f->Ddf);
+    k_D_df<<<dim3((a + 15) / 16, (X + 15) / 16), 256, 0, st>>>(f->Adf, f->bdf, X, a, ap, f->Ddf);
     NOF_LAUNCH_CHECK();
     k_W_digits<<<dim3(f->nkp, (a + 7) / 8), 128, 0, st>>>(f->bdf, f->Bcdf, f->Ddf, X, a, ap, f->nkp, f->nd, f->bn3,
                                                           f->Wd3, f->epW);
     NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+// GEMM3 (Lambda' = sum_P T^P W^P), Lambda, lambda = C^T Lambda and g, on the context's stream,
+// once the digits of T and W, H C and the occupations are written.
+int lagrangian(nof_ctx* c, const double* C) {
+    FastState* f = c->fast;
+    cudaStream_t st = c->stream;
     NOF_TRY(digit_gemm_run(f->g3, st));
-    const long long na = (long long)n * a;
-    k_lambda_from_parts<<<(unsigned)((na + 31) / 32), 256, 0, st>>>(f->Lpart, f->g3.g.kchunks, na, c->HC, c->occ, a,
-                                                                   c->Lam);
+    const long long na = (long long)f->n * f->a;
+    k_lambda_from_parts<<<(unsigned)((na + 31) / 32), 256, 0, st>>>(f->Lpart, f->g3.g.kchunks, na, c->HC, c->occ,
+                                                                   f->a, c->Lam);
     NOF_LAUNCH_CHECK();
     return pnof_lambda_and_g(c, C, c->gorb, true);
 }
@@ -653,8 +656,8 @@ int grad_tail(nof_ctx* c, const double* C) {
 }  // namespace
 
 int fast_jk(nof_ctx* c, const double* C) {
-    NOF_TRY(jk_chain(c, C, nullptr));
-    NOF_TRY(jk_sum(c, c->stream));
+    NOF_TRY(b_chain(c, C, nullptr));
+    NOF_TRY(jk_from_b(c, c->stream));
     return pnof_hpp(c, C);
 }
 
@@ -663,25 +666,29 @@ int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad) 
     NOF_TRY(pnof_energy(c, c->stream));   // E and dE/dgamma
     if (!want_grad) return NOF_OK;
     NOF_TRY(t3_digits(c, c->stream));
-    return grad_tail(c, C);
+    NOF_TRY(w_digits(c));
+    return lagrangian(c, C);
 }
 
-// One evaluation (fast_jk + fast_grad) as two streams. The J/K chain and the gradient run on
-// the context's stream. A low-priority side stream, forked from it, computes what the chain does
-// not need: the occupations and PNOF coefficients from gamma, H C and h_pp from C, the digits of
-// T for the Lagrangian once GEMM1 has written T, and, once the J/K partials exist, J and K
-// themselves, E and dE/dgamma. The
-// gradient waits for the side stream's inputs before D = A d; the evaluation ends when both
-// streams are done. Every buffer the side stream writes is read only after the matching wait,
-// the fork orders it after the previous evaluation, and no FP64 GEMM shares the split-K scratch
-// with H C.
+// One evaluation (fast_jk + fast_grad) on two streams. The context's stream runs the chain the
+// gradient needs: C digits, GEMM1, the digits of T, GEMM2, D = A d and the digits of W, GEMM3,
+// Lambda, lambda and g. A low-priority side stream, forked from it by an event, runs the rest:
+// - the occupations and PNOF coefficients from gamma (the chain waits for them before D);
+// - H C and h_pp from C, and the GEMM3 digits of T once GEMM1 has written T (the chain waits
+//   for these before GEMM3);
+// - once GEMM2 has written b: the J/K partials, J and K, then E and dE/dgamma (the evaluation
+//   ends when these are done too).
+// Every buffer the side stream writes is read only after the matching wait. The fork orders
+// the side stream after the previous evaluation. No FP64 GEMM shares the split-K scratch with
+// H C while it runs.
 int fast_eval(nof_ctx* c, const double* C, const double* gamma, bool want_grad) {
     cudaStream_t st = c->stream, sd = c->side;
     NOF_CUDA(cudaEventRecord(c->ev_s0, st));
     NOF_CUDA(cudaStreamWaitEvent(sd, c->ev_s0, 0));
     NOF_TRY(pnof_occupations(c, gamma, sd));
+    NOF_CUDA(cudaEventRecord(c->ev_sO, sd));
     NOF_TRY(pnof_hpp(c, C, sd));
-    NOF_TRY(jk_chain(c, C, want_grad ? c->ev_sT : nullptr));
+    NOF_TRY(b_chain(c, C, want_grad ? c->ev_sT : nullptr));
     NOF_CUDA(cudaEventRecord(c->ev_sJ, st));
     if (want_grad) {
         NOF_CUDA(cudaStreamWaitEvent(sd, c->ev_sT, 0));
@@ -689,12 +696,14 @@ int fast_eval(nof_ctx* c, const double* C, const double* gamma, bool want_grad) 
         NOF_CUDA(cudaEventRecord(c->ev_s1, sd));
     }
     NOF_CUDA(cudaStreamWaitEvent(sd, c->ev_sJ, 0));
-    NOF_TRY(jk_sum(c, sd));
+    NOF_TRY(jk_from_b(c, sd));
     NOF_TRY(pnof_energy(c, sd));
     NOF_CUDA(cudaEventRecord(c->ev_s2, sd));
     if (want_grad) {
+        NOF_CUDA(cudaStreamWaitEvent(st, c->ev_sO, 0));
+        NOF_TRY(w_digits(c));
         NOF_CUDA(cudaStreamWaitEvent(st, c->ev_s1, 0));
-        NOF_TRY(grad_tail(c, C));
+        NOF_TRY(lagrangian(c, C));
     }
     NOF_CUDA(cudaStreamWaitEvent(st, c->ev_s2, 0));
     return NOF_OK;

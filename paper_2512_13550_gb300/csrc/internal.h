@@ -66,10 +66,11 @@ struct nof_ctx {
     FastState* fast;
     // fork/join events of the batched evaluation
     cudaEvent_t ev_fork, ev_join;
-    // low-priority side stream of a split-precision evaluation (the work off the J/K chain) and
-    // its events: fork, T written, J and K written, side inputs of the gradient ready, energy done
+    // low-priority side stream of a split-precision evaluation (the work off the gradient's
+    // chain) and its events: fork, occupations written, T written, b written, the rest of the
+    // gradient's side inputs written, J/K and energy done
     cudaStream_t side;
-    cudaEvent_t ev_s0, ev_sT, ev_sJ, ev_s1, ev_s2;
+    cudaEvent_t ev_s0, ev_sO, ev_sT, ev_sJ, ev_s1, ev_s2;
     // recorded graph of nof_energy_grad (option graphs): the argument pointers it was recorded
     // with, the kernel launches it holds, the pointers of the last direct call, and a flag set when
     // recording failed once (the context then launches directly)
