@@ -12,6 +12,9 @@ Follows DoNOF 2.0 (arXiv 2512.13550):
         n_{p_i} = h_g cos^2 gamma_{p_1} ... cos^2 gamma_{p_{i-1}} sin^2 gamma_{p_i}  (i < N_g),
         n_{p_{N_g}} = h_g cos^2 gamma_{p_1} ... cos^2 gamma_{p_{N_g - 1}}.
     Angles are stored slot-major: gamma[i * npair + g], slot 0 = gamma_g, slot i = gamma_{p_i}.
+  * softmax mapping (same subsection, ISOFTMAX = 1), N_g variables per subspace, one per weak
+    orbital, stored slot-major too: gamma[k * npair + g] = gamma_{p_{k+1}};
+        n_g = 1 / (1 + sum_k exp(gamma_{p_k})),   n_{p_i} = n_g exp(gamma_{p_i}).
   * JKL-only energy (Eq. PNOF), with L = K for real orbitals:
         E = 2 sum_p n_p h_pp + sum_pq A_pq J_pq - sum_pq B_pq K_pq + V_nn.
     The paper defers A and B to the PNOF5/PNOF7 publications. Reading (spin-restricted
@@ -41,11 +44,15 @@ import numpy as np
 
 
 class PairMap:
-    """Closed-shell pairing structure for N electrons, N_g weak orbitals per subspace."""
+    """Closed-shell pairing structure for N electrons, N_g weak orbitals per subspace, and the
+    ON mapping (isoftmax = 0: trigonometric, 1: softmax)."""
 
-    def __init__(self, nelec: int, ncwo: int, nbf: int):
+    def __init__(self, nelec: int, ncwo: int, nbf: int, isoftmax: int = 0):
         if nelec % 2 or nelec <= 0:
             raise ValueError("closed-shell singlet needs an even, positive electron count")
+        if isoftmax not in (0, 1):
+            raise ValueError("isoftmax must be 0 (trigonometric) or 1 (softmax)")
+        self.isoftmax = isoftmax
         self.npair = nelec // 2
         self.ncwo = ncwo
         self.nact = self.npair * (ncwo + 1)
@@ -73,9 +80,12 @@ def _sgn(x):
 
 
 def occupations(gamma, pm: PairMap):
-    """sqrt(n_p), sqrt(1 - n_p) and their derivatives with respect to every gamma.
+    """sqrt(n_p), sqrt(1 - n_p) and their derivatives with respect to every gamma, for the
+    mapping pm.isoftmax selects.
 
     Returns s, t (length nact) and ds, dt (nact x ngamma)."""
+    if pm.isoftmax:
+        return occupations_softmax(gamma, pm)
     gamma = np.asarray(gamma, np.float64)
     a, ng, P, Ng = pm.nact, pm.ngamma, pm.npair, pm.ncwo
     s = np.zeros(a); t = np.zeros(a)
@@ -108,6 +118,39 @@ def occupations(gamma, pm: PairMap):
                 ds[p, km] += dfm * others
             t[p] = np.sqrt(1.0 - val * val)
             dt[p, :] = -val * ds[p, :] / t[p]
+    return s, t, ds, dt
+
+
+def occupations_softmax(gamma, pm: PairMap):
+    """The softmax mapping: per subspace g with variables x_k = gamma_{p_k} (k = 1..N_g),
+        Z = 1 + sum_k exp(x_k),  n_g = 1 / Z,  n_{p_i} = n_g exp(x_i),
+    so that sqrt(n_g) = Z^{-1/2}, sqrt(n_{p_i}) = exp(x_i / 2) Z^{-1/2}, and
+        d sqrt(n_q) / d x_j = sqrt(n_q) (delta_{q, p_j} - n_{p_j}) / 2
+    for every orbital q of the subspace (with delta_{g, p_j} = 0). sqrt(1 - n) follows from
+    1 - n_g = sum_k n_{p_k} and 1 - n_{p_i} = n_g + sum_{k != i} n_{p_k}, and
+    d sqrt(1 - n) = -sqrt(n) d sqrt(n) / sqrt(1 - n).
+
+    Returns s, t (length nact) and ds, dt (nact x ngamma) as occupations() does."""
+    gamma = np.asarray(gamma, np.float64)
+    a, ng, P, Ng = pm.nact, pm.ngamma, pm.npair, pm.ncwo
+    s = np.zeros(a); t = np.zeros(a)
+    ds = np.zeros((a, ng)); dt = np.zeros((a, ng))
+    for g in range(P):
+        keys = [k * P + g for k in range(Ng)]              # gamma index of x_{k+1}
+        ex = np.array([np.exp(gamma[k]) for k in keys])
+        Z = 1.0 + ex.sum()
+        n_g = 1.0 / Z
+        n_w = n_g * ex                                     # n_{p_1} .. n_{p_Ng}
+        orbs = [g] + [pm.weak_orbital(g, i) for i in range(1, Ng + 1)]
+        occ = [n_g] + list(n_w)
+        rest = [n_w.sum()] + [n_g + n_w.sum() - n_w[i] for i in range(Ng)]  # 1 - n, per orbital
+        for m, q in enumerate(orbs):
+            s[q] = np.sqrt(occ[m])
+            t[q] = np.sqrt(rest[m])
+            for j, kj in enumerate(keys):
+                own = 1.0 if m == j + 1 else 0.0
+                ds[q, kj] = 0.5 * s[q] * (own - n_w[j])
+                dt[q, kj] = -s[q] * ds[q, kj] / t[q]
     return s, t, ds, dt
 
 

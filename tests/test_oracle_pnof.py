@@ -164,3 +164,89 @@ def test_gradients_match_finite_differences(ipnof, ncwo):
         e = np.zeros(pm.ngamma); e[k] = 1e-5
         fd = (pnof.energy(B, H, C, gam + e, pm, vnn, ipnof) - pnof.energy(B, H, C, gam - e, pm, vnn, ipnof)) / 2e-5
         assert abs(fd - r["g_gamma"][k]) < 1e-7 * max(1.0, abs(fd))
+
+
+# ---------------------------------------------------------------------------------------
+# softmax ON mapping (isoftmax = 1)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("ncwo", [1, 2, 3])
+def test_softmax_sum_rule_and_trace(ncwo):
+    npair = 3
+    pm = pnof.PairMap(2 * npair, ncwo, npair * (ncwo + 1) + 2, isoftmax=1)
+    for seed in range(5):
+        gam = inputs.uniform(200 + seed, pm.ngamma, -4.0, 4.0)
+        n = pnof.occupation_numbers(gam, pm)
+        assert np.all(n > 0) and np.all(n < 1)
+        for g in range(npair):
+            assert abs(np.sum(n[pm.pair == g]) - 1.0) < 1e-15
+        assert abs(2 * np.sum(n) - 2 * npair) < 1e-13
+        s, t, _, _ = pnof.occupations(gam, pm)
+        np.testing.assert_allclose(s * s + t * t, 1.0, atol=1e-15)
+
+
+def test_softmax_one_weak_orbital_is_the_logistic_function():
+    """N_g = 1: n_p = exp(x) / (1 + exp(x)) is the logistic function (scipy's expit), n_g its
+    complement; a positive variable puts more than half the pair's electrons in the weak orbital
+    (the mapping does not keep n_g >= 1/2)."""
+    from scipy.special import expit
+    pm = pnof.PairMap(6, 1, 6, isoftmax=1)
+    gam = np.array([-2.5, 0.0, 1.75])
+    n = pnof.occupation_numbers(gam, pm)
+    for g in range(3):
+        p = pm.weak_orbital(g, 1)
+        assert abs(n[p] - expit(gam[g])) < 1e-15
+        assert abs(n[g] - expit(-gam[g])) < 1e-15
+    assert n[2] < 0.5
+
+
+@pytest.mark.parametrize("ncwo", [1, 2])
+def test_softmax_and_trigonometric_agree_at_equal_occupations(ncwo):
+    """Both mappings reach the same occupations (x_i = ln(n_{p_i} / n_g)); the energy and the
+    orbital gradient then agree, and dE/dx follows from dE/dgamma_trig through the Jacobians:
+    dE/dn restricted to the sum-rule surface is the same whichever variables describe it."""
+    natom = 4
+    nb = 2 if ncwo == 2 else 1
+    orb = inputs.Basis(inputs.even_tempered_shells(0.3, 4.0, nb)) if nb == 2 else None
+    basis = (orb, inputs.basis_h4()[1]) if orb is not None else None
+    S, H, B, vnn = _system(natom, basis=basis)
+    n_bf = S.shape[0]
+    C = reference.orthonormal_orbitals(S, inputs.random_orthogonal(n_bf, 5))
+    pm_t = pnof.PairMap(natom, ncwo, n_bf)
+    pm_s = pnof.PairMap(natom, ncwo, n_bf, isoftmax=1)
+    gam_t = inputs.random_gamma(pm_t.ngamma, 6)
+    n = pnof.occupation_numbers(gam_t, pm_t)
+    x = np.zeros(pm_s.ngamma)
+    for g in range(pm_s.npair):
+        for i in range(1, ncwo + 1):
+            x[(i - 1) * pm_s.npair + g] = np.log(n[pm_s.weak_orbital(g, i)] / n[g])
+    np.testing.assert_allclose(pnof.occupation_numbers(x, pm_s), n, atol=1e-15)
+    rt = pnof.energy_and_gradients(B, H, C, gam_t, pm_t, vnn)
+    rs = pnof.energy_and_gradients(B, H, C, x, pm_s, vnn)
+    assert abs(rt["E"] - rs["E"]) < 1e-12
+    np.testing.assert_allclose(rs["g"], rt["g"], atol=1e-12)
+    # chain rule check: with dn/dgamma (trig) and dn/dx (softmax) both spanning the sum-rule
+    # tangent space, dE/dx = (dn/dx)^T G and dE/dgamma = (dn/dgamma)^T G for one G
+    def dn(gam, pm):
+        s, _, ds, _ = pnof.occupations(gam, pm)
+        return 2.0 * s[:, None] * ds
+    Jt, Js = dn(gam_t, pm_t), dn(x, pm_s)
+    G, *_ = np.linalg.lstsq(Jt.T, rt["g_gamma"], rcond=None)
+    np.testing.assert_allclose(Js.T @ G, rs["g_gamma"], atol=1e-10)
+
+
+@pytest.mark.parametrize("ipnof,ncwo", [(7, 1), (5, 1), (7, 2)])
+def test_softmax_gradients_match_finite_differences(ipnof, ncwo):
+    natom = 4
+    nb = 2 if ncwo == 2 else 1
+    orb = inputs.Basis(inputs.even_tempered_shells(0.3, 4.0, nb)) if nb == 2 else None
+    basis = (orb, inputs.basis_h4()[1]) if orb is not None else None
+    S, H, B, vnn = _system(natom, basis=basis)
+    n = S.shape[0]
+    C = reference.orthonormal_orbitals(S, inputs.random_orthogonal(n, 0))
+    pm = pnof.PairMap(natom, ncwo, n, isoftmax=1)
+    gam = inputs.uniform(7, pm.ngamma, -2.0, 1.0)
+    r = pnof.energy_and_gradients(B, H, C, gam, pm, vnn, ipnof)
+    for k in range(pm.ngamma):
+        e = np.zeros(pm.ngamma); e[k] = 1e-5
+        fd = (pnof.energy(B, H, C, gam + e, pm, vnn, ipnof) - pnof.energy(B, H, C, gam - e, pm, vnn, ipnof)) / 2e-5
+        assert abs(fd - r["g_gamma"][k]) < 1e-7 * max(1.0, abs(fd))
