@@ -21,7 +21,9 @@
  *    energy to be the functional's.
  *  - Orbitals 0 .. nact-1 are active (nonzero occupation); nact = (N/2)(ncwo + 1).
  *  - gamma has ngamma = (N/2) ncwo entries stored slot-major: gamma[i * (N/2) + g] is the
- *    angle of slot i of subspace g (slot 0 = the strong orbital's gamma_g).
+ *    variable of slot i of subspace g. Trigonometric mapping: slot 0 is the strong orbital's
+ *    angle gamma_g and slot i the angle of weak orbital p_i. Softmax mapping: slot i is the
+ *    variable of weak orbital p_{i+1}.
  *  - The library owns only its workspaces (allocated by nof_build_B, freed by nof_destroy).
  */
 #ifndef NOF_H
@@ -53,7 +55,9 @@ typedef struct nof_ctx nof_ctx;
  * exists (IPNOF, ISOFTMAX, NCWO = N_g of Eq. OmegaG). */
 typedef struct {
     int ipnof;        /* 7 = PNOF7 (default), 5 = PNOF5 */
-    int isoftmax;     /* 0 = trigonometric mapping (the only mapping implemented) */
+    int isoftmax;     /* ON mapping (Occupation Number Optimization subsection): 0 = trigonometric
+                         (default); 1 = softmax, n_g = 1 / (1 + sum_k exp(gamma_{p_k})) and
+                         n_{p_i} = n_g exp(gamma_{p_i}), which does not keep n_g >= 1/2 */
     int ncwo;         /* N_g, weak orbitals per subspace (>= 1) */
     int precision;    /* NOF_PREC_FP64 or NOF_PREC_SPLIT_BF16 */
     int on_iters;     /* steepest-descent ON steps per nof_step (default 20) */

@@ -188,8 +188,8 @@ int nof_create(nof_ctx** out, const nof_options* opt, void* stream) {
         nof_set_error("nof_create: ipnof must be 5 or 7");
         return NOF_EINVAL;
     }
-    if (o.isoftmax != 0) {
-        nof_set_error("nof_create: only the trigonometric mapping (isoftmax = 0) is implemented");
+    if (o.isoftmax != 0 && o.isoftmax != 1) {
+        nof_set_error("nof_create: isoftmax must be 0 (trigonometric mapping) or 1 (softmax mapping)");
         return NOF_EINVAL;
     }
     if (o.ncwo < 1 || o.on_iters < 0 ||

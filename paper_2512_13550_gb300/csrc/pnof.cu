@@ -78,6 +78,40 @@ __global__ void k_occupations(const double* gamma, int npair, int ncwo, double* 
     }
 }
 
+// Softmax mapping (isoftmax = 1), same outputs as k_occupations. Subspace g has the variables
+// x_k = gamma[k * npair + g] (k < ncwo), x_k belonging to the weak orbital p_{k+1}:
+//   Z = 1 + sum_k exp(x_k),  n_g = 1 / Z,  n_{p_i} = exp(x_{i-1}) / Z,
+//   d sqrt(n_q) / d x_k = sqrt(n_q) ([q = p_{k+1}] - n_{p_{k+1}}) / 2,
+//   d sqrt(1 - n_q) = -sqrt(n_q) d sqrt(n_q) / sqrt(1 - n_q).
+// The exponentials are taken relative to max(0, max_k x_k) so that none overflows, and 1 - n_q
+// is summed from the other orbitals' weights (no cancellation).
+__global__ void k_occupations_softmax(const double* gamma, int npair, int ncwo, double* s, double* t,
+                                      double* ds, double* dt) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npair) return;
+    double m = 0.0;
+    for (int k = 0; k < ncwo; ++k) m = fmax(m, gamma[k * npair + g]);
+    const double w0 = exp(-m);  // weight of the strong orbital, exp(0 - m)
+    double z = w0;
+    for (int k = 0; k < ncwo; ++k) z += exp(gamma[k * npair + g] - m);
+    for (int q = 0; q <= ncwo; ++q) {  // q = 0: the strong orbital g; q = i: the weak orbital p_i
+        const int p = q == 0 ? g : npair + (q - 1) * npair + (npair - 1 - g);
+        const double w = q == 0 ? w0 : exp(gamma[(q - 1) * npair + g] - m);
+        double rest = q == 0 ? 0.0 : w0;
+        for (int k = 0; k < ncwo; ++k)
+            if (k + 1 != q) rest += exp(gamma[k * npair + g] - m);
+        const double sp = sqrt(w / z), tp = sqrt(rest / z);
+        s[p] = sp;
+        t[p] = tp;
+        for (int k = 0; k < ncwo; ++k) {
+            const double nk = exp(gamma[k * npair + g] - m) / z;
+            const double d = 0.5 * sp * ((q == k + 1 ? 1.0 : 0.0) - nk);
+            ds[p * ncwo + k] = d;
+            dt[p * ncwo + k] = -sp * d / tp;
+        }
+    }
+}
+
 // A and B of Eq. PNOF for every active pair (p, q); optionally also as double-floats (hi, lo) for
 // the split path (Adf, Bcdf may be null).
 __global__ void k_coefficients(const double* s, const double* t, const int* pair, const int* slot,
@@ -304,8 +338,12 @@ __global__ void k_step_stats(const double* E, const double* g, const double* lam
 
 // ---------------------------------------------------------------------------------------
 int pnof_occupations(nof_ctx* c, const double* gamma, cudaStream_t st) {
-    k_occupations<<<nblk(c->npair, 128), 128, 0, st>>>(gamma, c->npair, c->opt.ncwo, c->s,
-                                                               c->t, c->ds, c->dt);
+    if (c->opt.isoftmax)
+        k_occupations_softmax<<<nblk(c->npair, 128), 128, 0, st>>>(gamma, c->npair, c->opt.ncwo, c->s, c->t,
+                                                                     c->ds, c->dt);
+    else
+        k_occupations<<<nblk(c->npair, 128), 128, 0, st>>>(gamma, c->npair, c->opt.ncwo, c->s, c->t, c->ds,
+                                                             c->dt);
     NOF_LAUNCH_CHECK();
     long long aa = (long long)c->nact * c->nact;
     float2 *Adf = nullptr, *Bcdf = nullptr;

@@ -78,3 +78,5 @@ def test_bad_options_rejected(lib):
     assert o.graphs == 1
     o.graphs = 2
     assert lib.nof_create(ctypes.byref(h), ctypes.byref(o), None) == nof.NOF_EINVAL
+    o.graphs, o.isoftmax = 1, 2  # 0 = trigonometric, 1 = softmax mapping
+    assert lib.nof_create(ctypes.byref(h), ctypes.byref(o), None) == nof.NOF_EINVAL
