@@ -167,6 +167,51 @@ int nof_energy_grad_batch(nof_ctx* const* ctxs, int count, const double* const* 
                           const double* const* gamma, double* const* E, double* const* g_orb,
                           double* const* g_gamma, void* stream);
 
+/* ---- Finite-field polarizability and hyperpolarizabilities (NLOPs subsection) ------------ */
+
+/* Static electric field F (atomic units, host array of 3: x, y, z), the EVEC input of the
+ * NLOPs subsection. The Hamiltonian gains -mu.F with mu = -sum_i r_i + sum_A Z_A R_A: every
+ * later evaluation and step of the context uses h + F.<mu|r|nu> and V_nn - F.sum_A Z_A R_A.
+ * F = (0, 0, 0) restores the field-free values exactly. The dipole integrals (s Gaussians: the
+ * product-centre times the overlap of each primitive pair) are computed on the first call.
+ * Stream-ordered. Errors: NOF_EINVAL (null pointer, non-finite F), NOF_ESTATE (before
+ * nof_build_B), NOF_ENOMEM. */
+int nof_set_field(nof_ctx* ctx, const double* F);
+
+/* Dipole moment of the state (C, gamma): mu_k = -2 sum_p n_p <phi_p|r_k|phi_p> + sum_A Z_A R_A,k
+ * for k = x, y, z: the expectation value with the one-particle density matrix of the
+ * functional, which is diagonal in the natural orbitals (NLOPs subsection). C, gamma: device
+ * arrays as for nof_energy_grad; mu: device array of 3 doubles. Stream-ordered; the sums run in
+ * a fixed order. Errors: NOF_EINVAL, NOF_ESTATE, NOF_ENOMEM. */
+int nof_dipole(nof_ctx* ctx, const double* C, const double* gamma, double* mu);
+
+/* Centred finite differences of order h^2 at the dyadic steps h_k = step 2^{k-1},
+ * k = 1 .. npoint (NLOPs subsection), from dipoles at the 2 npoint + 3 distinct fields in the
+ * order 0, h_1 .. h_{npoint+1}, -h_1 .. -h_{npoint+1} (2 h_k = h_{k+1}):
+ *   alpha(h) = (mu(h) - mu(-h)) / (2h),  beta(h) = (mu(h) - 2 mu(0) + mu(-h)) / h^2,
+ *   gamma(h) = (mu(2h) - 2 mu(h) + 2 mu(-h) - mu(-2h)) / (2 h^3).
+ * Host arrays: mu [2 npoint + 3], alpha, beta, gamma [npoint]. No device work.
+ * Errors: NOF_EINVAL (null pointer, npoint < 1, step <= 0). */
+int nof_field_differences(const double* mu, int npoint, double step, double* alpha, double* beta,
+                          double* gamma);
+
+/* Romberg-Richardson triangle with p = 2 (NLOPs subsection) of D[k-1] = D(h_k), k = 1 .. npoint:
+ * R(k, 1) = D(h_k), R(k, j) = R(k, j-1) + (R(k, j-1) - R(k+1, j-1)) / (4^{j-1} - 1) for
+ * k <= npoint - j + 1. R: host [npoint][npoint], R[(k-1) npoint + j-1] = R(k, j), the other
+ * entries NaN. Selection: over every column j and vertical pair (k, k+1) of it, the smallest
+ * Delta = |R(k+1, j) - R(k, j)| selects R(k, j+1); equal Deltas go to the smaller |value|.
+ * best[0] = value, best[1] = Delta; sel[0], sel[1] = the selecting pair's k and j (1-based).
+ * With npoint = 1, best = (D[0], NaN) and sel = (1, 1). No device work.
+ * Errors: NOF_EINVAL (null pointer, npoint < 1). */
+int nof_romberg(const double* D, int npoint, double* R, double* best, int* sel);
+
+/* nof_step on `count` contexts at once (the independent field instances of the finite-field
+ * workload): each context on its own stream, forked from `stream` and joined back with events,
+ * as nof_energy_grad_batch. Host arrays of `count` pointers: C, gamma, m, v, out (device) and
+ * t (host step counters). Errors: as nof_step; NOF_EINVAL for a bad count or a null entry. */
+int nof_step_batch(nof_ctx* const* ctxs, int count, double* const* C, double* const* gamma,
+                   double* const* m, double* const* v, int* const* t, double* const* out, void* stream);
+
 /* Learned starting guess (no counterpart in the paper, which only notes that its Python version
  * suits machine-learning workflows): a perceptron x (F) -> relu (H) -> relu (H) -> y (O) in FP32
  * with hand-written kernels. Parameters theta are packed W1 [H][F], b1 [H], W2 [H][H], b2 [H],

@@ -82,6 +82,11 @@ SIGNATURES = {
                                          _P, _P]),
     "nof_mlp_adam": (ctypes.c_int, [ctypes.c_longlong, _P, _P, _P, _P, ctypes.c_int, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
+    "nof_set_field": (ctypes.c_int, [_P, _P]),
+    "nof_dipole": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nof_field_differences": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, _P, _P, _P]),
+    "nof_romberg": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+    "nof_step_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]),
     "nof_last_error": (ctypes.c_char_p, []),
 }
 
@@ -124,6 +129,42 @@ def bench_digit_gemm(M: int, N: int, bn: int, nd: int, katoms: int, chunk_atoms:
     chunk = chunk_atoms if chunk_atoms > 0 else katoms
     _check(load_library().nof_bench_digit_gemm(M, N, bn, nd, katoms, chunk, mode, reps, ctypes.byref(us)))
     return us.value
+
+
+def field_differences(mu, npoint: int, step: float):
+    """alpha(h_k), beta(h_k), gamma(h_k), k = 1 .. npoint, from the dipoles at the 2 npoint + 3
+    distinct fields 0, +h_1 .. +h_{npoint+1}, -h_1 .. -h_{npoint+1} (nof_field_differences)."""
+    mu = np.ascontiguousarray(mu, np.float64)
+    if mu.size != 2 * npoint + 3:
+        raise ValueError("expected 2 npoint + 3 dipoles")
+    out = [np.zeros(npoint) for _ in range(3)]
+    _check(load_library().nof_field_differences(mu.ctypes.data_as(ctypes.c_void_p), npoint, float(step),
+                                                *(o.ctypes.data_as(ctypes.c_void_p) for o in out)))
+    return tuple(out)
+
+
+def romberg(D):
+    """Romberg-Richardson triangle of D(h_k) and the selected (value, Delta, k, j) (nof_romberg)."""
+    D = np.ascontiguousarray(D, np.float64)
+    N = D.size
+    R = np.zeros((N, N))
+    best = np.zeros(2)
+    sel = np.zeros(2, np.int32)
+    _check(load_library().nof_romberg(D.ctypes.data_as(ctypes.c_void_p), N, R.ctypes.data_as(ctypes.c_void_p),
+                                      best.ctypes.data_as(ctypes.c_void_p), sel.ctypes.data_as(ctypes.c_void_p)))
+    return R, (float(best[0]), float(best[1]), int(sel[0]), int(sel[1]))
+
+
+def step_batch(contexts, Cs, gammas, ms, vs, outs, stream=None):
+    """One nof_step on every context concurrently (each on its own stream), forked from `stream`."""
+    import torch
+    n = len(contexts)
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    arr = lambda ts: (ctypes.c_void_p * n)(*[_dptr(t).value for t in ts])
+    hs = (ctypes.c_void_p * n)(*[c._h.value for c in contexts])
+    ts = (ctypes.c_void_p * n)(*[ctypes.addressof(c.t) for c in contexts])
+    _check(load_library().nof_step_batch(hs, n, arr(Cs), arr(gammas), arr(ms), arr(vs), ts, arr(outs),
+                                         ctypes.c_void_p(stream.cuda_stream)))
 
 
 def energy_grad_batch(contexts, Cs, gammas, Es, gs=None, ggs=None, stream=None):
@@ -269,6 +310,19 @@ class Context:
         _check(load_library().nof_step(self._h, _dptr(C), _dptr(gamma), _dptr(m), _dptr(v),
                                        ctypes.byref(self.t), _dptr(out)))
         return out
+
+    def set_field(self, F):
+        """Static field F = (Fx, Fy, Fz) in atomic units for every later call (nof_set_field)."""
+        f = np.ascontiguousarray(F, np.float64)
+        if f.shape != (3,):
+            raise ValueError("F has three components")
+        _check(load_library().nof_set_field(self._h, f.ctypes.data_as(ctypes.c_void_p)))
+
+    def dipole(self, C, gamma, mu=None):
+        """Dipole moment (3,) of the state (C, gamma) as a device tensor (nof_dipole)."""
+        mu = self._empty(3) if mu is None else mu
+        _check(load_library().nof_dipole(self._h, _dptr(C), _dptr(gamma), _dptr(mu)))
+        return mu
 
     def profile(self, enable: bool = True):
         _check(load_library().nof_profile(self._h, 1 if enable else 0))

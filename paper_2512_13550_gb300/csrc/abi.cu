@@ -104,6 +104,7 @@ void free_system(nof_ctx* c) {
     dfree(c->s); dfree(c->t); dfree(c->ds); dfree(c->dt); dfree(c->occ); dfree(c->E);
     dfree(c->part); dfree(c->ggam); dfree(c->gorb);
     dfree(c->y); dfree(c->U); dfree(c->U2); dfree(c->tmpn); dfree(c->gwork);
+    dfree(c->Dip); dfree(c->H0); dfree(c->vnn0); dfree(c->dipw);
     c->built = 0;
 }
 

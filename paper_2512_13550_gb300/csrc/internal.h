@@ -79,6 +79,9 @@ struct nof_ctx {
     const void* glast[5];
     long long gkernels;
     int gfail;
+    // static field (nof_set_field): dipole integrals [3][n][n], the field-free h and V_nn,
+    // scratch of the dipole moment [3][a]; all allocated on first use
+    double *Dip, *H0, *vnn0, *dipw;
     // dominant-kernel timing (nof_profile)
     int prof_on;
     const char* prof_name;

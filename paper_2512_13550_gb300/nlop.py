@@ -1,0 +1,66 @@
+"""Finite-field polarizability and hyperpolarizabilities on the GPU (NLOPs subsection of
+DoNOF 2.0, arXiv 2512.13550).
+
+The differences use the dipole at -2h, -h, 0, h, 2h for every step h_k = STEP 2^{k-1},
+k = 1 .. NPOINT. Since 2 h_k = h_{k+1}, these 5 NPOINT points hold 2 NPOINT + 3 distinct
+fields: 0 and +-h_1 .. +-h_{NPOINT+1}. Every distinct field gets a context (same geometry and
+basis, field set by nof_set_field) and its own state. All states take `nsteps` alternating
+steps together (nof_step_batch: one stream per field, forked from and joined to the caller's
+stream). The dipole along `axis` at each final state (nof_dipole) then gives the centred
+differences (nof_field_differences) and the three Romberg-Richardson triangles with their
+selected values (nof_romberg). All arithmetic is in the library; this module only allocates
+device memory and orders the calls.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import PREC_FP64, Context, field_differences, romberg, step_batch
+
+
+def field_points(step: float, npoint: int) -> np.ndarray:
+    """The distinct fields in the order nof_field_differences expects: 0, +h_1 .. +h_{n+1},
+    -h_1 .. -h_{n+1}."""
+    h = step * 2.0 ** np.arange(npoint + 1)
+    return np.concatenate([[0.0], h, -h])
+
+
+def finite_field(xyz, orb, aux, axis: int = 2, step: float = 1e-3, npoint: int = 9, nsteps: int = 100,
+                 precision: int = PREC_FP64, C0=None, gamma0=None, **opts):
+    """alpha, beta, gamma along `axis` from `nsteps` alternating steps at every field.
+
+    C0, gamma0: the common starting point (default: the field-free core guess and gamma = 0.3).
+    Returns a dict: fields, mu (dipole along the axis at each field), D = (alpha(h), beta(h),
+    gamma(h)), alpha / beta / gamma = (R, (value, Delta, k, j)), and the contexts."""
+    import torch
+    fields = field_points(step, npoint)
+    ctxs = []
+    for f in fields:
+        c = Context(precision=precision, stream=torch.cuda.Stream(), **opts)
+        c.build_B(xyz, orb, aux)
+        F = np.zeros(3)
+        F[axis] = f
+        c.set_field(F)
+        ctxs.append(c)
+    s = ctxs[0].sizes
+    n, ng = s["nbf"], s["ngamma"]
+    dev = dict(dtype=torch.float64, device="cuda")
+    if C0 is None:
+        C0, _ = ctxs[0].core_guess()  # fields[0] = 0
+    C0 = torch.as_tensor(np.asarray(C0.cpu() if hasattr(C0, "cpu") else C0), **dev)
+    g0 = torch.full((ng,), 0.3, **dev) if gamma0 is None else torch.as_tensor(np.asarray(gamma0), **dev)
+    torch.cuda.synchronize()
+    Cs = [C0.clone() for _ in ctxs]
+    gs = [g0.clone() for _ in ctxs]
+    ms = [torch.zeros(n, n, **dev) for _ in ctxs]
+    vs = [torch.zeros(n, n, **dev) for _ in ctxs]
+    outs = [torch.empty(3, **dev) for _ in ctxs]
+    torch.cuda.synchronize()
+    for _ in range(nsteps):
+        step_batch(ctxs, Cs, gs, ms, vs, outs)
+    mus = [c.dipole(C, g) for c, C, g in zip(ctxs, Cs, gs)]
+    torch.cuda.synchronize()
+    mu = np.array([m[axis].item() for m in mus])
+    al, be, ga = field_differences(mu, npoint, step)
+    return dict(fields=fields, mu=mu, D=(al, be, ga), alpha=romberg(al), beta=romberg(be), gamma=romberg(ga),
+                steps_out=[o.cpu().numpy() for o in outs], contexts=ctxs)
