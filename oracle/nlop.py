@@ -23,9 +23,12 @@ Readings (the paper leaves these to the code it describes):
   * at fixed orbitals and occupations E(F) = E(0) - F.mu, exactly;
   * 2 h_k = h_{k+1}, so the 5 NPOINT field points hold 2 NPOINT + 3 distinct fields; each is
     computed once;
-  * the state at each field is what a fixed number of the library's alternating steps reaches
-    from one common starting point (the paper converges each field to tight thresholds; the
-    step count here is a parameter, and the same steps run on both sides).
+  * the state at each field is what the library's alternating steps reach from one common
+    starting point. The paper converges each field to tight thresholds (NTHRESHL on the
+    symmetry of the Lagrange multipliers, NTHRESHE on the energy). Here a field stops at the
+    first check (every `check` steps) where the step reports ||g|| < gtol, or after `nsteps`
+    steps. Stopping matters: once converged, further ADAM steps eventually leave the minimum,
+    at a point that depends on rounding.
 
 Parity: the dipole integrals are pinned by quadrature and by their origin dependence, the field
 term by the exact linearity of E(F), the differences and the triangle by polynomials they must
@@ -119,17 +122,24 @@ def romberg(D):
 
 
 def run(B, H, D, xyz, vnn, pm: pnof.PairMap, axis: int, step_size: float, npoint: int, nsteps: int,
-        C0, gamma0, ipnof: int = 7, Z=None, **opt):
-    """The whole workload: nsteps alternating steps at every distinct field from (C0, gamma0),
-    the dipole along `axis` at each final state, the differences and the three triangles."""
-    mu = {}
+        C0, gamma0, ipnof: int = 7, Z=None, gtol=None, check: int = 25, **opt):
+    """The whole workload: alternating steps at every distinct field from (C0, gamma0) (at most
+    nsteps; with gtol, stopping at the first multiple of `check` steps whose step reported
+    ||g|| < gtol), the dipole along `axis` at each final state, the differences and the three
+    triangles. `steps` holds the step count of each field."""
+    mu, steps = {}, {}
     for f in field_points(step_size, npoint):
         F = np.zeros(3)
         F[axis] = f
         Hf, vf = field_hamiltonian(H, D, F, xyz, vnn, Z)
         st = step.State(C0, gamma0)
-        for _ in range(nsteps):
-            step.step(B, Hf, vf, st, pm, ipnof, **opt)
+        done = 0
+        for it in range(nsteps):
+            _, gn, _ = step.step(B, Hf, vf, st, pm, ipnof, **opt)
+            done = it + 1
+            if gtol is not None and done % check == 0 and gn < gtol:
+                break
         mu[f] = dipole(st.C, st.gamma, pm, D, xyz, Z)[axis]
+        steps[f] = done
     al, be, ga = differences(mu, step_size, npoint)
-    return dict(mu=mu, alpha=romberg(al), beta=romberg(be), gamma=romberg(ga), D=(al, be, ga))
+    return dict(mu=mu, steps=steps, alpha=romberg(al), beta=romberg(be), gamma=romberg(ga), D=(al, be, ga))

@@ -4,11 +4,13 @@ DoNOF 2.0, arXiv 2512.13550).
 The differences use the dipole at -2h, -h, 0, h, 2h for every step h_k = STEP 2^{k-1},
 k = 1 .. NPOINT. Since 2 h_k = h_{k+1}, these 5 NPOINT points hold 2 NPOINT + 3 distinct
 fields: 0 and +-h_1 .. +-h_{NPOINT+1}. Every distinct field gets a context (same geometry and
-basis, field set by nof_set_field) and its own state. All states take `nsteps` alternating
-steps together (nof_step_batch: one stream per field, forked from and joined to the caller's
-stream). The dipole along `axis` at each final state (nof_dipole) then gives the centred
-differences (nof_field_differences) and the three Romberg-Richardson triangles with their
-selected values (nof_romberg). All arithmetic is in the library; this module only allocates
+basis, field set by nof_set_field) and its own state. The states take alternating steps
+together (nof_step_batch: one stream per field, forked from and joined to the caller's stream),
+at most `nsteps`. With `gtol`, every `check` steps the fields whose last step reported
+||g|| < gtol stop (the paper converges every field to thresholds; continued ADAM steps would
+eventually leave a converged minimum). The dipole along `axis` at each final state
+(nof_dipole) then gives the centred differences (nof_field_differences) and the three
+Romberg-Richardson triangles with their selected values (nof_romberg). All arithmetic is in the library; this module only allocates
 device memory and orders the calls.
 """
 from __future__ import annotations
@@ -26,12 +28,13 @@ def field_points(step: float, npoint: int) -> np.ndarray:
 
 
 def finite_field(xyz, orb, aux, axis: int = 2, step: float = 1e-3, npoint: int = 9, nsteps: int = 100,
-                 precision: int = PREC_FP64, C0=None, gamma0=None, **opts):
-    """alpha, beta, gamma along `axis` from `nsteps` alternating steps at every field.
+                 precision: int = PREC_FP64, C0=None, gamma0=None, gtol=None, check: int = 25, **opts):
+    """alpha, beta, gamma along `axis` from alternating steps at every field.
 
     C0, gamma0: the common starting point (default: the field-free core guess and gamma = 0.3).
-    Returns a dict: fields, mu (dipole along the axis at each field), D = (alpha(h), beta(h),
-    gamma(h)), alpha / beta / gamma = (R, (value, Delta, k, j)), and the contexts."""
+    Returns a dict: fields, mu (dipole along the axis at each field), steps (per field),
+    D = (alpha(h), beta(h), gamma(h)), alpha / beta / gamma = (R, (value, Delta, k, j)), and the
+    contexts."""
     import torch
     fields = field_points(step, npoint)
     ctxs = []
@@ -56,11 +59,21 @@ def finite_field(xyz, orb, aux, axis: int = 2, step: float = 1e-3, npoint: int =
     vs = [torch.zeros(n, n, **dev) for _ in ctxs]
     outs = [torch.empty(3, **dev) for _ in ctxs]
     torch.cuda.synchronize()
-    for _ in range(nsteps):
-        step_batch(ctxs, Cs, gs, ms, vs, outs)
+    active = list(range(len(ctxs)))
+    steps = [0] * len(ctxs)
+    for it in range(nsteps):
+        step_batch([ctxs[i] for i in active], [Cs[i] for i in active], [gs[i] for i in active],
+                   [ms[i] for i in active], [vs[i] for i in active], [outs[i] for i in active])
+        for i in active:
+            steps[i] = it + 1
+        if gtol is not None and (it + 1) % check == 0:
+            gn = torch.stack([outs[i][1] for i in active]).cpu().numpy()
+            active = [i for i, g in zip(active, gn) if not g < gtol]
+            if not active:
+                break
     mus = [c.dipole(C, g) for c, C, g in zip(ctxs, Cs, gs)]
     torch.cuda.synchronize()
     mu = np.array([m[axis].item() for m in mus])
     al, be, ga = field_differences(mu, npoint, step)
-    return dict(fields=fields, mu=mu, D=(al, be, ga), alpha=romberg(al), beta=romberg(be), gamma=romberg(ga),
-                steps_out=[o.cpu().numpy() for o in outs], contexts=ctxs)
+    return dict(fields=fields, mu=mu, steps=np.array(steps), D=(al, be, ga), alpha=romberg(al),
+                beta=romberg(be), gamma=romberg(ga), steps_out=[o.cpu().numpy() for o in outs], contexts=ctxs)

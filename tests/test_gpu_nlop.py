@@ -88,3 +88,34 @@ def test_pipeline_matches_oracle():
         Rw, bw = onlop.romberg(got["D"][i])
         assert got[key][1][2:] == bw[2:]
         assert got[key][1][0] == pytest.approx(bw[0], rel=1e-13, abs=1e-300)
+
+
+def test_converged_h2_polarizabilities_match_oracle():
+    """H2 (R = 1.4 bohr, 3 s + 10 aux s per H, N_g = 1) with the paper's default ladder
+    (NPOINT = 9, STEP = 1e-4), every field stepped until its step reports ||g|| < 1e-9 (checked
+    every 25 steps): GPU and oracle reach the same converged states, so the dipoles agree to the
+    convergence threshold and the selected alpha, beta, gamma agree. beta vanishes (H2 is
+    centrosymmetric) and alpha is positive."""
+    from paper_2512_13550_gb300 import nlop
+    orb, aux = inputs.basis_3s_10aux()
+    xyz = inputs.chain(2, 1.4)
+    xyz = xyz - xyz.mean(axis=0)
+    S, T, V = integrals.one_electron(orb, xyz)
+    H = T + V
+    B = ri.fitted_B(orb, aux, xyz)
+    vnn = integrals.nuclear_repulsion(xyz)
+    n = S.shape[0]
+    pm = pnof.PairMap(2, 1, n)
+    C0 = reference.core_guess(S, H)
+    kw = dict(axis=2, npoint=9, nsteps=2000, gtol=1e-9, check=25)
+    want = onlop.run(B, H, onlop.dipole_integrals(orb, xyz), xyz, vnn, pm, step_size=1e-4, C0=C0,
+                     gamma0=np.full(pm.ngamma, 0.3), **kw)
+    got = nlop.finite_field(xyz, orb, aux, step=1e-4, C0=C0, **kw)
+    fields = nlop.field_points(1e-4, 9)
+    assert np.all(got["steps"] < 2000)
+    np.testing.assert_allclose(got["mu"], [want["mu"][f] for f in fields], rtol=0, atol=1e-9)
+    a_got, a_want = got["alpha"][1][0], want["alpha"][1][0]
+    assert a_got > 1.0 and abs(a_got - a_want) < 1e-6 * abs(a_want)
+    assert abs(got["beta"][1][0]) < 1e-3 and abs(want["beta"][1][0]) < 1e-3
+    g_got, g_want = got["gamma"][1][0], want["gamma"][1][0]
+    assert abs(g_got - g_want) < 1e-2 * max(1.0, abs(g_want))
