@@ -45,10 +45,11 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["h50", "h200", "batch"], default="h50",
+    ap.add_argument("--workload", choices=["h50", "h200", "batch", "nlop"], default="h50",
                     help="h50: the single-geometry benchmark; h200: the 10 x 20 lattice (nbf 600, "
                          "naux 2000, nact 200); batch: many uneven H-chain frames evaluated "
-                         "concurrently as one CUDA-graph launch")
+                         "concurrently as one CUDA-graph launch; nlop: the finite-field polarizability "
+                         "and hyperpolarizabilities of H2 (21 field instances stepped together)")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-max", type=int, default=64, help="largest chain length in the batch")
     ap.add_argument("--no-graph", action="store_true",
@@ -258,12 +259,86 @@ def run_batch(args):
     return 0
 
 
+def run_nlop(args):
+    """The finite-field workload on H2 (R = 1.4 bohr, centred; 3 s + 10 aux s per H; N_g = 1;
+    FP64 path): the paper's default ladder NPOINT = 9, STEP = 1e-4 along the bond, i.e. 21
+    distinct fields, every field stepped from the field-free core guess until its step reports
+    ||g|| < 1e-9 (checked every 25 steps), then the dipoles, differences and Romberg triangles.
+    The rate is field-instance steps per second over the whole run (set-up excluded)."""
+    import torch
+    import paper_2512_13550_gb300 as nof
+    from paper_2512_13550_gb300 import inputs, nlop
+    orb, aux = inputs.basis_3s_10aux()
+    xyz = inputs.chain(2, 1.4)
+    xyz = xyz - xyz.mean(axis=0)
+    kw = dict(axis=2, step=1e-4, npoint=9, nsteps=2000, gtol=1e-9, check=25)
+    res = None
+    times = []
+    runs = max(1, min(args.steps, 5))  # a run is a whole workload (about half a second)
+    for rep in range(args.warmup + runs):  # every run builds its own contexts (set-up untimed)
+        r = {}
+        res = nlop.finite_field(xyz, orb, aux, **kw, timing=r)
+        if rep >= args.warmup:
+            times.append((r["ms"], int(res["steps"].sum()), r["step_launches"]))
+    ms = sum(t[0] for t in times)
+    total_steps = sum(t[1] for t in times)
+    line = {"metric": "field-instance alternating steps/s (finite-field NLOP workload)",
+            "value": total_steps / (ms / 1e3), "unit": "steps/s", "n_gpus": 1, "steps": runs,
+            "warmup": args.warmup, "ms_per_step": ms / runs, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "H2 R=1.4 bohr, 3 s + 10 aux s per H, N_g=1, field along the bond, "
+                                   "NPOINT=9, STEP=1e-4 (21 fields), stop at ||g|| < 1e-9 (checked every 25 "
+                                   "steps), at most 2000 steps",
+                       "runs": "one bench step is one whole run of the workload (at most 5 runs)",
+                       "timing": "wall time, device synchronised on both sides, of the stepping (one "
+                                 "CUDA-graph replay of the batched step per step; host convergence checks "
+                                 "every 25 steps included), dipoles, differences and triangles of one run; "
+                                 "context set-up excluded",
+                       "steps_per_field": [int(x) for x in res["steps"]]},
+            "result": {k: {"value": res[k][1][0], "delta": res[k][1][1], "k": res[k][1][2], "j": res[k][1][3]}
+                       for k in ("alpha", "beta", "gamma")},
+            "gpu_launches": int(sum(t[2] for t in times))}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = nlop_cpu_baseline(xyz, orb, aux)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def nlop_cpu_baseline(xyz, orb, aux, nfield=3):
+    """The oracle's stepping for the first `nfield` fields of the same workload (same stopping
+    rule), in field-instance steps per second."""
+    import numpy as np
+    from oracle import integrals, nlop as onlop, pnof, reference, ri, step as ostep
+    S, T, V = integrals.one_electron(orb, xyz)
+    H = T + V
+    B = ri.fitted_B(orb, aux, xyz)
+    vnn = integrals.nuclear_repulsion(xyz)
+    pm = pnof.PairMap(2, 1, S.shape[0])
+    D = onlop.dipole_integrals(orb, xyz)
+    C0 = reference.core_guess(S, H)
+    done = 0
+    t0 = time.perf_counter()
+    for f in onlop.field_points(1e-4, 9)[:nfield]:
+        Hf, vf = onlop.field_hamiltonian(H, D, [0.0, 0.0, f], xyz, vnn)
+        st = ostep.State(C0, np.full(pm.ngamma, 0.3))
+        for it in range(2000):
+            _, gn, _ = ostep.step(B, Hf, vf, st, pm)
+            done += 1
+            if (it + 1) % 25 == 0 and gn < 1e-9:
+                break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "steps/s", "cores": _cores(), "kind": "oracle",
+            "sample": f"{done} oracle steps over the first {nfield} of the 21 fields in {dt:.1f} s"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "nlop":
+        return run_nlop(args)
     import torch
     import paper_2512_13550_gb300 as nof
     from paper_2512_13550_gb300 import inputs

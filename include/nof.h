@@ -153,7 +153,12 @@ int nof_energy_grad(nof_ctx* ctx, const double* C, const double* gamma, double* 
  *   1. J, K, h_pp at C;  2. on_iters ON steps gamma -= on_lr dE/dgamma with J, K fixed;
  *   3. E, lambda, g at (C, gamma);  4. ADAM on g (moments m, v: nbf x nbf, step counter *t
  *   on the host, incremented);  5. C <- C exp(y) (Taylor-12 scaling and squaring).
- * out (device, 3 doubles): E at (C_old, gamma_new), ||g||_F, max |lambda - lambda^T|. */
+ * out (device, 3 doubles): E at (C_old, gamma_new), ||g||_F, max |lambda - lambda^T|.
+ * t == NULL selects a step that can be captured in a CUDA graph: the step counter is a device
+ * integer owned by the context (zero after nof_build_B, advanced on the device), and exp(y) is
+ * scaled by a fixed 2^-12 with 12 squarings instead of a scaling read back to the host. Such a
+ * step makes no host synchronisation and no host-side state change; a rotation with
+ * ||y||_F > 4096 is reported by nof_sync as NOF_ENOTCONV. */
 int nof_step(nof_ctx* ctx, double* C, double* gamma, double* m, double* v, int* t, double* out);
 
 /* Batched evaluation (the batching of many geometries): `count` independent contexts, each built
@@ -208,7 +213,9 @@ int nof_romberg(const double* D, int npoint, double* R, double* best, int* sel);
 /* nof_step on `count` contexts at once (the independent field instances of the finite-field
  * workload): each context on its own stream, forked from `stream` and joined back with events,
  * as nof_energy_grad_batch. Host arrays of `count` pointers: C, gamma, m, v, out (device) and
- * t (host step counters). Errors: as nof_step; NOF_EINVAL for a bad count or a null entry. */
+ * t (host step counters); t itself may be NULL, selecting every context's device-side counter
+ * (see nof_step), so that capturing `stream` captures the whole batched step as one CUDA graph.
+ * Errors: as nof_step; NOF_EINVAL for a bad count or a null entry. */
 int nof_step_batch(nof_ctx* const* ctxs, int count, double* const* C, double* const* gamma,
                    double* const* m, double* const* v, int* const* t, double* const* out, void* stream);
 

@@ -155,14 +155,15 @@ def romberg(D):
     return R, (float(best[0]), float(best[1]), int(sel[0]), int(sel[1]))
 
 
-def step_batch(contexts, Cs, gammas, ms, vs, outs, stream=None):
-    """One nof_step on every context concurrently (each on its own stream), forked from `stream`."""
+def step_batch(contexts, Cs, gammas, ms, vs, outs, stream=None, device_counter: bool = False):
+    """One nof_step on every context concurrently (each on its own stream), forked from `stream`.
+    device_counter: the contexts' device-side step counters (the call is then capturable)."""
     import torch
     n = len(contexts)
     stream = stream if stream is not None else torch.cuda.current_stream()
     arr = lambda ts: (ctypes.c_void_p * n)(*[_dptr(t).value for t in ts])
     hs = (ctypes.c_void_p * n)(*[c._h.value for c in contexts])
-    ts = (ctypes.c_void_p * n)(*[ctypes.addressof(c.t) for c in contexts])
+    ts = None if device_counter else (ctypes.c_void_p * n)(*[ctypes.addressof(c.t) for c in contexts])
     _check(load_library().nof_step_batch(hs, n, arr(Cs), arr(gammas), arr(ms), arr(vs), ts, arr(outs),
                                          ctypes.c_void_p(stream.cuda_stream)))
 
@@ -305,10 +306,12 @@ class Context:
                                               _dptr(g) if grad else None, _dptr(gg) if grad else None))
         return E, g, gg
 
-    def step(self, C, gamma, m, v, out=None):
+    def step(self, C, gamma, m, v, out=None, device_counter: bool = False):
+        """One alternating step (nof_step). device_counter: keep the ADAM step counter on the
+        device (t == NULL), which makes the call capturable in a CUDA graph."""
         out = self._empty(3) if out is None else out
         _check(load_library().nof_step(self._h, _dptr(C), _dptr(gamma), _dptr(m), _dptr(v),
-                                       ctypes.byref(self.t), _dptr(out)))
+                                       None if device_counter else ctypes.byref(self.t), _dptr(out)))
         return out
 
     def set_field(self, F):

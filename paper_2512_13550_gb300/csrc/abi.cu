@@ -104,7 +104,7 @@ void free_system(nof_ctx* c) {
     dfree(c->s); dfree(c->t); dfree(c->ds); dfree(c->dt); dfree(c->occ); dfree(c->E);
     dfree(c->part); dfree(c->ggam); dfree(c->gorb);
     dfree(c->y); dfree(c->U); dfree(c->U2); dfree(c->tmpn); dfree(c->gwork);
-    dfree(c->Dip); dfree(c->H0); dfree(c->vnn0); dfree(c->dipw);
+    dfree(c->Dip); dfree(c->H0); dfree(c->vnn0); dfree(c->dipw); dfree(c->tdev);
     c->built = 0;
 }
 
@@ -397,6 +397,8 @@ int nof_build_B(nof_ctx* c, int natom, const double* xyz, const double* Z, int c
     NOF_TRY(dalloc(&c->ds, (size_t)a * ncwo)); NOF_TRY(dalloc(&c->dt, (size_t)a * ncwo));
     NOF_TRY(dalloc(&c->E, 1)); NOF_TRY(dalloc(&c->part, 4 * (size_t)a)); NOF_TRY(dalloc(&c->ggam, c->ngamma));
     NOF_TRY(dalloc(&c->y, nn)); NOF_TRY(dalloc(&c->U, nn)); NOF_TRY(dalloc(&c->U2, nn)); NOF_TRY(dalloc(&c->tmpn, nn));
+    NOF_TRY(dalloc(&c->tdev, 1));  // device-side step counter (nof_step with t == NULL)
+    NOF_CUDA(cudaMemsetAsync(c->tdev, 0, sizeof(int), c->stream));
     {   // split-K scratch for the small FP64 GEMMs (n x n, n x a, a x a, X x a outputs)
         size_t big = nn > (size_t)X * a ? nn : (size_t)X * a;
         size_t cap = 304 * big;
@@ -589,7 +591,7 @@ int nof_energy_grad(nof_ctx* c, const double* C, const double* gamma, double* E,
 
 int nof_step(nof_ctx* c, double* C, double* gamma, double* m, double* v, int* t, double* out) {
     NOF_TRY(check_ctx(c, true));
-    if (!C || !gamma || !m || !v || !t || !out) {
+    if (!C || !gamma || !m || !v || !out) {
         nof_set_error("nof_step: null pointer");
         return NOF_EINVAL;
     }
@@ -672,6 +674,11 @@ int nof_sync(nof_ctx* c) {
         if (h & NOF_DEV_ILLCOND) {
             nof_set_error("ill-conditioned metric");
             return NOF_EILLCOND;
+        }
+        if (h & NOF_DEV_RANGE) {
+            nof_set_error("a step's rotation exceeded the fixed scaling of the device-counter step "
+                          "(||y||_F > 4096)");
+            return NOF_ENOTCONV;
         }
     }
     return NOF_OK;

@@ -31,7 +31,7 @@ void nof_count_launch();
     } while (0)
 
 // Device status word bits (written by kernels, read by nof_sync).
-enum { NOF_DEV_NONFINITE = 1, NOF_DEV_TIMEOUT = 2, NOF_DEV_ILLCOND = 4 };
+enum { NOF_DEV_NONFINITE = 1, NOF_DEV_TIMEOUT = 2, NOF_DEV_ILLCOND = 4, NOF_DEV_RANGE = 8 };
 
 // ---------------------------------------------------------------------------------------
 // Split-precision (exact BF16 digit) storage of the RI tensor; defined in fast.cu.
@@ -82,6 +82,8 @@ struct nof_ctx {
     // static field (nof_set_field): dipole integrals [3][n][n], the field-free h and V_nn,
     // scratch of the dipole moment [3][a]; all allocated on first use
     double *Dip, *H0, *vnn0, *dipw;
+    // ADAM step counter on the device for nof_step with t == NULL (zero after nof_build_B)
+    int* tdev;
     // dominant-kernel timing (nof_profile)
     int prof_on;
     const char* prof_name;
@@ -130,6 +132,11 @@ int newton_schulz_invsqrt(const double* S, double* Xout, double* w1, double* w2,
                           size_t work_cap = 0);
 int expm_antisym_device(const double* y, double* U, double* w1, double* w2, int n,
                         cudaStream_t st, double* work = nullptr, size_t work_cap = 0);
+// The same series with a fixed scaling 2^-12 and 12 squarings: no host synchronisation, so it can
+// be captured in a CUDA graph. Sets NOF_DEV_RANGE in *status when ||y||_F > 2^12 (the scaled
+// norm would exceed 1).
+int expm_antisym_device_fixed(const double* y, double* U, double* w1, double* w2, int n, int* status,
+                              cudaStream_t st, double* work = nullptr, size_t work_cap = 0);
 
 int sym_eig(double* A, double* Vwork, double* Vout, double* w, int n, int* sweeps_dev, cudaStream_t st);
 

@@ -483,6 +483,36 @@ int newton_schulz_invsqrt(const double* S, double* Xout, double* Y, double* Z, d
 
 // U = exp(y) for antisymmetric y: s = smallest integer with ||y||_F / 2^s <= 1/2,
 // Horner form of the degree-12 Taylor polynomial of z = y / 2^s, then s squarings.
+// *flag |= NOF_DEV_RANGE when *nrm > limit (one thread)
+__global__ void k_range_check(const double* nrm, double limit, int* flag) {
+    if (!(*nrm <= limit)) atomicOr(flag, NOF_DEV_RANGE);
+}
+
+int expm_antisym_device_fixed(const double* y, double* U, double* w1, double* w2, int n, int* status,
+                              cudaStream_t st, double* work, size_t work_cap) {
+    constexpr int kS = 12;
+    long long nn = (long long)n * n;
+    k_frob<<<1, 256, 0, st>>>(y, nn, w1);
+    NOF_LAUNCH_CHECK();
+    k_range_check<<<1, 1, 0, st>>>(w1, std::ldexp(1.0, kS), status);
+    NOF_LAUNCH_CHECK();
+    double* z = w1;  // the norm is no longer needed
+    k_scale<<<blocks_for(nn), 256, 0, st>>>(y, std::ldexp(1.0, -kS), z, nn);
+    NOF_LAUNCH_CHECK();
+    k_axpy_identity<<<blocks_for(nn), 256, 0, st>>>(z, 0.0, U, n);
+    NOF_LAUNCH_CHECK();
+    for (int k = 12; k >= 1; --k) {
+        NOF_TRY(gemm64(square_gemm(z, U, w2, n, work, work_cap), st));  // w2 = z U
+        k_axpy_identity<<<blocks_for(nn), 256, 0, st>>>(w2, 1.0 / k, U, n);
+        NOF_LAUNCH_CHECK();
+    }
+    for (int i = 0; i < kS; ++i) {
+        NOF_TRY(gemm64(square_gemm(U, U, w2, n, work, work_cap), st));
+        NOF_CUDA(cudaMemcpyAsync(U, w2, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    return NOF_OK;
+}
+
 int expm_antisym_device(const double* y, double* U, double* w1, double* w2, int n,
                         cudaStream_t st, double* work, size_t work_cap) {
     long long nn = (long long)n * n;

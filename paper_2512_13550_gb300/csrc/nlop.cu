@@ -220,13 +220,13 @@ int nof_romberg(const double* D, int npoint, double* R, double* best, int* sel) 
 
 int nof_step_batch(nof_ctx* const* ctxs, int count, double* const* C, double* const* gamma, double* const* m,
                    double* const* v, int* const* t, double* const* out, void* stream) {
-    if (count <= 0 || !ctxs || !C || !gamma || !m || !v || !t || !out) {
+    if (count <= 0 || !ctxs || !C || !gamma || !m || !v || !out) {
         nof_set_error("nof_step_batch: bad count or null array");
         return NOF_EINVAL;
     }
     for (int i = 0; i < count; ++i) {
         NOF_TRY(check(ctxs[i]));
-        if (!C[i] || !gamma[i] || !m[i] || !v[i] || !t[i] || !out[i]) {
+        if (!C[i] || !gamma[i] || !m[i] || !v[i] || !out[i]) {
             nof_set_error("nof_step_batch: null entry");
             return NOF_EINVAL;
         }
@@ -236,7 +236,7 @@ int nof_step_batch(nof_ctx* const* ctxs, int count, double* const* C, double* co
     for (int i = 0; i < count; ++i) {
         nof_ctx* c = ctxs[i];
         NOF_CUDA(cudaStreamWaitEvent(c->stream, ctxs[0]->ev_fork, 0));
-        NOF_TRY(nof_step(c, C[i], gamma[i], m[i], v[i], t[i], out[i]));
+        NOF_TRY(nof_step(c, C[i], gamma[i], m[i], v[i], t ? t[i] : nullptr, out[i]));
         NOF_CUDA(cudaEventRecord(c->ev_join, c->stream));
         NOF_CUDA(cudaStreamWaitEvent(master, c->ev_join, 0));
     }

@@ -295,9 +295,14 @@ __global__ void k_gamma_descent(double* gamma, const double* grad, double lr, in
 
 // ADAM moments and rotation generator y = -lr mhat / (sqrt(vhat) + eps)
 __global__ void k_adam(const double* g, double* m, double* v, double* y, long long nn, double b1,
-                       double b2, double c1, double c2, double lr, double eps) {
+                       double b2, double c1, double c2, double lr, double eps, const int* tdev) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= nn) return;
+    if (tdev) {  // bias corrections of step t = *tdev + 1 (the counter is advanced by k_tick)
+        const int t = *tdev + 1;
+        c1 = 1.0 - pow(b1, (double)t);
+        c2 = 1.0 - pow(b2, (double)t);
+    }
     double gi = g[i];
     double mi = b1 * m[i] + (1.0 - b1) * gi;
     double vi = b2 * v[i] + (1.0 - b2) * gi * gi;
@@ -305,6 +310,8 @@ __global__ void k_adam(const double* g, double* m, double* v, double* y, long lo
     v[i] = vi;
     y[i] = -lr * (mi / c1) / (sqrt(vi / c2) + eps);
 }
+
+__global__ void k_tick(int* t) { *t += 1; }
 
 // out[0] = E, out[1] = ||g||_F, out[2] = max |lambda - lambda^T|
 __global__ void k_step_stats(const double* E, const double* g, const double* lam, int n, int a,
@@ -513,14 +520,26 @@ int pnof_adam_rotate(nof_ctx* c, double* C, double* m, double* v, int* t, double
     const int n = c->nbf;
     cudaStream_t st = c->stream;
     long long nn = (long long)n * n;
-    *t += 1;
-    double c1 = 1.0 - std::pow(c->opt.b1, *t), c2 = 1.0 - std::pow(c->opt.b2, *t);
+    double c1 = 0.0, c2 = 0.0;
+    if (t) {
+        *t += 1;
+        c1 = 1.0 - std::pow(c->opt.b1, *t);
+        c2 = 1.0 - std::pow(c->opt.b2, *t);
+    }
     k_adam<<<nblk(nn), 256, 0, st>>>(c->gorb, m, v, c->y, nn, c->opt.b1, c->opt.b2, c1, c2,
-                                     c->opt.lr, c->opt.eps);
+                                     c->opt.lr, c->opt.eps, t ? nullptr : c->tdev);
     NOF_LAUNCH_CHECK();
+    if (!t) {
+        k_tick<<<1, 1, 0, st>>>(c->tdev);
+        NOF_LAUNCH_CHECK();
+    }
     k_step_stats<<<1, 256, 0, st>>>(c->E, c->gorb, c->lam, n, c->nact, out);
     NOF_LAUNCH_CHECK();
-    NOF_TRY(expm_antisym_device(c->y, c->U, c->U2, c->tmpn, n, st, c->gwork, c->gwork_cap));
+    if (t)
+        NOF_TRY(expm_antisym_device(c->y, c->U, c->U2, c->tmpn, n, st, c->gwork, c->gwork_cap));
+    else
+        NOF_TRY(expm_antisym_device_fixed(c->y, c->U, c->U2, c->tmpn, n, c->status, st, c->gwork,
+                                          c->gwork_cap));
     Gemm64 g;  // tmp = C U
     g.M = n; g.N = n; g.K = n;
     g.A = C; g.sAm = n; g.sAk0 = 1;

@@ -103,3 +103,39 @@ def test_graph_replay_matches_direct_launches(precision):
     cg.close()
     cd.close()
 
+
+
+def test_device_counter_step_can_be_captured():
+    """nof_step with t == NULL (device-side ADAM counter, fixed exp(y) scaling): direct calls and
+    CUDA-graph replays of one captured step give the same bits, and both follow the host-counter
+    step (rounding differences only: exp(y) is scaled differently)."""
+    import paper_2512_13550_gb300 as nof
+    sysm = systems.h4()
+    n = sysm.oracle["n"]
+
+    def ctx_state():
+        st = torch.cuda.Stream()
+        ctx = nof.Context(precision=0, stream=st)
+        ctx.build_B(sysm.xyz, sysm.orb, sysm.aux)
+        C, g = _t(sysm.orbitals(0)), _t(sysm.gamma(1))
+        m, v = torch.zeros(n, n, dtype=torch.float64, device="cuda"), torch.zeros(n, n, dtype=torch.float64,
+                                                                                   device="cuda")
+        out = torch.empty(3, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        return ctx, st, C, g, m, v, out
+
+    host, dev, rep = ctx_state(), ctx_state(), ctx_state()
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=rep[1]):
+        rep[0].step(rep[2], rep[3], rep[4], rep[5], rep[6], device_counter=True)
+    for it in range(12):
+        host[0].step(host[2], host[3], host[4], host[5], host[6])
+        dev[0].step(dev[2], dev[3], dev[4], dev[5], dev[6], device_counter=True)
+        cg.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(dev[2], rep[2]) and torch.equal(dev[3], rep[3]), it
+        assert torch.equal(dev[6], rep[6]), it
+        np.testing.assert_allclose(dev[2].cpu().numpy(), host[2].cpu().numpy(), rtol=0, atol=1e-10)
+        assert abs(dev[6][0].item() - host[6][0].item()) < 1e-10
+    for c in (host, dev, rep):
+        c[0].sync()  # raises if a device-side check (range of the fixed exp(y) scaling) fired
