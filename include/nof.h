@@ -210,6 +210,12 @@ int nof_field_differences(const double* mu, int npoint, double step, double* alp
  * Errors: NOF_EINVAL (null pointer, npoint < 1). */
 int nof_romberg(const double* D, int npoint, double* R, double* best, int* sel);
 
+/* ISOALPHA (NLOPs subsection): from the diagonal polarizabilities a[0..2] = alpha_xx, alpha_yy,
+ * alpha_zz, out[0] = (axx + ayy + azz) / 3 and out[1] = sqrt(((axx - ayy)^2 + (ayy - azz)^2 +
+ * (azz - axx)^2) / 2) (the anisotropy, Raman convention). Host arrays; no device work.
+ * Errors: NOF_EINVAL (null pointer). */
+int nof_polarizability_invariants(const double* a, double* out);
+
 /* nof_step on `count` contexts at once (the independent field instances of the finite-field
  * workload): each context on its own stream, forked from `stream` and joined back with events,
  * as nof_energy_grad_batch. Host arrays of `count` pointers: C, gamma, m, v, out (device) and

@@ -12,7 +12,9 @@ Follows the NLOPs subsection (Polarizabilities and Hyperpolarizabilities) of DoN
         R(k, j) = R(k, j-1) + (R(k, j-1) - R(k+1, j-1)) / (4^{j-1} - 1),  k <= NPOINT - j + 1;
   * the value reported: over every column j and every vertical pair (k, k+1) of it, the pair
     with the smallest Delta_{k,j} = |R(k+1, j) - R(k, j)| selects R(k, j+1), with Delta as its
-    uncertainty; equal Deltas are resolved towards the candidate of smallest magnitude.
+    uncertainty; equal Deltas are resolved towards the candidate of smallest magnitude;
+  * ISOALPHA: alpha_xx, alpha_yy, alpha_zz from fields along x, y, z, the isotropic mean and the
+    anisotropy in the Raman convention.
 
 Readings (the paper leaves these to the code it describes):
   * the field couples through the dipole operator mu = -sum_i r_i + sum_A Z_A R_A: the
@@ -119,6 +121,14 @@ def romberg(D):
     if best is None:
         return R, (float(D[0]), float("nan"), 1, 1)
     return R, (best[2], best[0], best[3], best[4])
+
+
+def polarizability_invariants(axx: float, ayy: float, azz: float):
+    """ISOALPHA: the isotropic polarizability (axx + ayy + azz) / 3 and the anisotropy (Raman
+    convention) sqrt(((axx - ayy)^2 + (ayy - azz)^2 + (azz - axx)^2) / 2)."""
+    iso = (axx + ayy + azz) / 3.0
+    aniso = np.sqrt(((axx - ayy) ** 2 + (ayy - azz) ** 2 + (azz - axx) ** 2) / 2.0)
+    return iso, aniso
 
 
 def run(B, H, D, xyz, vnn, pm: pnof.PairMap, axis: int, step_size: float, npoint: int, nsteps: int,

@@ -87,6 +87,7 @@ SIGNATURES = {
     "nof_field_differences": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, _P, _P, _P]),
     "nof_romberg": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "nof_step_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]),
+    "nof_polarizability_invariants": (ctypes.c_int, [_P, _P]),
     "nof_last_error": (ctypes.c_char_p, []),
 }
 
@@ -153,6 +154,15 @@ def romberg(D):
     _check(load_library().nof_romberg(D.ctypes.data_as(ctypes.c_void_p), N, R.ctypes.data_as(ctypes.c_void_p),
                                       best.ctypes.data_as(ctypes.c_void_p), sel.ctypes.data_as(ctypes.c_void_p)))
     return R, (float(best[0]), float(best[1]), int(sel[0]), int(sel[1]))
+
+
+def polarizability_invariants(axx: float, ayy: float, azz: float):
+    """Isotropic polarizability and anisotropy (Raman convention) (nof_polarizability_invariants)."""
+    a = np.array([axx, ayy, azz], np.float64)
+    out = np.zeros(2)
+    _check(load_library().nof_polarizability_invariants(a.ctypes.data_as(ctypes.c_void_p),
+                                                         out.ctypes.data_as(ctypes.c_void_p)))
+    return float(out[0]), float(out[1])
 
 
 def step_batch(contexts, Cs, gammas, ms, vs, outs, stream=None, device_counter: bool = False):

@@ -218,6 +218,17 @@ int nof_romberg(const double* D, int npoint, double* R, double* best, int* sel) 
     return NOF_OK;
 }
 
+int nof_polarizability_invariants(const double* a, double* out) {
+    if (!a || !out) {
+        nof_set_error("nof_polarizability_invariants: null pointer");
+        return NOF_EINVAL;
+    }
+    out[0] = (a[0] + a[1] + a[2]) / 3.0;
+    const double d01 = a[0] - a[1], d12 = a[1] - a[2], d20 = a[2] - a[0];
+    out[1] = std::sqrt((d01 * d01 + d12 * d12 + d20 * d20) / 2.0);
+    return NOF_OK;
+}
+
 int nof_step_batch(nof_ctx* const* ctxs, int count, double* const* C, double* const* gamma, double* const* m,
                    double* const* v, int* const* t, double* const* out, void* stream) {
     if (count <= 0 || !ctxs || !C || !gamma || !m || !v || !out) {

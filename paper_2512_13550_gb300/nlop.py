@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import PREC_FP64, Context, field_differences, romberg, step_batch
+from . import PREC_FP64, Context, field_differences, polarizability_invariants, romberg, step_batch
 
 
 def field_points(step: float, npoint: int) -> np.ndarray:
@@ -121,3 +121,15 @@ def finite_field(xyz, orb, aux, axis: int = 2, step: float = 1e-3, npoint: int =
         timing["step_launches"] = launches
     return dict(fields=fields, mu=mu, steps=np.array(steps), D=(al, be, ga), **out,
                 steps_out=[o.cpu().numpy() for o in outs], contexts=ctxs)
+
+
+def isotropic_alpha(xyz, orb, aux, **kw):
+    """ISOALPHA: alpha_xx, alpha_yy, alpha_zz (the selected Romberg values of finite_field with the
+    field along x, y and z), the isotropic mean and the anisotropy (Raman convention)."""
+    diag = []
+    for axis in range(3):
+        r = finite_field(xyz, orb, aux, axis=axis, **kw)
+        diag.append(r["alpha"][1][0])
+    iso, aniso = polarizability_invariants(*diag)
+    return dict(alpha_diag=tuple(diag), alpha_iso=iso, alpha_aniso=aniso)
+

@@ -119,3 +119,17 @@ def test_converged_h2_polarizabilities_match_oracle():
     assert abs(got["beta"][1][0]) < 1e-3 and abs(want["beta"][1][0]) < 1e-3
     g_got, g_want = got["gamma"][1][0], want["gamma"][1][0]
     assert abs(g_got - g_want) < 1e-2 * max(1.0, abs(g_want))
+
+
+def test_isotropic_alpha_of_h2_in_an_s_basis():
+    """ISOALPHA on H2 along z with s functions only: every x and y dipole integral vanishes (all
+    centres on the z axis), so alpha_xx = alpha_yy = 0 exactly, the isotropic mean is alpha_zz / 3
+    and the anisotropy is alpha_zz."""
+    from paper_2512_13550_gb300 import nlop
+    orb, aux = inputs.basis_3s_10aux()
+    xyz = inputs.chain(2, 1.4)
+    xyz = xyz - xyz.mean(axis=0)
+    r = nlop.isotropic_alpha(xyz, orb, aux, step=1e-4, npoint=9, nsteps=2000, gtol=1e-9)
+    axx, ayy, azz = r["alpha_diag"]
+    assert axx == 0.0 and ayy == 0.0 and azz > 1.0
+    assert abs(r["alpha_iso"] - azz / 3) < 1e-14 * azz and abs(r["alpha_aniso"] - azz) < 1e-14 * azz

@@ -54,3 +54,12 @@ def test_host_entry_points_reject_bad_arguments(lib):
     assert lib.nof_set_field(None, p) == nof.NOF_EINVAL
     assert lib.nof_dipole(None, p, p, p) == nof.NOF_EINVAL
     assert lib.nof_step_batch(None, 0, None, None, None, None, None, None, None) == nof.NOF_EINVAL
+
+
+def test_polarizability_invariants_match_oracle(lib):
+    for seed in range(5):
+        a = inputs.uniform(70 + seed, 3, 0.5, 9.0)
+        got = nof.polarizability_invariants(*a)
+        want = onlop.polarizability_invariants(*a)
+        assert abs(got[0] - want[0]) < 1e-15 * abs(want[0]) + 1e-300
+        assert abs(got[1] - want[1]) < 1e-14 * max(1.0, want[1])

@@ -136,3 +136,11 @@ def test_centrosymmetric_chain_dipole_is_odd_in_the_field():
     al, be, ga = r["D"]
     h = 2e-3 * 2.0 ** np.arange(4)
     np.testing.assert_allclose(be, -2.0 * r["mu"][0.0] / h ** 2, rtol=1e-6)
+
+
+def test_polarizability_invariants():
+    """Isotropic tensor: mean = the value, anisotropy 0; axially symmetric (a, a, c): anisotropy
+    |c - a| (the Raman-convention formula reduces to it)."""
+    assert nlop.polarizability_invariants(4.0, 4.0, 4.0) == (4.0, 0.0)
+    iso, an = nlop.polarizability_invariants(2.0, 2.0, 5.0)
+    assert abs(iso - 3.0) < 1e-15 and abs(an - 3.0) < 1e-15
