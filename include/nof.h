@@ -172,6 +172,23 @@ int nof_energy_grad_batch(nof_ctx* const* ctxs, int count, const double* const* 
                           const double* const* gamma, double* const* E, double* const* g_orb,
                           double* const* g_gamma, void* stream);
 
+/* ---- Nuclear gradient ----------------------------------------------------------------- */
+
+/* dE/dR (atomic units, device array [natom][3]) of the RI-PNOF energy at the state (C, gamma),
+ * for the geometry optimisation and dynamics the paper lists among DoNOF's capabilities (the
+ * paper prints no formula). The orbitals follow the nuclei through the connection
+ * C(x) = C (C^T S(x) C)^{-1/2}, which keeps them orthonormal:
+ *   dE/dx = sum P h^x - 2 sum (C lambda C^T) S^x + sum_P sum Gamma^P (uv|P)^x - sum Z V^x + V_nn^x
+ * with the one-particle density P = 2 C diag(n) C^T, the Lagrangian lambda of nof_energy_grad,
+ * Gamma^P = C Y^P C^T and Z from the fitting coefficients c = V^-1 (Q|pq)
+ * (Y^P_pq = 2 delta_pq sum_r A_pr c^P_rr - 2 B_pq c^P_pq, Z_PQ = sum A_pq c^P_pp c^Q_qq -
+ * B_pq c^P_pq c^Q_pq). At a converged state this is the physical force (negated). Integral
+ * derivatives of the s Gaussians are evaluated on the fly; the sums run in a fixed order.
+ * NOF_PREC_FP64 contexts only. Workspaces (about X nbf^2 doubles) are allocated on the first
+ * call. Stream-ordered. Errors: NOF_EINVAL (null pointer, split-precision context),
+ * NOF_ESTATE, NOF_ENOMEM. */
+int nof_nuclear_gradient(nof_ctx* ctx, const double* C, const double* gamma, double* grad);
+
 /* ---- Finite-field polarizability and hyperpolarizabilities (NLOPs subsection) ------------ */
 
 /* Static electric field F (atomic units, host array of 3: x, y, z), the EVEC input of the

@@ -82,6 +82,7 @@ SIGNATURES = {
                                          _P, _P]),
     "nof_mlp_adam": (ctypes.c_int, [ctypes.c_longlong, _P, _P, _P, _P, ctypes.c_int, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
+    "nof_nuclear_gradient": (ctypes.c_int, [_P, _P, _P, _P]),
     "nof_set_field": (ctypes.c_int, [_P, _P]),
     "nof_dipole": (ctypes.c_int, [_P, _P, _P, _P]),
     "nof_field_differences": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, _P, _P, _P]),
@@ -254,6 +255,7 @@ class Context:
                                           None if zarr is None else zarr.ctypes.data_as(ctypes.c_void_p),
                                           charge, mult, ctypes.byref(ob), ctypes.byref(ab)))
         self.sizes = self.query()
+        self.natom = int(xyz.shape[0])
         self.t = ctypes.c_int(0)
         return self.sizes
 
@@ -323,6 +325,14 @@ class Context:
         _check(load_library().nof_step(self._h, _dptr(C), _dptr(gamma), _dptr(m), _dptr(v),
                                        None if device_counter else ctypes.byref(self.t), _dptr(out)))
         return out
+
+    def nuclear_gradient(self, C, gamma, grad=None):
+        """dE/dR [natom][3] at (C, gamma) along the orbital connection (nof_nuclear_gradient)."""
+        import torch
+        natom = self.natom
+        grad = torch.empty(natom, 3, dtype=torch.float64, device="cuda") if grad is None else grad
+        _check(load_library().nof_nuclear_gradient(self._h, _dptr(C), _dptr(gamma), _dptr(grad)))
+        return grad
 
     def set_field(self, F):
         """Static field F = (Fx, Fy, Fz) in atomic units for every later call (nof_set_field)."""

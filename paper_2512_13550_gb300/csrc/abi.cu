@@ -105,6 +105,7 @@ void free_system(nof_ctx* c) {
     dfree(c->part); dfree(c->ggam); dfree(c->gorb);
     dfree(c->y); dfree(c->U); dfree(c->U2); dfree(c->tmpn); dfree(c->gwork);
     dfree(c->Dip); dfree(c->H0); dfree(c->vnn0); dfree(c->dipw); dfree(c->tdev);
+    dfree(c->Linv); dfree(c->gr_cfit); dfree(c->gr_Y); dfree(c->gr_Gam); dfree(c->gr_Z); dfree(c->gr_small);
     c->built = 0;
 }
 
@@ -377,7 +378,11 @@ int nof_build_B(nof_ctx* c, int natom, const double* xyz, const double* Z, int c
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) r = nof_cuda_fail(e, "build sync", __FILE__, __LINE__);
     }
-    cudaFree(M3); cudaFree(V2); cudaFree(Linv); cudaFree(Bp);
+    cudaFree(M3); cudaFree(V2); cudaFree(Bp);
+    if (r == NOF_OK && c->opt.precision == NOF_PREC_FP64)
+        c->Linv = Linv;  // kept for the nuclear gradient's fitting coefficients
+    else
+        cudaFree(Linv);
     if (r != NOF_OK) {
         free_system(c);
         return r;

@@ -84,6 +84,9 @@ struct nof_ctx {
     double *Dip, *H0, *vnn0, *dipw;
     // ADAM step counter on the device for nof_step with t == NULL (zero after nof_build_B)
     int* tdev;
+    // nuclear gradient (FP64 path): L^-1 of the Coulomb metric kept from set-up, and workspaces
+    // allocated on the first nof_nuclear_gradient
+    double *Linv, *gr_cfit, *gr_Y, *gr_Gam, *gr_Z, *gr_small;
     // dominant-kernel timing (nof_profile)
     int prof_on;
     const char* prof_name;
