@@ -45,11 +45,12 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["h50", "h200", "batch", "nlop"], default="h50",
+    ap.add_argument("--workload", choices=["h50", "h200", "batch", "nlop", "gradient"], default="h50",
                     help="h50: the single-geometry benchmark; h200: the 10 x 20 lattice (nbf 600, "
                          "naux 2000, nact 200); batch: many uneven H-chain frames evaluated "
                          "concurrently as one CUDA-graph launch; nlop: the finite-field polarizability "
-                         "and hyperpolarizabilities of H2 (21 field instances stepped together)")
+                         "and hyperpolarizabilities of H2 (21 field instances stepped together); gradient: "
+                         "the nuclear gradient of the H50 chain on the FP64 path")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-max", type=int, default=64, help="largest chain length in the batch")
     ap.add_argument("--no-graph", action="store_true",
@@ -331,6 +332,51 @@ def nlop_cpu_baseline(xyz, orb, aux, nfield=3):
             "sample": f"{done} oracle steps over the first {nfield} of the 21 fields in {dt:.1f} s"}
 
 
+def run_gradient(args):
+    """Nuclear gradients per second for the H50 chain of the h50 workload (FP64 path, the state of
+    the h50 workload: Loewdin orbitals of a seeded rotation, seeded gamma), L2 flushed before each
+    gradient, CUDA events on the context's stream."""
+    import torch
+    import paper_2512_13550_gb300 as nof
+    from paper_2512_13550_gb300 import inputs
+    xyz, orb, aux = workload(2, "h50")
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = nof.Context(precision=nof.PREC_FP64, stream=stream)
+    ctx.build_B(xyz, orb, aux)
+    s = ctx.sizes
+    C = ctx.lowdin(torch.tensor(inputs.random_orthogonal(s["nbf"], 0), dtype=torch.float64, device="cuda"))
+    gam = torch.tensor(inputs.random_gamma(s["ngamma"], 1), dtype=torch.float64, device="cuda")
+    grad = torch.empty(xyz.shape[0], 3, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    steps = max(1, min(args.steps, 20))
+    for _ in range(max(3, args.warmup)):
+        ctx.nuclear_gradient(C, gam, grad)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    l0 = nof.kernel_launches()
+    with ClockSampler(0) as clk:
+        for i in range(steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            ctx.nuclear_gradient(C, gam, grad)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = nof.kernel_launches() - l0
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    g = grad.cpu().numpy()
+    line = {"metric": "nuclear gradients/s (RI-PNOF7, FP64 path)", "value": steps / (ms / 1e3), "unit": "gradients/s",
+            "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup), "ms_per_step": ms / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (FP64 path)", "l2": "flushed (256 MiB write) before every gradient",
+                       "timing": "CUDA events on the context's stream around one gradient (J/K, Lagrangian, "
+                                 "fitting coefficients, Gamma, Z, integral-derivative contractions)"},
+            "result": {"max_abs_component": float(np.abs(g).max()), "net_force": float(np.abs(g.sum(axis=0)).max())},
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -339,6 +385,8 @@ def main():
         return run_batch(args)
     if args.workload == "nlop":
         return run_nlop(args)
+    if args.workload == "gradient":
+        return run_gradient(args)
     import torch
     import paper_2512_13550_gb300 as nof
     from paper_2512_13550_gb300 import inputs

@@ -19,6 +19,7 @@
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi52 = 34.98683665524972497;  // 2 pi^{5/2}
 
 __device__ __forceinline__ double g_boys0(double t) {
     if (t < 1e-8) return 1.0 - t / 3.0 + t * t / 10.0;
@@ -105,7 +106,8 @@ __global__ void __launch_bounds__(256) k_grad_1e_rows(Basis bs, const double* Pa
             for (int j = 0; j < bs.fn_nprim[v]; ++j) {
                 const double b = bs.pexp[bs.fn_first[v] + j], cb = bs.pcoef[bs.fn_first[v] + j];
                 const double p = a + b, mu = a * b / p, K = exp(-mu * ab2), w = ca * cb;
-                const double Sp = pow(kPi / p, 1.5) * K;
+                const double r = kPi / p;
+                const double Sp = r * sqrt(r) * K;
                 // overlap and kinetic: first-centre derivatives
                 const double fS = -2.0 * mu * Sp, fT = -2.0 * mu * mu * (5.0 - 2.0 * mu * ab2) * Sp;
                 for (int k = 0; k < 3; ++k) acc[k] += w * AB[k] * (Puv * fT - 2.0 * Wuv * fS);
@@ -170,7 +172,7 @@ __device__ __forceinline__ void three_center_pair(double a, double b, double w, 
                           (a * A[2] + b * B[2]) / p - Cc[2]};
     const double rho = p * q / (p + q);
     const double t = rho * (PC[0] * PC[0] + PC[1] * PC[1] + PC[2] * PC[2]);
-    const double pre = g * w * nq * 2.0 * pow(kPi, 2.5) / (p * q * sqrt(p + q));
+    const double pre = g * w * nq * kTwoPi52 / (p * q * sqrt(p + q));
     const double F0 = g_boys0(t), F1v = g_boys1(t);
     for (int k = 0; k < 3; ++k) {
         d1[k] += pre * (-2.0 * mu * AB[k] * K * F0 - 2.0 * rho * (a / p) * K * F1v * PC[k]);
@@ -178,50 +180,50 @@ __device__ __forceinline__ void three_center_pair(double a, double b, double w, 
     }
 }
 
-// F3[u] = sum_v sum_P Gamma^P_uv d(uv|P)/dA_u
-__global__ void __launch_bounds__(256) k_grad_3c_rows(Basis bs, const double* Gam, double* F3) {
+// One pass over the triples (u, v, P): block (u, chunk) takes basis function u and the aux
+// functions P of its chunk of 256, one per thread. F3p[u][chunk] = sum_v sum_P Gamma^P_uv
+// d(uv|P)/dA_u (fixed-order block sum) and HPu[u][P] = sum_v Gamma^P_uv d(uv|P)/dR_P (one
+// thread per P, so no reduction is needed); the sums over chunks and over u follow in order.
+__global__ void __launch_bounds__(256) k_grad_3c(Basis bs, const double* Gam, double* F3p, double* HPu) {
     __shared__ double red[3 * 256];
-    const int u = blockIdx.x, n = bs.n;
+    const int u = blockIdx.x, n = bs.n, X = bs.X;
     const double* A = bs.xyz + 3 * bs.fn_atom[u];
-    double acc[3] = {0.0, 0.0, 0.0}, dummy[3] = {0.0, 0.0, 0.0};
-    for (long long vP = threadIdx.x; vP < (long long)n * bs.X; vP += 256) {
-        const int P = (int)(vP / n), v = (int)(vP - (long long)P * n);
-        const double g = Gam[((long long)P * n + u) * n + v];
-        const double* B = bs.xyz + 3 * bs.fn_atom[v];
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int P = blockIdx.y * 256 + threadIdx.x; P < X && P < (int)(blockIdx.y + 1) * 256; P += 256) {
         const double* Cc = bs.xyz + 3 * bs.ax_atom[P];
         const double q = bs.axexp[P], nq = g_norm(q);
-        for (int i = 0; i < bs.fn_nprim[u]; ++i)
-            for (int j = 0; j < bs.fn_nprim[v]; ++j)
-                three_center_pair(bs.pexp[bs.fn_first[u] + i], bs.pexp[bs.fn_first[v] + j],
-                                  bs.pcoef[bs.fn_first[u] + i] * bs.pcoef[bs.fn_first[v] + j], A, B, Cc, q, nq, g,
-                                  acc, dummy);
+        double dP[3] = {0.0, 0.0, 0.0};
+        for (int v = 0; v < n; ++v) {
+            const double g = Gam[((long long)P * n + u) * n + v];
+            const double* B = bs.xyz + 3 * bs.fn_atom[v];
+            for (int i = 0; i < bs.fn_nprim[u]; ++i)
+                for (int j = 0; j < bs.fn_nprim[v]; ++j)
+                    three_center_pair(bs.pexp[bs.fn_first[u] + i], bs.pexp[bs.fn_first[v] + j],
+                                      bs.pcoef[bs.fn_first[u] + i] * bs.pcoef[bs.fn_first[v] + j], A, B, Cc, q, nq, g,
+                                      acc, dP);
+        }
+        for (int k = 0; k < 3; ++k) HPu[((long long)u * X + P) * 3 + k] = dP[k];
     }
     block_sum3(acc, red);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) F3[3 * u + k] = acc[k];
+        for (int k = 0; k < 3; ++k) F3p[((long long)u * gridDim.y + blockIdx.y) * 3 + k] = acc[k];
 }
 
-// HP[P] = sum_uv Gamma^P_uv d(uv|P)/dR_P
-__global__ void __launch_bounds__(256) k_grad_3c_aux(Basis bs, const double* Gam, double* HP) {
-    __shared__ double red[3 * 256];
-    const int P = blockIdx.x, n = bs.n;
-    const double* Cc = bs.xyz + 3 * bs.ax_atom[P];
-    const double q = bs.axexp[P], nq = g_norm(q);
-    double acc[3] = {0.0, 0.0, 0.0}, dummy[3] = {0.0, 0.0, 0.0};
-    for (long long uv = threadIdx.x; uv < (long long)n * n; uv += 256) {
-        const int u = (int)(uv / n), v = (int)(uv - (long long)u * n);
-        const double g = Gam[(long long)P * n * n + uv];
-        const double* A = bs.xyz + 3 * bs.fn_atom[u];
-        const double* B = bs.xyz + 3 * bs.fn_atom[v];
-        for (int i = 0; i < bs.fn_nprim[u]; ++i)
-            for (int j = 0; j < bs.fn_nprim[v]; ++j)
-                three_center_pair(bs.pexp[bs.fn_first[u] + i], bs.pexp[bs.fn_first[v] + j],
-                                  bs.pcoef[bs.fn_first[u] + i] * bs.pcoef[bs.fn_first[v] + j], A, B, Cc, q, nq, g,
-                                  dummy, acc);
+// HP[P] = sum_u HPu[u][P] in order of u; F3[u] = sum_c F3p[u][c] in order of c
+__global__ void k_grad_3c_sums(const double* HPu, const double* F3p, int n, int X, int nch, double* HP,
+                               double* F3) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < 3LL * X) {
+        double s = 0.0;
+        for (int u = 0; u < n; ++u) s += HPu[(long long)u * 3 * X + i];
+        HP[i] = s;
+    } else if (i < 3LL * X + 3LL * n) {
+        const long long j = i - 3LL * X;
+        const int u = (int)(j / 3), k = (int)(j % 3);
+        double s = 0.0;
+        for (int c = 0; c < nch; ++c) s += F3p[((long long)u * nch + c) * 3 + k];
+        F3[j] = s;
     }
-    block_sum3(acc, red);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) HP[3 * P + k] = acc[k];
 }
 
 // E2[P] = sum_Q Z_PQ d(P|Q)/dR_P
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(256) k_grad_2c_rows(Basis bs, const double* Zm
         const double D[3] = {Cp[0] - Cq[0], Cp[1] - Cq[1], Cp[2] - Cq[2]};
         const double rho = p * q / (p + q);
         const double t = rho * (D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
-        const double f = -Zm[(long long)P * X + Q] * np_ * g_norm(q) * 2.0 * pow(kPi, 2.5) / (p * q * sqrt(p + q)) *
+        const double f = -Zm[(long long)P * X + Q] * np_ * g_norm(q) * kTwoPi52 / (p * q * sqrt(p + q)) *
                          2.0 * rho * g_boys1(t);
         for (int k = 0; k < 3; ++k) acc[k] += f * D[k];
     }
@@ -322,7 +324,9 @@ extern "C" int nof_nuclear_gradient(nof_ctx* c, const double* C, const double* g
     NOF_TRY(galloc(&c->gr_Y, (size_t)(X * aa)));
     NOF_TRY(galloc(&c->gr_Gam, (size_t)(X * nn)));
     NOF_TRY(galloc(&c->gr_Z, (size_t)X * X));
-    NOF_TRY(galloc(&c->gr_small, (size_t)(2 * X * a + 3 * nn + 3 * (2 * n + natom + 2 * X))));
+    const int nch = (X + 255) / 256;
+    NOF_TRY(galloc(&c->gr_small, (size_t)(2 * X * a + 3 * nn + 3 * (2 * n + natom + 2 * X) + 3LL * n * X +
+                                          3LL * n * nch)));
     double* cd = c->gr_small;
     double* tXa = cd + (long long)X * a;
     double* Pao = tXa + (long long)X * a;
@@ -333,6 +337,8 @@ extern "C" int nof_nuclear_gradient(nof_ctx* c, const double* C, const double* g
     double* G = F3 + 3 * n;
     double* HP = G + 3 * natom;
     double* E2 = HP + 3 * X;
+    double* HPu = E2 + 3 * X;              // [n][X][3]
+    double* F3p = HPu + 3LL * n * X;       // [n][nch][3]
     // fitting coefficients c = L^-T b
     {
         Gemm64 g = mk(X, (int)aa, X, c->Linv, 1, X, c->b, 1, aa, c->gr_cfit, aa, c);
@@ -371,9 +377,9 @@ extern "C" int nof_nuclear_gradient(nof_ctx* c, const double* C, const double* g
     NOF_LAUNCH_CHECK();
     k_grad_1e_ops<<<natom, 256, 0, st>>>(bs, Pao, G);
     NOF_LAUNCH_CHECK();
-    k_grad_3c_rows<<<n, 256, 0, st>>>(bs, c->gr_Gam, F3);
+    k_grad_3c<<<dim3(n, nch), 256, 0, st>>>(bs, c->gr_Gam, F3p, HPu);
     NOF_LAUNCH_CHECK();
-    k_grad_3c_aux<<<X, 256, 0, st>>>(bs, c->gr_Gam, HP);
+    k_grad_3c_sums<<<blocks(3LL * (X + n)), 256, 0, st>>>(HPu, F3p, n, X, nch, HP, F3);
     NOF_LAUNCH_CHECK();
     k_grad_2c_rows<<<X, 256, 0, st>>>(bs, c->gr_Z, E2);
     NOF_LAUNCH_CHECK();
