@@ -12,6 +12,7 @@
 // so the result does not depend on scheduling). Derivatives with respect to the second centre of
 // a symmetric pair equal those with respect to the first after swapping the pair, which gives the
 // factors of 2 below; the aux centre of (uv|P) takes minus the sum of the other two.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -20,6 +21,10 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi52 = 34.98683665524972497;  // 2 pi^{5/2}
+// Screening: a primitive pair with mu |A-B|^2 > 39 has a Gaussian product exp(-mu |A-B|^2) below
+// 1.2e-17, and every integral and derivative of it carries that factor; such pairs are skipped
+// before any exponential is taken.
+constexpr double kScreenExponent = 39.0;
 
 __device__ __forceinline__ double g_boys0(double t) {
     if (t < 1e-8) return 1.0 - t / 3.0 + t * t / 10.0;
@@ -105,7 +110,9 @@ __global__ void __launch_bounds__(256) k_grad_1e_rows(Basis bs, const double* Pa
             const double a = bs.pexp[bs.fn_first[u] + i], ca = bs.pcoef[bs.fn_first[u] + i];
             for (int j = 0; j < bs.fn_nprim[v]; ++j) {
                 const double b = bs.pexp[bs.fn_first[v] + j], cb = bs.pcoef[bs.fn_first[v] + j];
-                const double p = a + b, mu = a * b / p, K = exp(-mu * ab2), w = ca * cb;
+                const double p = a + b, mu = a * b / p;
+                if (mu * ab2 > kScreenExponent) continue;
+                const double K = exp(-mu * ab2), w = ca * cb;
                 const double r = kPi / p;
                 const double Sp = r * sqrt(r) * K;
                 // overlap and kinetic: first-centre derivatives
@@ -130,13 +137,14 @@ __global__ void __launch_bounds__(256) k_grad_1e_rows(Basis bs, const double* Pa
         for (int k = 0; k < 3; ++k) F1[3 * u + k] = acc[k];
 }
 
-// G[C] = sum_uv P_uv dV^C_uv / dR_C (the operator centre)
-__global__ void __launch_bounds__(256) k_grad_1e_ops(Basis bs, const double* Pao, double* G) {
+// Gp[C][s] = sum over the pairs uv of slice s of P_uv dV^C_uv / dR_C (the operator centre);
+// block (C, s), the pairs strided over gridDim.y slices.
+__global__ void __launch_bounds__(256) k_grad_1e_ops(Basis bs, const double* Pao, double* Gp) {
     __shared__ double red[3 * 256];
     const int C = blockIdx.x, n = bs.n;
     const double* R = bs.xyz + 3 * C;
     double acc[3] = {0.0, 0.0, 0.0};
-    for (long long uv = threadIdx.x; uv < (long long)n * n; uv += 256) {
+    for (long long uv = blockIdx.y * 256LL + threadIdx.x; uv < (long long)n * n; uv += 256LL * gridDim.y) {
         const int u = (int)(uv / n), v = (int)(uv - (long long)u * n);
         const double* A = bs.xyz + 3 * bs.fn_atom[u];
         const double* B = bs.xyz + 3 * bs.fn_atom[v];
@@ -146,7 +154,9 @@ __global__ void __launch_bounds__(256) k_grad_1e_ops(Basis bs, const double* Pao
             const double a = bs.pexp[bs.fn_first[u] + i], ca = bs.pcoef[bs.fn_first[u] + i];
             for (int j = 0; j < bs.fn_nprim[v]; ++j) {
                 const double b = bs.pexp[bs.fn_first[v] + j], cb = bs.pcoef[bs.fn_first[v] + j];
-                const double p = a + b, K = exp(-a * b / p * ab2);
+                const double p = a + b;
+                if (a * b / p * ab2 > kScreenExponent) continue;
+                const double K = exp(-a * b / p * ab2);
                 const double PC[3] = {(a * A[0] + b * B[0]) / p - R[0], (a * A[1] + b * B[1]) / p - R[1],
                                       (a * A[2] + b * B[2]) / p - R[2]};
                 const double t = p * (PC[0] * PC[0] + PC[1] * PC[1] + PC[2] * PC[2]);
@@ -157,7 +167,7 @@ __global__ void __launch_bounds__(256) k_grad_1e_ops(Basis bs, const double* Pao
     }
     block_sum3(acc, red);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) G[3 * C + k] = acc[k];
+        for (int k = 0; k < 3; ++k) Gp[((long long)C * gridDim.y + blockIdx.y) * 3 + k] = acc[k];
 }
 
 // One primitive pair of (uv|P): accumulate the first-centre derivative (w.r.t. A_u) into d1 and
@@ -167,7 +177,9 @@ __device__ __forceinline__ void three_center_pair(double a, double b, double w, 
                                                   double dP[3]) {
     const double p = a + b, mu = a * b / p;
     const double AB[3] = {A[0] - B[0], A[1] - B[1], A[2] - B[2]};
-    const double K = exp(-mu * (AB[0] * AB[0] + AB[1] * AB[1] + AB[2] * AB[2]));
+    const double mab2 = mu * (AB[0] * AB[0] + AB[1] * AB[1] + AB[2] * AB[2]);
+    if (mab2 > kScreenExponent) return;
+    const double K = exp(-mab2);
     const double PC[3] = {(a * A[0] + b * B[0]) / p - Cc[0], (a * A[1] + b * B[1]) / p - Cc[1],
                           (a * A[2] + b * B[2]) / p - Cc[2]};
     const double rho = p * q / (p + q);
@@ -249,15 +261,15 @@ __global__ void __launch_bounds__(256) k_grad_2c_rows(Basis bs, const double* Zm
 }
 
 // grad[A] = 2 sum_{u on A} (F1 + F3)[u] + G[A] + sum_{P on A} (HP - 2 E2)[P] + dV_nn/dR_A
-__global__ void k_grad_assemble(Basis bs, const double* F1, const double* F3, const double* G, const double* HP,
-                                const double* E2, double* grad) {
+__global__ void k_grad_assemble(Basis bs, const double* F1, const double* F3, const double* Gp, int nslice,
+                                const double* HP, const double* E2, double* grad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 3 * bs.natom) return;
     const int A = i / 3, k = i - 3 * A;
     double s = 0.0;
     for (int u = 0; u < bs.n; ++u)
         if (bs.fn_atom[u] == A) s += 2.0 * (F1[3 * u + k] + F3[3 * u + k]);
-    s += G[3 * A + k];
+    for (int sl = 0; sl < nslice; ++sl) s += Gp[((long long)A * nslice + sl) * 3 + k];
     for (int P = 0; P < bs.X; ++P)
         if (bs.ax_atom[P] == A) s += HP[3 * P + k] - 2.0 * E2[3 * P + k];
     const double* RA = bs.xyz + 3 * A;
@@ -325,8 +337,9 @@ extern "C" int nof_nuclear_gradient(nof_ctx* c, const double* C, const double* g
     NOF_TRY(galloc(&c->gr_Gam, (size_t)(X * nn)));
     NOF_TRY(galloc(&c->gr_Z, (size_t)X * X));
     const int nch = (X + 255) / 256;
-    NOF_TRY(galloc(&c->gr_small, (size_t)(2 * X * a + 3 * nn + 3 * (2 * n + natom + 2 * X) + 3LL * n * X +
-                                          3LL * n * nch)));
+    const int nslice = (int)std::min<long long>(32, (nn + 4095) / 4096);
+    NOF_TRY(galloc(&c->gr_small, (size_t)(2 * X * a + 3 * nn + 3 * (2 * n + 2 * X) + 3LL * n * X + 3LL * n * nch +
+                                          3LL * natom * 32)));
     double* cd = c->gr_small;
     double* tXa = cd + (long long)X * a;
     double* Pao = tXa + (long long)X * a;
@@ -334,11 +347,11 @@ extern "C" int nof_nuclear_gradient(nof_ctx* c, const double* C, const double* g
     double* tn = Wao + nn;
     double* F1 = tn + nn;
     double* F3 = F1 + 3 * n;
-    double* G = F3 + 3 * n;
-    double* HP = G + 3 * natom;
+    double* HP = F3 + 3 * n;
     double* E2 = HP + 3 * X;
     double* HPu = E2 + 3 * X;              // [n][X][3]
     double* F3p = HPu + 3LL * n * X;       // [n][nch][3]
+    double* G = F3p + 3LL * n * nch;       // [natom][nslice][3]
     // fitting coefficients c = L^-T b
     {
         Gemm64 g = mk(X, (int)aa, X, c->Linv, 1, X, c->b, 1, aa, c->gr_cfit, aa, c);
@@ -375,7 +388,7 @@ extern "C" int nof_nuclear_gradient(nof_ctx* c, const double* C, const double* g
     Basis bs{c->fn_atom, c->fn_first, c->fn_nprim, c->pexp, c->pcoef, c->xyz, c->Z, n, natom, c->ax_atom, c->axexp, X};
     k_grad_1e_rows<<<n, 256, 0, st>>>(bs, Pao, Wao, F1);
     NOF_LAUNCH_CHECK();
-    k_grad_1e_ops<<<natom, 256, 0, st>>>(bs, Pao, G);
+    k_grad_1e_ops<<<dim3(natom, nslice), 256, 0, st>>>(bs, Pao, G);
     NOF_LAUNCH_CHECK();
     k_grad_3c<<<dim3(n, nch), 256, 0, st>>>(bs, c->gr_Gam, F3p, HPu);
     NOF_LAUNCH_CHECK();
@@ -383,7 +396,7 @@ extern "C" int nof_nuclear_gradient(nof_ctx* c, const double* C, const double* g
     NOF_LAUNCH_CHECK();
     k_grad_2c_rows<<<X, 256, 0, st>>>(bs, c->gr_Z, E2);
     NOF_LAUNCH_CHECK();
-    k_grad_assemble<<<blocks(3 * natom, 128), 128, 0, st>>>(bs, F1, F3, G, HP, E2, grad);
+    k_grad_assemble<<<blocks(3 * natom, 128), 128, 0, st>>>(bs, F1, F3, G, nslice, HP, E2, grad);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
