@@ -94,7 +94,7 @@ def test_h50_plain_parity():
 
 
 def test_step_trajectory_h4():
-    """Config-1 style run: 20 alternating steps from a seeded orthonormal C and seeded gamma."""
+    """H4 run: 20 alternating steps from a seeded orthonormal C and seeded gamma."""
     sysm = systems.h4()
     o = sysm.oracle
     ctx = _ctx(sysm)
