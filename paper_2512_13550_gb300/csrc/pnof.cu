@@ -27,11 +27,8 @@ __device__ __forceinline__ double sgn1(double x) { return x >= 0.0 ? 1.0 : -1.0;
 
 // One thread per subspace g: s = sqrt(n), t = sqrt(1-n) and their derivatives with respect to
 // the N_g angles of the subspace (ds[p * ncwo + slot]).
-__global__ void k_occupations(const double* gamma, int npair, int ncwo, double* s, double* t,
-                              double* ds, double* dt) {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= npair) return;
-    const double rt2 = 1.4142135623730950488;
+__device__ void occupations_trig(int g, const double* gamma, int npair, int ncwo, double* s, double* t, double* ds,
+                                 double* dt) {    const double rt2 = 1.4142135623730950488;
     double th0 = gamma[g];
     double s0 = sin(th0), c0 = cos(th0);
     double sg = sqrt(0.5 * (1.0 + c0 * c0));
@@ -78,6 +75,13 @@ __global__ void k_occupations(const double* gamma, int npair, int ncwo, double* 
     }
 }
 
+__global__ void k_occupations(const double* gamma, int npair, int ncwo, double* s, double* t,
+                              double* ds, double* dt) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npair) return;
+    occupations_trig(g, gamma, npair, ncwo, s, t, ds, dt);
+}
+
 // Softmax mapping (isoftmax = 1), same outputs as k_occupations. Subspace g has the variables
 // x_k = gamma[k * npair + g] (k < ncwo), x_k belonging to the weak orbital p_{k+1}:
 //   Z = 1 + sum_k exp(x_k),  n_g = 1 / Z,  n_{p_i} = exp(x_{i-1}) / Z,
@@ -85,11 +89,8 @@ __global__ void k_occupations(const double* gamma, int npair, int ncwo, double* 
 //   d sqrt(1 - n_q) = -sqrt(n_q) d sqrt(n_q) / sqrt(1 - n_q).
 // The exponentials are taken relative to max(0, max_k x_k) so that none overflows, and 1 - n_q
 // is summed from the other orbitals' weights (no cancellation).
-__global__ void k_occupations_softmax(const double* gamma, int npair, int ncwo, double* s, double* t,
-                                      double* ds, double* dt) {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= npair) return;
-    double m = 0.0;
+__device__ void occupations_softmax(int g, const double* gamma, int npair, int ncwo, double* s, double* t,
+                                    double* ds, double* dt) {    double m = 0.0;
     for (int k = 0; k < ncwo; ++k) m = fmax(m, gamma[k * npair + g]);
     const double w0 = exp(-m);  // weight of the strong orbital, exp(0 - m)
     double z = w0;
@@ -112,14 +113,17 @@ __global__ void k_occupations_softmax(const double* gamma, int npair, int ncwo, 
     }
 }
 
+__global__ void k_occupations_softmax(const double* gamma, int npair, int ncwo, double* s, double* t,
+                                      double* ds, double* dt) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= npair) return;
+    occupations_softmax(g, gamma, npair, ncwo, s, t, ds, dt);
+}
+
 // A and B of Eq. PNOF for every active pair (p, q); optionally also as double-floats (hi, lo) for
 // the split path (Adf, Bcdf may be null).
-__global__ void k_coefficients(const double* s, const double* t, const int* pair, const int* slot,
-                               int a, int ipnof, double* occ, double* A, double* Bc, float2* Adf,
-                               float2* Bcdf) {
-    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= (long long)a * a) return;
-    int p = (int)(idx / a), q = (int)(idx % a);
+__device__ void coefficient_one(long long idx, const double* s, const double* t, const int* pair, const int* slot,
+                                int a, int ipnof, double* occ, double* A, double* Bc, float2* Adf, float2* Bcdf) {    int p = (int)(idx / a), q = (int)(idx % a);
     double np = s[p] * s[p], nq = s[q] * s[q];
     if (q == 0) occ[p] = np;
     double av, bv;
@@ -143,6 +147,14 @@ __global__ void k_coefficients(const double* s, const double* t, const int* pair
         Adf[idx] = make_float2(ah, (float)(av - (double)ah));
         Bcdf[idx] = make_float2(bh, (float)(bv - (double)bh));
     }
+}
+
+__global__ void k_coefficients(const double* s, const double* t, const int* pair, const int* slot,
+                               int a, int ipnof, double* occ, double* A, double* Bc, float2* Adf,
+                               float2* Bcdf) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)a * a) return;
+    coefficient_one(idx, s, t, pair, slot, a, ipnof, occ, A, Bc, Adf, Bcdf);
 }
 
 // hpp_p = sum_mu C_mu,p (H C)_mu,p, one warp per p
@@ -229,13 +241,9 @@ __global__ void k_orbital_gradient(const double* lam, int n, int a, double* g) {
 // Partial derivatives of E with respect to n_p, c_p and Phi_p, and the energy row
 // E_p = 2 n_p h_pp + sum_q (A_pq J_pq - B_pq K_pq), one warp per active orbital p
 // (out [4][a]: dE/dn, dE/dc, dE/dPhi, E_p).
-__global__ void k_dE_parts(const double* s, const double* t, const int* pair, const int* slot,
-                           const double* hpp, const double* J, const double* K, const double* A,
-                           const double* Bc, int a, int ipnof, double* out) {
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= a) return;
-    int p = warp;
-    double sn = 0.0, sc = 0.0, sf = 0.0, se = 0.0;
+__device__ void dE_parts_warp(int p, int lane, const double* s, const double* t, const int* pair, const int* slot,
+                              const double* hpp, const double* J, const double* K, const double* A,
+                              const double* Bc, int a, int ipnof, double* out) {    double sn = 0.0, sc = 0.0, sf = 0.0, se = 0.0;
     for (int q = lane; q < a; q += 32) {
         const long long pq = (long long)p * a + q;
         double Jpq = J[pq], Kpq = K[pq];
@@ -263,8 +271,32 @@ __global__ void k_dE_parts(const double* s, const double* t, const int* pair, co
     }
 }
 
+__global__ void k_dE_parts(const double* s, const double* t, const int* pair, const int* slot,
+                           const double* hpp, const double* J, const double* K, const double* A,
+                           const double* Bc, int a, int ipnof, double* out) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= a) return;
+    int p = warp;
+    dE_parts_warp(p, lane, s, t, pair, slot, hpp, J, K, A, Bc, a, ipnof, out);
+}
+
 // dE/dgamma for gamma index k = i * npair + g: sum over the orbitals of subspace g. Warp 0 of
 // block 0 also forms E = V_nn + sum_p E_p in a fixed order.
+// dE/dgamma_k by the chain rule through sqrt(n), c and Phi of the orbitals of its subspace.
+__device__ double gamma_chain_one(int k, const double* s, const double* t, const double* ds, const double* dt,
+                                  const int* slot, const double* parts, int npair, int ncwo, int a) {
+    int i = k / npair, g = k % npair;
+    double acc = 0.0;
+    for (int m = 0; m <= ncwo; ++m) {
+        int p = (m == 0) ? g : npair + (m - 1) * npair + (npair - 1 - g);
+        double dsk = ds[p * ncwo + i], dtk = dt[p * ncwo + i];
+        double sign = slot[p] == 0 ? 1.0 : -1.0;
+        acc += parts[p] * 2.0 * s[p] * dsk + parts[a + p] * sign * dsk +
+               parts[2 * a + p] * (dsk * t[p] + s[p] * dtk);
+    }
+    return acc;
+}
+
 __global__ void k_gamma_chain(const double* s, const double* t, const double* ds, const double* dt,
                               const int* slot, const double* parts, int npair, int ncwo, int a,
                               const double* vnn, double* E, double* out) {
@@ -276,16 +308,39 @@ __global__ void k_gamma_chain(const double* s, const double* t, const double* ds
     }
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= npair * ncwo) return;
-    int i = k / npair, g = k % npair;
-    double acc = 0.0;
-    for (int m = 0; m <= ncwo; ++m) {
-        int p = (m == 0) ? g : npair + (m - 1) * npair + (npair - 1 - g);
-        double dsk = ds[p * ncwo + i], dtk = dt[p * ncwo + i];
-        double sign = slot[p] == 0 ? 1.0 : -1.0;
-        acc += parts[p] * 2.0 * s[p] * dsk + parts[a + p] * sign * dsk +
-               parts[2 * a + p] * (dsk * t[p] + s[p] * dtk);
+    out[k] = gamma_chain_one(k, s, t, ds, dt, slot, parts, npair, ncwo, a);
+}
+
+// The ON update of nof_step (`iters` steepest-descent steps on gamma with J, K and h_pp fixed)
+// in one block for systems with a <= 256: each iteration runs the occupations, the coefficients,
+// the energy parts, the chain rule and the descent through the same device functions as the
+// separate kernels, with block barriers between them, so the results are the same bits as those
+// of the launch-per-kernel loop in a single launch instead of five per iteration.
+__global__ void __launch_bounds__(1024) k_on_update_fused(double* gamma, int npair, int ncwo, int isoftmax,
+                                                         double* s, double* t, double* ds, double* dt,
+                                                         const int* pair, const int* slot, int a, int ipnof,
+                                                         double* occ, double* A, double* Bc, float2* Adf,
+                                                         float2* Bcdf, const double* hpp, const double* J,
+                                                         const double* K, double* parts, double* ggam,
+                                                         double lr, int iters) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    const int ng = npair * ncwo;
+    for (int it = 0; it < iters; ++it) {
+        for (int g = tid; g < npair; g += blockDim.x) {
+            if (isoftmax) occupations_softmax(g, gamma, npair, ncwo, s, t, ds, dt);
+            else occupations_trig(g, gamma, npair, ncwo, s, t, ds, dt);
+        }
+        __syncthreads();
+        for (long long idx = tid; idx < (long long)a * a; idx += blockDim.x)
+            coefficient_one(idx, s, t, pair, slot, a, ipnof, occ, A, Bc, Adf, Bcdf);
+        __syncthreads();
+        for (int p = warp; p < a; p += nw) dE_parts_warp(p, lane, s, t, pair, slot, hpp, J, K, A, Bc, a, ipnof, parts);
+        __syncthreads();
+        for (int k = tid; k < ng; k += blockDim.x) ggam[k] = gamma_chain_one(k, s, t, ds, dt, slot, parts, npair, ncwo, a);
+        __syncthreads();
+        for (int k = tid; k < ng; k += blockDim.x) gamma[k] -= lr * ggam[k];
+        __syncthreads();
     }
-    out[k] = acc;
 }
 
 __global__ void k_gamma_descent(double* gamma, const double* grad, double lr, int ng) {
@@ -506,6 +561,17 @@ int plain_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad)
 // J, K and h_pp of the current orbitals held fixed.
 int pnof_on_update(nof_ctx* c, double* gamma) {
     cudaStream_t st = c->stream;
+    if (c->nact <= 256) {  // one block does every iteration
+        if (c->opt.on_iters <= 0) return NOF_OK;
+        float2 *Adf = nullptr, *Bcdf = nullptr;
+        fast_coefficient_buffers(c, &Adf, &Bcdf);
+        k_on_update_fused<<<1, 1024, 0, st>>>(gamma, c->npair, c->opt.ncwo, c->opt.isoftmax, c->s, c->t, c->ds, c->dt,
+                                               c->pair, c->slot, c->nact, c->opt.ipnof, c->occ, c->A, c->Bc, Adf,
+                                               Bcdf, c->hpp, c->J, c->K, c->part, c->ggam, c->opt.on_lr,
+                                               c->opt.on_iters);
+        NOF_LAUNCH_CHECK();
+        return NOF_OK;
+    }
     for (int it = 0; it < c->opt.on_iters; ++it) {
         NOF_TRY(pnof_occupations(c, gamma));
         NOF_TRY(pnof_gamma_grad(c, c->ggam, c->stream));
