@@ -5,8 +5,9 @@ The paper lists geometry optimisation (OPTGEO) and an interface for ab initio mo
 among DoNOF's capabilities without printing their algorithms. Readings:
   * every geometry gets the converged state of the library's alternating steps from the core
     guess and gamma = 0.3, stopped at the first check (every `check` steps) where the step
-    reports ||g|| < gtol (as in nlop.run); the energy and the analytic gradient (gradient.py)
-    are taken at that state;
+    reports ||g|| < gtol (as in nlop.run; gtol = 1e-8 by default: a tighter threshold meets the
+    rounding floor of the steps, and further ADAM steps drift off the minimum); the energy and
+    the analytic gradient (gradient.py) are taken at that state;
   * optimisation: BFGS on the Cartesian coordinates with the inverse Hessian started at
     I / hess0, each step scaled down to at most `max_step` bohr, stopping when the largest force
     component is below ftol;
@@ -21,7 +22,7 @@ import numpy as np
 from . import gradient, integrals, pnof, reference, ri, step
 
 
-def converged_point(orb, aux, xyz, ncwo=1, ipnof=7, gtol=1e-9, check=25, max_steps=4000, Z=None):
+def converged_point(orb, aux, xyz, ncwo=1, ipnof=7, gtol=1e-8, check=25, max_steps=4000, Z=None):
     """(E, dE/dR [natom][3], steps) at the converged state of geometry xyz."""
     S, T, V = integrals.one_electron(orb, xyz, Z)
     H = T + V
