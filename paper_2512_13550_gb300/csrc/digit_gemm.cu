@@ -195,8 +195,9 @@ __host__ __device__ constexpr int stage_pitch(int BN) { return (BN >= 32 ? BN / 
 template <int ND>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
 k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, DigitGemmArgs g) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // 32-byte swizzling repeats every 256 bytes: every operand block starts on a 256-byte boundary
+    extern __shared__ __align__(256) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 255) & ~(uintptr_t)255);
     const int BN = g.BN, S = g.stages, NB = g.nbuf;
     const uint32_t a_stage_bytes = (uint32_t)ND * kStageAtoms * kBM * 32u;
     const uint32_t b_stage_bytes = (uint32_t)ND * kStageAtoms * (uint32_t)BN * 32u;
@@ -482,7 +483,7 @@ constexpr size_t kSmemLimit = 227 * 1024;
 
 size_t smem_bytes(int BN, int stages, int nd) {
     return (size_t)stages * nd * kStageAtoms * 32 * (kBM + BN) + 8 * (2 * stages + 4) + 16 + 16 +
-           (size_t)kEpiWarps * 32 * stage_pitch(BN) * sizeof(float2) + 1024;
+           (size_t)kEpiWarps * 32 * stage_pitch(BN) * sizeof(float2) + 256;
 }
 
 }  // namespace
