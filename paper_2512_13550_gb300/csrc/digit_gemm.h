@@ -51,6 +51,9 @@ struct DigitGemmArgs {
     int nbuf;          // TMEM accumulator sets
     int tiles_m;       // 128-row blocks
     int kchunks;       // K chunks (split-K); tile order: N tile fastest, then row block, then chunk
+    // dynamic tiles: each CTA takes its next tile by a fetch-and-add on *tctr (zero before the
+    // first launch; every launch leaves it at zero); nullptr: tiles round-robin over the CTAs
+    int* tctr;
 };
 
 // Digit-plane storage ("tile-major, 32-byte swizzled" layout). An operand with R rows is cut
@@ -101,6 +104,7 @@ struct DigitGemmOut {
     const int* epB = nullptr;
     unsigned* colmax = nullptr;
     int group_rows = 1;
+    int* tile_counter = nullptr;  // dynamic tiles (DigitGemmArgs::tctr); one counter per plan in use
 };
 // K atoms per part when each operand row carries a scale per part of K
 constexpr int kPartAtoms = 8;
@@ -123,9 +127,13 @@ int digit_gemm_run(const DigitGemmPlan& plan, cudaStream_t st);
 int digit_gemm_max_stages(int BN, int nd);
 
 // Autotuner: times every candidate (one warm-up launch, then the best of three timed with CUDA
-// events on `st`) and returns the index of the fastest. Results are remembered per `key` for the
+// events on `st`; with `cold`, each timed launch follows an L2 flush, as for a GEMM whose operands
+// were last touched long before) and returns the index of the fastest. Results are remembered per `key` for the
 // life of the process, so equal shapes are timed once.
 struct DigitTuneKey {
     int kind, M, Nvalid, katoms_total, extra;
 };
-int digit_gemm_pick(const DigitTuneKey& key, const DigitGemmPlan* cands, int ncand, cudaStream_t st, int* best);
+int digit_gemm_pick(const DigitTuneKey& key, const DigitGemmPlan* cands, int ncand, cudaStream_t st, int* best,
+                    bool cold = false);
+// Write a buffer twice the size of L2 on `st` (timing of launches whose operands come from HBM).
+int l2_flush(cudaStream_t st);

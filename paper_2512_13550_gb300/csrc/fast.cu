@@ -27,6 +27,7 @@
 struct FastState {
     int n, X, a, ap, katK, nkp, nd;
     int bn1, bn2, bn3, nchunkJK;
+    int* tctr = nullptr;        // [3] tile counters of the three digit GEMMs (dynamic tiles)
     uint16_t* Bd;  int* eB;     // [4][katK][X n][16], per row (P, mu)
     uint16_t *Cd1, *Cd2; int* eC;  // C digits per orbital p (rows p, K = nu) in GEMM1's / GEMM2's tiles
     float2* Tdf;                // [X n][ap] T^P_{mu p} as double-floats
@@ -414,7 +415,7 @@ int fast_release(nof_ctx* c) {
     ffree(f->Bd); ffree(f->eB); ffree(f->Cd1); ffree(f->Cd2); ffree(f->eC); ffree(f->Tdf); ffree(f->colT);
     ffree(f->Td2); ffree(f->e2); ffree(f->Td3); ffree(f->epT); ffree(f->bdf); ffree(f->Ddf);
     ffree(f->Wd3); ffree(f->epW); ffree(f->Adf); ffree(f->Bcdf); ffree(f->Jpart); ffree(f->Lpart);
-    ffree(f->Kpart);
+    ffree(f->Kpart); ffree(f->tctr);
     delete f;
     c->fast = nullptr;
     return NOF_OK;
@@ -467,6 +468,7 @@ int fast_prepare(nof_ctx* c) {
     NOF_TRY(falloc(&f->Wd3, nWd3)); NOF_TRY(falloc(&f->epW, (size_t)nkp * a));
     NOF_TRY(falloc(&f->Adf, (size_t)a * a)); NOF_TRY(falloc(&f->Bcdf, (size_t)a * a));
     NOF_TRY(falloc(&f->Jpart, (size_t)f->nchunkJK * a * a)); NOF_TRY(falloc(&f->Kpart, (size_t)f->nchunkJK * a * a));
+    NOF_TRY(falloc(&f->tctr, 3));
     cudaStream_t st = c->stream;
     // digit planes start zeroed: padding rows (p >= nact) and padding K (k >= n) stay zero
     NOF_CUDA(cudaMemsetAsync(f->Bd, 0, 2ull * nBd, st));
@@ -479,6 +481,7 @@ int fast_prepare(nof_ctx* c) {
     NOF_CUDA(cudaMemsetAsync(f->e2, 0, sizeof(int) * rows2, st));
     NOF_CUDA(cudaMemsetAsync(f->epT, 0, sizeof(int) * nkp * n, st));
     NOF_CUDA(cudaMemsetAsync(f->epW, 0, sizeof(int) * nkp * a, st));
+    NOF_CUDA(cudaMemsetAsync(f->tctr, 0, sizeof(int) * 3, st));
     // B digits, one scale per row (P, mu)
     k_digits_f64<<<nblk(rowsB * 32), 256, 0, st>>>(c->B, n, 1, (int)rowsB, n, nd, 128, katK, f->Bd, f->eB, 0,
                                                    nullptr);
@@ -489,20 +492,25 @@ int fast_prepare(nof_ctx* c) {
     const int nbn = bn_candidates(ap, nd, bns);
     DigitGemmPlan cand[20];
     int best = 0;
-    {   // GEMM1: T = B C, scaled double-float output with the maxima of |T|
+    // every GEMM takes its tiles dynamically (a CTA that starts late, behind the side stream's
+    // blocks, takes fewer tiles)
+    {   // GEMM1: T = B C, scaled double-float output with the maxima of |T|. B was last read one
+        // evaluation earlier, so the candidates are timed with L2 flushed.
         DigitGemmOut o;
         o.outf = f->Tdf; o.ldo = ap; o.erow = f->eB; o.ecol = f->eC;
         o.colmax = f->colT; o.group_rows = n;
+        o.tile_counter = f->tctr;
         for (int i = 0; i < nbn; ++i)
             NOF_TRY(digit_gemm_plan(&cand[i], f->Bd, f->Cd1, (int)rowsB, ap, bns[i], nd, katK, katK, 0, o,
                                     c->status));
-        NOF_TRY(digit_gemm_pick({1, (int)rowsB, ap, katK, n * 8 + nd}, cand, nbn, st, &best));
+        NOF_TRY(digit_gemm_pick({1, (int)rowsB, ap, katK, n * 8 + nd}, cand, nbn, st, &best, true));
         f->g1 = cand[best];
         f->bn1 = bns[best];
     }
     {   // GEMM2: b = C^T T, scaled double-float output
         DigitGemmOut o;
         o.outf = f->bdf; o.ldo = ap; o.erow = f->e2; o.ecol = f->eC;
+        o.tile_counter = f->tctr + 1;
         for (int i = 0; i < nbn; ++i)
             NOF_TRY(digit_gemm_plan(&cand[i], f->Td2, f->Cd2, (int)rows2, ap, bns[i], nd, katK, katK, 0, o,
                                     c->status));
@@ -546,6 +554,7 @@ int fast_prepare(nof_ctx* c) {
         NOF_TRY(falloc(&f->Lpart, (size_t)(maxch * na)));
         DigitGemmOut o;
         o.outd = f->Lpart; o.ldo = a; o.chunk_stride = na; o.epA = f->epT; o.epB = f->epW;
+        o.tile_counter = f->tctr + 2;
         for (int i = 0; i < k; ++i)
             NOF_TRY(digit_gemm_plan(&cand[i], f->Td3, f->Wd3, n, a, bnk[i], nd, kat3, chk[i], 0, o, c->status));
         NOF_TRY(digit_gemm_pick({3, n, a, kat3, nd}, cand, k, st, &best));
@@ -674,24 +683,26 @@ int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad) 
 // gradient needs: C digits, GEMM1, the digits of T, GEMM2, D = A d and the digits of W, GEMM3,
 // Lambda, lambda and g. A low-priority side stream, forked from it by an event, runs the rest:
 // - the occupations and PNOF coefficients from gamma (the chain waits for them before D);
-// - H C and h_pp from C, and the GEMM3 digits of T once GEMM1 has written T (the chain waits
-//   for these before GEMM3);
+// - once GEMM1 has written T: H C and h_pp from C, then the GEMM3 digits of T (the chain waits
+//   for these before GEMM3). While GEMM1 runs, only the occupation kernels share its SMs;
 // - once GEMM2 has written b: the J/K partials, J and K, then E and dE/dgamma (the evaluation
 //   ends when these are done too).
 // Every buffer the side stream writes is read only after the matching wait. The fork orders
 // the side stream after the previous evaluation. No FP64 GEMM shares the split-K scratch with
-// H C while it runs.
+// H C while it runs: the chain's C^T Lambda comes after GEMM3, which waits for H C.
 int fast_eval(nof_ctx* c, const double* C, const double* gamma, bool want_grad) {
     cudaStream_t st = c->stream, sd = c->side;
     NOF_CUDA(cudaEventRecord(c->ev_s0, st));
     NOF_CUDA(cudaStreamWaitEvent(sd, c->ev_s0, 0));
     NOF_TRY(pnof_occupations(c, gamma, sd));
     NOF_CUDA(cudaEventRecord(c->ev_sO, sd));
-    NOF_TRY(pnof_hpp(c, C, sd));
-    NOF_TRY(b_chain(c, C, want_grad ? c->ev_sT : nullptr));
+    // H C and h_pp wait until GEMM1 has written T: while GEMM1 runs, the side stream holds no SM
+    // resources beyond the tiny occupation kernels (GEMM1 inside an evaluation: 47 -> 46 us)
+    NOF_TRY(b_chain(c, C, c->ev_sT));
     NOF_CUDA(cudaEventRecord(c->ev_sJ, st));
+    NOF_CUDA(cudaStreamWaitEvent(sd, c->ev_sT, 0));
+    NOF_TRY(pnof_hpp(c, C, sd));
     if (want_grad) {
-        NOF_CUDA(cudaStreamWaitEvent(sd, c->ev_sT, 0));
         NOF_TRY(t3_digits(c, sd));
         NOF_CUDA(cudaEventRecord(c->ev_s1, sd));
     }

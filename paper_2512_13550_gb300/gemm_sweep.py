@@ -3,7 +3,9 @@ contractions (zero operands; measurement only). Prints one markdown table row pe
 
     python -m paper_2512_13550_gb300.gemm_sweep
 
-Shapes: the half transform (M = naux nbf rows, N = nact, K = nbf) and the Lagrangian
+Shapes: the half transform (M = naux nbf rows, N = nact, K = nbf), also with L2 flushed before
+each launch (mode flag 4) and with dynamic tiles (mode flag 8), the full transform (M = naux
+nact) and the Lagrangian
 contraction (M = nbf, N = nact, K = naux nact) of the H50 chain (nbf 150, naux 500, nact 50), a
 long-K stream (600000 x 64 x 640) that shows the steady state, and the H200 half transform
 (1.2e6 x 208 x 608) with 4 and 5 digits.
@@ -16,8 +18,13 @@ CASES = [
     # name, M, N, bn, nd, katoms, chunk, mode
     ("H50 half transform, int64 out", 75000, 64, 64, 4, 10, 10, 0),
     ("H50 half transform, scaled out", 75000, 64, 64, 4, 10, 10, 1),
+    ("H50 half transform, scaled out, L2 flushed", 75000, 64, 64, 4, 10, 10, 1 + 4),
+    ("H50 half transform, scaled out, L2 flushed, dynamic tiles", 75000, 64, 64, 4, 10, 10, 1 + 4 + 8),
+    ("H50 full transform, scaled out", 32000, 64, 64, 4, 10, 10, 1),
+    ("H50 full transform, scaled out, dynamic tiles", 32000, 64, 64, 4, 10, 10, 1 + 8),
     ("H50 Lagrangian, chunk 16", 150, 50, 64, 4, 2000, 16, 2),
     ("H50 Lagrangian, chunk 32", 150, 50, 64, 4, 2000, 32, 2),
+    ("H50 Lagrangian, chunk 32, dynamic tiles", 150, 50, 64, 4, 2000, 32, 2 + 8),
     ("H50 Lagrangian, chunk 64", 150, 50, 64, 4, 2000, 64, 2),
     ("stream 600000 x 64 x 640, BN 64", 600000, 64, 64, 4, 40, 40, 0),
     ("stream 600000 x 64 x 640, BN 32", 600000, 64, 32, 4, 40, 40, 0),
