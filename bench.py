@@ -464,7 +464,7 @@ def main():
     if prec == nof.PREC_SPLIT_BF16:
         t = ctx.tuned_tiles()
         tiles = {"gemm1_bn": t[0], "gemm2_bn": t[1], "gemm3_bn": t[2], "gemm3_chunk_atoms": t[3],
-                 "picked_by": "autotuner (CUDA-event timing of candidate launch shapes at set-up)"}
+                 "picked_by": "autotuner (CUDA-event timing of candidate launch shapes at set-up; GEMM1 with L2 flushed)"}
     Q = torch.tensor(inputs.random_orthogonal(n, 0), dtype=torch.float64, device="cuda")
     C = ctx.lowdin(Q)
     gam = torch.tensor(inputs.random_gamma(s["ngamma"], 1), dtype=torch.float64, device="cuda")
@@ -665,7 +665,7 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
 # DRAM bytes (read + write) of one GEMM1 launch on the H50 workload from an ncu capture of the
 # current kernel (profiles/), or None when the kernel has changed since the counters were taken.
-TRAFFIC_GEMM1_BYTES = 96588032 + 4565248  # profiles/digit_gemm_h50_ncu.md
+TRAFFIC_GEMM1_BYTES = 96594176 + 4378112  # profiles/digit_gemm_h50_ncu.md (dynamic-tile kernel)
 
 
 def roofline(prec, s, ms_per_launch, name, traffic=None):
