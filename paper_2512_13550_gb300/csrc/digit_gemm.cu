@@ -188,9 +188,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
 // int64 sums, or double-float sums of the scaled values), hand the set back, and after the last
 // part of a tile write the staged rows as contiguous segments. With two sets the drain of one part
 // overlaps the MMAs of the next.
-// Tiles go to CTAs round-robin, or, with a tile counter, dynamically: the producer takes each next
-// tile by a fetch-and-add and hands its index to the MMA and epilogue warps through a small queue
-// in shared memory. A CTA that starts late (its SM still busy with another stream's blocks) then
+// Tiles go to CTAs round-robin, or, with a tile counter, dynamically: after its first tile
+// (blockIdx.x) the producer takes each next tile by a fetch-and-add and hands every index to the
+// MMA and epilogue warps through a small queue in shared memory. A CTA that starts late (its SM still busy with another stream's blocks) then
 // takes fewer tiles instead of holding up the whole launch.
 constexpr int kEpiWarps = 8;  // two per TMEM lane group, each owning half of the columns
 constexpr int kTileQ = 4;     // tile-index queue slots (dynamic tiles)
@@ -272,17 +272,18 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
 
     if (warp == 0) {
         if (lane == 0) {  // bulk-copy producer
-            // dynamic tiles: fetch-and-add on the launch's counter. Every CTA's run ends with one
-            // fetch past the last tile, so a launch makes ntiles + gridDim.x fetches; the final one
-            // puts the counter back to 0 for the next launch of the plan.
+            // dynamic tiles: every CTA starts with tile blockIdx.x (gridDim.x <= ntiles) and takes
+            // each further tile as gridDim.x + a fetch-and-add on the launch's counter. Every CTA's
+            // run ends with one fetch past the last tile, so a launch makes ntiles fetches; the
+            // final one (counter value ntiles - 1) puts the counter back to 0 for the next launch.
             const int last = ntiles + (int)gridDim.x - 1;
             auto fetch = [&]() {
-                const int t = atomicAdd(g.tctr, 1);
+                const int t = (int)gridDim.x + atomicAdd(g.tctr, 1);
                 if (t == last) atomicExch(g.tctr, 0);
                 return t;
             };
             int it = 0;
-            int tile = dyn ? fetch() : (int)blockIdx.x;
+            int tile = (int)blockIdx.x;
             for (int qi = 0; ok; ++qi) {
                 if (dyn) {  // hand the tile index to the MMA and epilogue warps
                     const int slot = qi % kTileQ;

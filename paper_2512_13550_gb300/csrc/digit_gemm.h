@@ -51,8 +51,9 @@ struct DigitGemmArgs {
     int nbuf;          // TMEM accumulator sets
     int tiles_m;       // 128-row blocks
     int kchunks;       // K chunks (split-K); tile order: N tile fastest, then row block, then chunk
-    // dynamic tiles: each CTA takes its next tile by a fetch-and-add on *tctr (zero before the
-    // first launch; every launch leaves it at zero); nullptr: tiles round-robin over the CTAs
+    // dynamic tiles: after tile blockIdx.x each CTA takes its next tile by a fetch-and-add on
+    // *tctr (zero before the first launch; every launch leaves it at zero); nullptr: tiles
+    // round-robin over the CTAs
     int* tctr;
 };
 
