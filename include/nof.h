@@ -126,6 +126,12 @@ int nof_get_B(nof_ctx* ctx, double* B);
  * NOF_EINVAL unless the context is built with NOF_PREC_SPLIT_BF16. */
 int nof_tuned_tiles(nof_ctx* ctx, int* out);
 
+/* Digits per element of the split path's operands (4 or 5: the option `digits`, or the automatic
+ * choice at nof_build_B) into *nd (host); no paper counterpart. A digit GEMM then makes
+ * nd (nd + 1) / 2 BF16 products per K atom and reads 2 nd bytes per operand element.
+ * NOF_EINVAL unless the context is built with NOF_PREC_SPLIT_BF16. */
+int nof_split_digits(nof_ctx* ctx, int* nd);
+
 /* C = S^{-1/2} Q (Loewdin orthonormalisation, S^{-1/2} by a Newton-Schulz iteration on the
  * device). Q: nbf x nbf orthogonal. Gives S-orthonormal orbitals for any orthogonal Q. */
 int nof_lowdin(nof_ctx* ctx, const double* Q, double* C);

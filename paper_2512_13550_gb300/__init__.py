@@ -61,6 +61,7 @@ SIGNATURES = {
     "nof_get_SH": (ctypes.c_int, [_P, _P, _P]),
     "nof_get_B": (ctypes.c_int, [_P, _P]),
     "nof_tuned_tiles": (ctypes.c_int, [_P, _P]),
+    "nof_split_digits": (ctypes.c_int, [_P, _P]),
     "nof_lowdin": (ctypes.c_int, [_P, _P, _P]),
     "nof_core_guess": (ctypes.c_int, [_P, _P, _P]),
     "nof_jk": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -281,6 +282,12 @@ class Context:
         B = self._empty(s["naux"], s["nbf"], s["nbf"])
         _check(load_library().nof_get_B(self._h, _dptr(B)))
         return B
+
+    def split_digits(self) -> int:
+        """Digits per operand element of the split path (4 or 5)."""
+        nd = ctypes.c_int(0)
+        _check(load_library().nof_split_digits(self._h, ctypes.byref(nd)))
+        return nd.value
 
     def tuned_tiles(self):
         """(N tile of GEMM1, of GEMM2, of GEMM3, GEMM3 split-K chunk in atoms) chosen by the autotuner."""

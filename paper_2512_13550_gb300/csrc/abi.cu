@@ -444,6 +444,16 @@ int nof_get_SH(nof_ctx* c, double* S, double* H) {
     return NOF_OK;
 }
 
+int nof_split_digits(nof_ctx* c, int* nd) {
+    NOF_TRY(check_ctx(c, true));
+    if (!nd || !c->fast) {
+        nof_set_error("nof_split_digits: null output or not a split-precision context");
+        return NOF_EINVAL;
+    }
+    *nd = fast_digits(c);
+    return NOF_OK;
+}
+
 int nof_tuned_tiles(nof_ctx* c, int* out) {
     NOF_TRY(check_ctx(c, true));
     if (!out || !c->fast) {

@@ -581,6 +581,8 @@ void fast_coefficient_buffers(nof_ctx* c, float2** Adf, float2** Bcdf) {
     *Bcdf = c->fast ? c->fast->Bcdf : nullptr;
 }
 
+int fast_digits(nof_ctx* c) { return c->fast->nd; }
+
 int fast_tiles(nof_ctx* c, int* out) {
     FastState* f = c->fast;
     out[0] = f->bn1;

@@ -169,5 +169,6 @@ int fast_grad(nof_ctx* c, const double* C, const double* gamma, bool want_grad);
 int fast_eval(nof_ctx* c, const double* C, const double* gamma, bool want_grad);
 int fast_get_B(nof_ctx* c, double* B);
 int fast_tiles(nof_ctx* c, int* out);
+int fast_digits(nof_ctx* c);
 // split path: double-float copies of A and B for k_coefficients (null outside the split path)
 void fast_coefficient_buffers(nof_ctx* c, float2** Adf, float2** Bcdf);

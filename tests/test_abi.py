@@ -58,6 +58,7 @@ def test_argument_checks_of_measurement_and_deployment_entry_points(lib):
     assert lib.nof_selftest_digit_gemm(128, 64, 24, 4, 10, 10, 1, ctypes.byref(ll)) == nof.NOF_EINVAL
     assert lib.nof_selftest_digit_gemm(0, 64, 64, 4, 10, 10, 1, ctypes.byref(ll)) == nof.NOF_EINVAL
     assert lib.nof_tuned_tiles(None, (ctypes.c_int * 4)()) == nof.NOF_EINVAL
+    assert lib.nof_split_digits(None, ctypes.byref(ctypes.c_int())) == nof.NOF_EINVAL
     # the allocation-free JK refuses sizes beyond its fixed scratch before touching the device
     p = ctypes.c_void_p(16)
     assert lib.nof_jk_static(2000, 600, 200, p, p, p, p, None) == nof.NOF_EINVAL

@@ -41,3 +41,20 @@ def test_two_replicas_take_the_slowest_rank_and_sum_work():
 def test_single_rank_needs_no_process_group():
     import bench
     assert bench.aggregate(200.0, 10, 1) == (50.0, 200.0)
+
+
+def test_roofline_counts_the_digits_of_the_operands():
+    """GEMM1's algorithmic work on the split path: 2 nd bytes per element of B plus the
+    double-float T, and nd (nd + 1) / 2 BF16 products. H50 (4 digits) is bound by HBM; H200
+    (5 digits) by the tensor cores, against the sustained BF16 peak."""
+    import bench
+    h50 = {"nbf": 150, "naux": 500, "nact": 50}
+    r = bench.roofline(2, h50, 0.0455, "GEMM1", nd=4)
+    assert r["bound"] == "hbm" and r["algorithmic_bytes"] == 8.0 * 500 * 150 ** 2 + 8.0 * 500 * 150 * 50
+    peaks, _ = bench._peaks()
+    assert abs(r["frac"] - r["algorithmic_bytes"] / 0.0455e-3 / 1e9 / peaks["hbm_gbs"]) < 1e-12
+    h200 = {"nbf": 600, "naux": 2000, "nact": 200}
+    r = bench.roofline(2, h200, 9.0, "GEMM1", nd=5)
+    assert r["bound"] == "tensor" and r["algorithmic_flops"] == 15 * 2.0 * 2000 * 600 ** 2 * 200
+    assert r["algorithmic_bytes"] == 10.0 * 2000 * 600 ** 2 + 8.0 * 2000 * 600 * 200
+    assert r["peak"] == peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
