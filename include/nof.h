@@ -69,11 +69,14 @@ typedef struct {
                          chooses 5 when naux * nact > 80000 (where the truncation error of 4
                          digits, accumulated over the naux * nact terms of the Lagrangian, nears
                          1e-6), else 4 */
-    int graphs;       /* 1 (default): when nof_energy_grad is called twice in a row with the same
-                         pointers, the second call records its kernels as a CUDA graph on the
-                         context's stream, and later calls with those pointers replay it (one
-                         launch instead of about 20). The graph reads the arrays, so their contents
-                         may change between calls. 0: every call launches its kernels one by one.
+    int graphs;       /* 1 (default): the second nof_energy_grad call with a set of pointers among
+                         the last four sets of direct calls records its kernels as a CUDA graph on
+                         the context's stream, and later calls with those pointers replay it (one
+                         launch instead of about 20). Up to four graphs are kept (the least
+                         recently used is replaced), so a caller may alternate between buffer
+                         sets, e.g. to overlap its copies with the evaluations. A graph reads the
+                         arrays, so their contents may change between calls. 0: every call
+                         launches its kernels one by one.
                          No graph is recorded on the legacy default stream (stream 0), while
                          nof_profile is on, or while the caller is capturing the stream. */
 } nof_options;

@@ -81,15 +81,18 @@ void dfree(T*& p) {
     p = nullptr;
 }
 
-// Forget the recorded evaluation graph (its kernels name workspaces that are about to change).
+// Forget the recorded evaluation graphs (their kernels name workspaces that are about to change).
 void drop_eval_graph(nof_ctx* c) {
-    if (c->geval) {
-        cudaStreamSynchronize(c->stream);  // no replay of it still pending
-        cudaGraphExecDestroy(c->geval);
+    bool any = false;
+    for (auto& g : c->geval) any = any || g.exec;
+    if (any) cudaStreamSynchronize(c->stream);  // no replay still pending
+    for (auto& g : c->geval) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = nof_ctx::EvalGraph{};
     }
-    c->geval = nullptr;
-    c->gkernels = 0;
-    for (int i = 0; i < 5; ++i) c->gkey[i] = c->glast[i] = nullptr;
+    for (auto& k : c->gseen)
+        for (auto& p : k) p = nullptr;
+    c->gseen_next = 0;
 }
 
 void free_system(nof_ctx* c) {
@@ -573,13 +576,34 @@ int nof_energy_grad(nof_ctx* c, const double* C, const double* gamma, double* E,
             if (k[i] != key[i]) return false;
         return true;
     };
-    if (!(c->geval && same_as(c->gkey))) {
-        if (!same_as(c->glast)) {  // new pointers: run directly and remember them (the graph stays)
-            for (int i = 0; i < 5; ++i) c->glast[i] = key[i];
+    nof_ctx::EvalGraph* hit = nullptr;
+    for (auto& g : c->geval)
+        if (g.exec && same_as(g.key)) hit = &g;
+    if (!hit) {
+        int seen = -1;
+        for (int s = 0; s < nof_ctx::kEvalGraphs; ++s)
+            if (same_as(c->gseen[s])) seen = s;
+        if (seen < 0) {  // new pointers: run directly and remember them (the graphs stay)
+            for (int i = 0; i < 5; ++i) c->gseen[c->gseen_next][i] = key[i];
+            c->gseen_next = (c->gseen_next + 1) % nof_ctx::kEvalGraphs;
             return energy_grad_body(c, C, gamma, E, g_orb, g_gamma);
         }
-        // second call in a row with these pointers: record the evaluation, then replay it below
-        drop_eval_graph(c);
+        // second call with these pointers: record the evaluation into the least recently used
+        // slot, then replay it below
+        for (int i = 0; i < 5; ++i) c->gseen[seen][i] = nullptr;
+        hit = nullptr;  // an empty slot, else the least recently used one
+        for (auto& g : c->geval)
+            if (!hit && !g.exec) hit = &g;
+        if (!hit) {
+            hit = &c->geval[0];
+            for (auto& g : c->geval)
+                if (g.used < hit->used) hit = &g;
+        }
+        if (hit->exec) {
+            cudaStreamSynchronize(c->stream);  // no replay of the replaced graph still pending
+            cudaGraphExecDestroy(hit->exec);
+            *hit = nof_ctx::EvalGraph{};
+        }
         const long long l0 = g_launches.load();
         NOF_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         int r = energy_grad_body(c, C, gamma, E, g_orb, g_gamma);
@@ -587,20 +611,21 @@ int nof_energy_grad(nof_ctx* c, const double* C, const double* gamma, double* E,
         cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
         const long long recorded = g_launches.load() - l0;
         g_launches.fetch_sub(recorded);  // counted again at each replay
-        if (r == NOF_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->geval, graph, 0);
+        if (r == NOF_OK && e == cudaSuccess) e = cudaGraphInstantiate(&hit->exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (r != NOF_OK || e != cudaSuccess) {
             // recording failed: nothing ran, so run directly and keep launching directly from now on
-            c->geval = nullptr;
+            hit->exec = nullptr;
             c->gfail = 1;
             cudaGetLastError();
             return energy_grad_body(c, C, gamma, E, g_orb, g_gamma);
         }
-        for (int i = 0; i < 5; ++i) c->gkey[i] = key[i];
-        c->gkernels = recorded;
+        for (int i = 0; i < 5; ++i) hit->key[i] = key[i];
+        hit->kernels = recorded;
     }
-    NOF_CUDA(cudaGraphLaunch(c->geval, c->stream));
-    g_launches.fetch_add(c->gkernels);
+    hit->used = ++c->gtick;
+    NOF_CUDA(cudaGraphLaunch(hit->exec, c->stream));
+    g_launches.fetch_add(hit->kernels);
     return NOF_OK;
 }
 

@@ -71,13 +71,21 @@ struct nof_ctx {
     // gradient's side inputs written, J/K and energy done
     cudaStream_t side;
     cudaEvent_t ev_s0, ev_sO, ev_sT, ev_sJ, ev_s1, ev_s2;
-    // recorded graph of nof_energy_grad (option graphs): the argument pointers it was recorded
-    // with, the kernel launches it holds, the pointers of the last direct call, and a flag set when
+    // recorded graphs of nof_energy_grad (option graphs), the least recently used replaced first:
+    // the argument pointers each was recorded with and the kernel launches it holds; the pointer
+    // sets of recent direct calls (a set is recorded on its second call); a flag set when
     // recording failed once (the context then launches directly)
-    cudaGraphExec_t geval;
-    const void* gkey[5];
-    const void* glast[5];
-    long long gkernels;
+    struct EvalGraph {
+        cudaGraphExec_t exec;
+        const void* key[5];
+        long long kernels;
+        unsigned long long used;
+    };
+    static constexpr int kEvalGraphs = 4;
+    EvalGraph geval[kEvalGraphs];
+    const void* gseen[kEvalGraphs][5];
+    int gseen_next;
+    unsigned long long gtick;
     int gfail;
     // static field (nof_set_field): dipole integrals [3][n][n], the field-free h and V_nn,
     // scratch of the dipole moment [3][a]; all allocated on first use

@@ -105,6 +105,42 @@ def test_graph_replay_matches_direct_launches(precision):
 
 
 
+@pytest.mark.parametrize("nsets", [2, 5])
+def test_alternating_buffer_sets_replay_their_own_graphs(nsets):
+    """Up to four recorded graphs are kept: a caller alternating between 2 buffer sets gets a
+    graph for each; with 5 sets in turn the least recently used graph is replaced at every
+    recording. Every call gives the bits of a context that launches directly, and no call writes
+    another set's outputs."""
+    import paper_2512_13550_gb300 as nof
+    sysm = systems.chain3s(10, seed=3)
+    cg, cd = _ctx(nof, sysm, 1, 1), _ctx(nof, sysm, 1, 0)
+    n, ng = cg.sizes["nbf"], cg.sizes["ngamma"]
+    sets = []
+    for k in range(nsets):
+        sets.append(dict(C=_t(sysm.orbitals(30 + k)), gam=_t(sysm.gamma(40 + k)),
+                         E=torch.full((1,), float("nan"), dtype=torch.float64, device="cuda"),
+                         g=torch.full((n, n), float("nan"), dtype=torch.float64, device="cuda"),
+                         gg=torch.full((ng,), float("nan"), dtype=torch.float64, device="cuda")))
+    ref = []
+    for st in sets:
+        E, g, gg = torch.empty(1, dtype=torch.float64, device="cuda"), torch.empty_like(st["g"]), \
+            torch.empty_like(st["gg"])
+        _eval(nof, cd, st["C"], st["gam"], E, g, gg)
+        ref.append((E.clone(), g.clone(), gg.clone()))
+    for it in range(4 * nsets):
+        k = it % nsets
+        st = sets[k]
+        launched = _eval(nof, cg, st["C"], st["gam"], st["E"], st["g"], st["gg"])
+        assert launched > 0
+        assert st["E"].item() == ref[k][0].item()
+        assert torch.equal(st["g"], ref[k][1]) and torch.equal(st["gg"], ref[k][2])
+        for j, other in enumerate(sets):  # every set holds its own results (or none yet)
+            if j != k and not torch.isnan(other["E"]).item():
+                assert other["E"].item() == ref[j][0].item()
+    cg.close()
+    cd.close()
+
+
 def test_device_counter_step_can_be_captured():
     """nof_step with t == NULL (device-side ADAM counter, fixed exp(y) scaling): direct calls and
     CUDA-graph replays of one captured step give the same bits, and both follow the host-counter
