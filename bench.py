@@ -6,8 +6,10 @@ even-tempered s functions per H (alpha = 0.2 * 4^k) and 10 aux s per H (alpha = 
 nbf = 150, naux = 500, 50 active orbitals, PNOF7 with 25 pairs and N_g = 1. One step is one
 energy+gradient evaluation (transforms, J, K, energy, Lagrangian, orbital and occupation
 gradients) at fixed (C, gamma), with C = S^{-1/2} Q for a seeded random orthogonal Q and
-gamma ~ U(0.1, 1.2). L2 is flushed (a 256 MiB write) before every timed step; the step itself
-is bracketed by CUDA events on the library's stream.
+gamma ~ U(0.1, 1.2). The K timed steps are one region bracketed by CUDA events on the library's
+stream. Every step's inputs exceed L2: when one context's B is smaller than twice L2 (H50: 90 MB
+of digits), two contexts of the workload with separate copies of B take the steps in turn, so
+each evaluation reads a B last touched two steps earlier.
 
 Under torchrun (N > 1) every rank evaluates its own independent geometry (seed 2 + rank):
 the path has no exchange step, so the ranks are replicas and `value` sums their work.
@@ -33,6 +35,7 @@ METRIC = "NOF energy+gradient evals/sec vs FP64 plain GPU path at |ΔE|≤1e-6 H
 WORKLOAD = ("H50 chain, spacing 1.8+U(-0.1,0.1) bohr, 3 s/H (0.2*4^k) + 10 aux s/H (0.1*3^k): "
             "nbf=150, naux=500, nact=50, PNOF7, 25 pairs, N_g=1")
 ACC_GATE = 1e-6
+L2_BYTES = 129 * 1000 * 1000  # GB300 L2
 
 
 def parse():
@@ -471,7 +474,6 @@ def main():
     E = torch.empty(1, dtype=torch.float64, device="cuda")
     g = torch.empty(n, n, dtype=torch.float64, device="cuda")
     gg = torch.empty(s["ngamma"], dtype=torch.float64, device="cuda")
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     if args.profile_evals:
         for _ in range(max(1, args.warmup)):
@@ -486,53 +488,85 @@ def main():
                           "E": float(E.item())}), flush=True)
         return 0
 
-    def timed_loop(c, steps, warmup, profile=False, graph=False):
-        """Time `steps` evaluations, L2 flushed before each; returns (ms, kernel launches, profile).
-        With graph=True one evaluation is captured in a CUDA graph and replayed (the library makes no
-        host synchronisation or allocation inside an evaluation, so the capture holds all of it)."""
-        for _ in range(warmup):
-            c.energy_grad(C, gam, E, g, gg)
+    def contexts(c, p):
+        """The contexts that take the timed steps in turn: `c` alone when its B (digits, or FP64)
+        is larger than twice L2, else `c` and a second context of the same workload with its own
+        copy of B, so that every evaluation reads a B last touched two steps earlier (inputs
+        larger than L2 instead of a flush between steps)."""
+        b_bytes = (2 * c.split_digits() if p == nof.PREC_SPLIT_BF16 else 8) * s["naux"] * n * n
+        return [c] if b_bytes > L2_BYTES * 2 else [c, make_ctx(p)]
+
+    def timed_loop(cs, steps, warmup, profile=False, graph=False, flush=None):
+        """Time `steps` evaluations as one region bracketed by CUDA events, the contexts `cs`
+        taking them in turn; returns (ms, kernel launches, profile). With graph=True one evaluation
+        per context is captured in a CUDA graph and replayed (the library makes no host
+        synchronisation or allocation inside an evaluation, so the capture holds all of it).
+        With a `flush` buffer (larger than L2) it is written before every step instead, and each
+        step is timed alone."""
+        for c in cs:
+            for _ in range(warmup):
+                c.energy_grad(C, gam, E, g, gg)
         torch.cuda.synchronize()
-        run = lambda: c.energy_grad(C, gam, E, g, gg)
+        runs = [(lambda c=c: c.energy_grad(C, gam, E, g, gg)) for c in cs]
         per_eval = None
         if graph:
-            cg = torch.cuda.CUDAGraph()
+            cgs = []
             l0 = nof.kernel_launches()
-            with torch.cuda.graph(cg, stream=stream):
-                c.energy_grad(C, gam, E, g, gg)
-            per_eval = nof.kernel_launches() - l0
+            for c in cs:
+                cg = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(cg, stream=stream):
+                    c.energy_grad(C, gam, E, g, gg)
+                cgs.append(cg)
+            per_eval = (nof.kernel_launches() - l0) // len(cs)
             torch.cuda.synchronize()
             for _ in range(warmup):
-                cg.replay()
+                for cg in cgs:
+                    cg.replay()
             torch.cuda.synchronize()
-            run = cg.replay
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            runs = [cg.replay for cg in cgs]
         l0 = nof.kernel_launches()
-        for i in range(steps):
-            flush.fill_(float(i))
-            evs[i][0].record(stream)
-            run()
-            evs[i][1].record(stream)
-        torch.cuda.synchronize()
-        launches = nof.kernel_launches() - l0 if per_eval is None else per_eval * steps
-        ms = sum(a.elapsed_time(b) for a, b in evs)
-        prof = None
-        if profile:  # the dominant kernel, timed with CUDA events inside the library on its stream
-            c.profile(True)
+        if flush is not None:
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(steps)]
             for i in range(steps):
                 flush.fill_(float(i))
-                c.energy_grad(C, gam, E, g, gg)
-            prof = c.profile_read()
-            c.profile(False)
+                evs[i][0].record(stream)
+                runs[i % len(cs)]()
+                evs[i][1].record(stream)
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in evs)
+        else:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(steps):
+                runs[i % len(cs)]()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        launches = nof.kernel_launches() - l0 if per_eval is None else per_eval * steps
+        prof = None
+        if profile:  # the dominant kernel of cs[0], timed with CUDA events inside the library
+            cs[0].profile(True)
+            for i in range(steps):
+                cs[i % len(cs)].energy_grad(C, gam, E, g, gg)
+            prof = cs[0].profile_read()
+            cs[0].profile(False)
         return ms, launches, prof
 
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    ctxs = contexts(ctx, prec)
+    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        ms, launches, prof = timed_loop(ctx, args.steps, args.warmup, profile=True, graph=not args.no_graph)
+        ms, launches, prof = timed_loop(ctxs, args.steps, args.warmup, profile=True, graph=not args.no_graph)
     torch.cuda.synchronize()
     value, t_max = aggregate(ms, args.steps, world, dist, device="cuda")
+    # the same steps on one context with a 256 MiB write before each (timed per step), reported
+    # beside the value for comparison
+    flushbuf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ms_fl, _, _ = timed_loop([ctx], args.steps, args.warmup, graph=not args.no_graph, flush=flushbuf)
+    del flushbuf
     if dist is not None:
         dist.barrier()
     E_fast = float(E.item())
@@ -544,7 +578,7 @@ def main():
         ms64, steps64 = ms, args.steps
     else:
         ctx64 = make_ctx(nof.PREC_FP64)
-        ms64, _, _ = timed_loop(ctx64, args.fp64_steps, 3, graph=not args.no_graph)
+        ms64, _, _ = timed_loop(contexts(ctx64, nof.PREC_FP64), args.fp64_steps, 3, graph=not args.no_graph)
         steps64 = args.fp64_steps
         E64 = float(E.item())
         dE = abs(E_fast - E64)
@@ -564,7 +598,7 @@ def main():
     bC, bgam = [torch.empty_like(C) for _ in range(2)], [torch.empty_like(gam) for _ in range(2)]
     bE, bg, bgg = [torch.empty_like(E) for _ in range(2)], [torch.empty_like(g) for _ in range(2)], \
         [torch.empty_like(gg) for _ in range(2)]
-    ctxs = [ctx, make_ctx(prec)]
+    ectx = ctxs * 2 if len(ctxs) == 1 else ctxs  # the context of each buffer set
     up, down = torch.cuda.Stream(), torch.cuda.Stream()
     ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("up", "done", "down")}
     e2e_steps = max(3, args.steps // 2)
@@ -581,7 +615,7 @@ def main():
             with torch.cuda.stream(stream):
                 stream.wait_event(ev["up"][k])
                 stream.wait_event(ev["down"][k])  # and its outputs once step i-2's readback is done
-                ctxs[k].energy_grad(bC[k], bgam[k], bE[k], bg[k], bgg[k])
+                ectx[k].energy_grad(bC[k], bgam[k], bE[k], bg[k], bgg[k])
                 ev["done"][k].record(stream)
             with torch.cuda.stream(down):
                 down.wait_event(ev["done"][k])
@@ -613,7 +647,9 @@ def main():
         "data": "synthetic",
         "config": {"workload": wl_name, "path": "split-bf16 tcgen05" if prec else "plain fp64",
                    "tiles": tiles,
-                   "l2": "flushed (256 MiB write) before every timed step",
+                   "l2": ("inputs larger than L2: two contexts with separate copies of B's digits take "
+                          "the steps in turn" if len(ctxs) == 2 else "inputs larger than L2 (B's digits)"),
+                   "l2_flushed_evals_per_s": args.steps / (ms_fl / 1e3),
                    "timing": "CUDA-graph replay of one evaluation per step" if not args.no_graph
                              else "one API call per step",
                    "parallelism": f"replicas x{world}"},
@@ -625,7 +661,8 @@ def main():
         "e2e": {"value": world * e2e_steps / e2e_s, "unit": "evals/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "pipeline": "two buffer sets in turn: upload of step i and readback of step i-1 overlap evaluation i",
-                "l2": "two contexts in turn, each with its own copy of B's digits (180 MB in all, more than L2)",
+                "l2": ("two contexts in turn, each with its own copy of B's digits (more than L2 in all)"
+                       if ectx[0] is not ectx[1] else "inputs larger than L2 (B's digits)"),
                 "readback_matches_device": e2e_ok},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
