@@ -162,8 +162,9 @@ def _cores():
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
 
-def cpu_baseline(budget_s: float):
-    """Time the FP64 oracle (as it stands) on a bounded sample of H50 evaluations."""
+def oracle_rate(budget_s: float):
+    """(evaluations, seconds) of the FP64 oracle (as it stands) on a bounded sample of H50
+    evaluations, set-up excluded."""
     system = oracle_setup()
     oracle_eval(system)
     t0 = time.perf_counter()
@@ -174,9 +175,28 @@ def cpu_baseline(budget_s: float):
         el = time.perf_counter() - t0
         if el >= budget_s or count >= 1000:
             break
-    return {"value": count / el, "unit": "evals/s", "cores": _cores(), "kind": "oracle",
+    return count, el
+
+
+def cpu_baseline(budget_s: float):
+    """The oracle with its BLAS on every core, and (in a child process whose BLAS and OpenMP
+    thread counts are set to 1) on one core."""
+    count, el = oracle_rate(budget_s)
+    line = {"value": count / el, "unit": "evals/s", "cores": _cores(), "kind": "oracle",
             "sample": f"{count} H50 energy+gradient evaluations of the numpy FP64 oracle in "
                       f"{el:.1f} s (set-up excluded; BLAS threads as configured)"}
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"print(json.dumps(bench.oracle_rate({budget_s / 2!r})))")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=10 * budget_s + 120)
+        c1, e1 = json.loads(out.stdout.strip().splitlines()[-1])
+        line["single_thread"] = {"value": c1 / e1, "unit": "evals/s", "cores": 1,
+                                 "sample": f"{c1} evaluations in {e1:.1f} s"}
+    except (subprocess.SubprocessError, ValueError, IndexError) as exc:
+        line["single_thread"] = {"value": None, "error": str(exc)[:200]}
+    return line
 
 
 def run_reference(args):
