@@ -194,6 +194,7 @@ def cpu_baseline(budget_s: float):
         c1, e1 = json.loads(out.stdout.strip().splitlines()[-1])
         line["single_thread"] = {"value": c1 / e1, "unit": "evals/s", "cores": 1,
                                  "sample": f"{c1} evaluations in {e1:.1f} s"}
+        line["parallel_speedup"] = line["value"] / (c1 / e1)  # BLAS on all cores over one core
     except (subprocess.SubprocessError, ValueError, IndexError) as exc:
         line["single_thread"] = {"value": None, "error": str(exc)[:200]}
     return line
