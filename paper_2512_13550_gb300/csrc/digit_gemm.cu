@@ -182,9 +182,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
 // fastest so that the CTAs working on the N tiles of one row block at the same time share its A
 // stages through L2. A chunk is cut into parts of at most g.apart atoms (one exact accumulation
 // each). Warp 0 lane 0 streams A and B stages with bulk copies through a ring of g.stages
-// shared-memory slots that carries over from one tile to the next; warp 1 lane 0 issues the 10
-// digit-product MMAs per K atom of a part into one of g.nbuf TMEM accumulator sets (4 levels x BN
-// columns); the epilogue warps drain each finished part into a shared-memory staging tile (exact
+// shared-memory slots that carries over from one tile to the next; warp 1 lane 0 issues the
+// digit-product MMAs (6 per K atom with 4 digits, 9 with 5: pairs of products share one MMA of
+// width 2 BN) of a part into one of g.nbuf TMEM accumulator sets (nd levels x BN columns); the
+// epilogue warps drain each finished part into a shared-memory staging tile (exact
 // int64 sums, or double-float sums of the scaled values), hand the set back, and after the last
 // part of a tile write the staged rows as contiguous segments. With two sets the drain of one part
 // overlaps the MMAs of the next.
@@ -324,7 +325,13 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
         }
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
-            const uint32_t idesc = idesc_bf16(BN);
+            // one MMA per digit product pair: A plane i against B planes j and j + 1 at once. The
+            // planes of a stage are consecutive BN-row blocks in shared memory and the levels
+            // consecutive BN-column blocks in TMEM, so the 2 BN-wide product lands in levels i + j
+            // and i + j + 1. An MMA costs the same for every N up to 96 and little more at 128,
+            // so pairs halve the MMA count: 6 instead of 10 per K atom with 4 digits, 9 instead
+            // of 15 with 5. Each level still receives the same exact integer products.
+            const uint32_t idesc = idesc_bf16(BN), idesc2 = idesc_bf16(2 * BN);
             // descriptors of the ring's slot 0; a slot, atom or plane offset is added in 16-byte
             // units straight to the 14-bit address field (shared addresses stay below 2^18)
             const uint64_t adesc0 = sdesc(smem_u32(sA)), bdesc0 = sdesc(smem_u32(sB));
@@ -367,10 +374,10 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
 #pragma unroll
                                 for (int i = 0; i < ND; ++i) {
 #pragma unroll
-                                    for (int j = 0; j < ND - i; ++j) {
+                                    for (int j = 0; j < ND - i; j += 2) {
                                         const uint32_t accf = (t > 0 || i > 0) ? 1u : acc0;
                                         mma_bf16(accl[i + j], adt + (uint64_t)(i * 256), bdt + (uint64_t)j * b_plane16,
-                                                 idesc, accf);
+                                                 j + 1 < ND - i ? idesc2 : idesc, accf);
                                     }
                                 }
                             }

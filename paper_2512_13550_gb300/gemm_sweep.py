@@ -44,7 +44,10 @@ def main():
     for name, M, N, bn, nd, katoms, chunk, mode in CASES:
         us = bench_digit_gemm(M, N, bn, nd, katoms, chunk, mode, reps=10)
         prods = nd * (nd + 1) // 2
-        mmas = ((M + 127) // 128) * ((N + bn - 1) // bn) * katoms * prods
+        # MMAs per K atom: A plane i meets B planes 0 .. nd - 1 - i two at a time (one MMA of
+        # width 2 BN per pair, a single one of width BN for an odd count)
+        per_atom = sum((nd - i + 1) // 2 for i in range(nd))
+        mmas = ((M + 127) // 128) * ((N + bn - 1) // bn) * katoms * per_atom
         tflops = 2.0 * M * N * katoms * 16 * prods / us / 1e6
         print(f"| {name} | {M} x {N} x {16 * katoms} | {nd} | {bn} | {us:.1f} | {mmas / 152 / us:.1f} | {tflops:.0f} |")
 
