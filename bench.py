@@ -722,7 +722,7 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
 # DRAM bytes (read + write) of one GEMM1 launch on the H50 workload from an ncu capture of the
 # current kernel (profiles/), or None when the kernel has changed since the counters were taken.
-TRAFFIC_GEMM1_BYTES = 96590080 + 3935232  # profiles/digit_gemm_h50_ncu.md (dynamic-tile kernel)
+TRAFFIC_GEMM1_BYTES = 96589824 + 4070656  # profiles/digit_gemm_h50_ncu.md (paired-MMA kernel)
 
 
 def roofline(prec, s, ms_per_launch, name, traffic=None, nd=4):
