@@ -227,7 +227,10 @@ class Context:
         o = Options()
         lib.nof_default_options(ctypes.byref(o))
         o.precision, o.ipnof, o.ncwo = precision, ipnof, ncwo
+        known = {name for name, _ in Options._fields_}
         for k, v in opts.items():
+            if k not in known:  # a misspelt option would otherwise be ignored silently
+                raise ValueError(f"unknown option {k!r}; the options are {sorted(known)}")
             setattr(o, k, v)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._h = ctypes.c_void_p()

@@ -81,3 +81,10 @@ def test_bad_options_rejected(lib):
     assert lib.nof_create(ctypes.byref(h), ctypes.byref(o), None) == nof.NOF_EINVAL
     o.graphs, o.isoftmax = 1, 2  # 0 = trigonometric, 1 = softmax mapping
     assert lib.nof_create(ctypes.byref(h), ctypes.byref(o), None) == nof.NOF_EINVAL
+
+
+def test_misspelt_context_option_is_an_error(lib):
+    """Context(**options) names the struct's fields; an unknown name raises before any device
+    work instead of being ignored."""
+    with pytest.raises(ValueError, match="unknown option 'grpahs'"):
+        nof.Context(precision=nof.PREC_SPLIT_BF16, grpahs=0)
