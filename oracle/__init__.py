@@ -21,6 +21,9 @@ Modules and the passages they follow (DoNOF 2.0, arXiv 2512.13550):
   step       ADAM orbital-rotation step C <- C exp(y) and the ON update.
   reference  brute-force validators for tiny systems: exact 4-index ERIs, RHF in AO form,
              two-electron full CI, two-orbital DOCI.
+  rdm        the reconstructed spin-orbital 2RDM of the cumulant expansion (Theory section,
+             the Delta/Pi structure) and Eq. (Energy) contracted with it: a second route to
+             the energy that pins the A/B bookkeeping of pnof.
 
 Parity status per function is recorded in each module header. Functions whose result the
 paper does not fix (the PNOF7 A/B coefficients and the ADAM hyper-parameters, which the paper

@@ -34,9 +34,12 @@ angles so that their derivatives never divide by a vanishing occupation; the one
 derivative from gamma > 0 is taken at the kink gamma = 0 (sign(0) := +1).
 
 Parity: pinned by the RHF limit (AO-form RHF energy), the two-electron DOCI/FCI cases, the
-sum rule and trace, and finite differences of E in y and in gamma. The A/B coefficients and
-the Fig. 1 ordering are readings of the paper (it defers them), so the PNOF7-specific
-inter-pair Phi term is pinned only through the finite-difference and invariance tests.
+sum rule and trace, finite differences of E in y and in gamma, and by the 2RDM route of rdm.py:
+the energy assembled here from A and B equals Eq. (Energy) contracted with the spin-orbital 2RDM
+of the Theory section's cumulant expansion, element by element, for PNOF5 and PNOF7 with N_g = 1
+and 2 (which pins every factor and sign of the A/B bookkeeping, the inter-pair Phi term's
+included). The values of Delta and Pi, and with them Phi_p = sqrt(n_p (1 - n_p)), are the
+functionals' readings (the paper defers them); the value of Phi is parity unpinned.
 """
 from __future__ import annotations
 
