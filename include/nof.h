@@ -310,14 +310,21 @@ int nof_bench_digit_gemm(int M, int N, int bn, int nd, int katoms, int chunk_ato
  * Some callers cannot call cudaMalloc: an application whose device memory is owned by another
  * allocator (a framework's caching pool that has reserved the GPU, or a fixed memory budget),
  * or code that must not stall or fail on an allocation mid-run. This entry point keeps its
- * scratch in a fixed 48 MiB device array inside the library (held by every GPU that loads the
- * library until exit) and only launches kernels on `stream` (a cudaStream_t; NULL = default).
+ * scratch in a fixed 48 MiB device array inside the library and only launches kernels on
+ * `stream` (a cudaStream_t; NULL = default).
  *   B: device FP64 [naux][nbf][nbf] RI tensor (e.g. from nof_get_B); C: device FP64
  *   [nbf][nbf] orbitals (first nact columns used); J, K: device FP64 [nact][nact] outputs.
- * Limit: naux*nbf*nact + naux*nact*(nact + 1) <= 6291456 doubles, else NOF_EINVAL.
- * The first call on each device (with that device current) looks up the array's device
- * address; make it before any stream capture. Calls share the array: calls that overlap on
- * the GPU race. Asynchronous like every other call. */
+ * Limits: naux*nbf*nact + naux*nact*(nact + 1) <= 6291456 doubles, naux <= 65535 and
+ * naux*nbf <= 65535*64; beyond them NOF_EINVAL before anything is queued.
+ * When the 48 MiB are reserved: CUDA loads the library's modules lazily by default, so the
+ * array is reserved on a device by the first call made with that device current (with eager
+ * module loading, when the library is loaded); it stays reserved until the process exits.
+ * A caller that later hands the GPU to its own pool or budget should make one call first.
+ * That first call also looks up the array's device address; make it before any stream
+ * capture. The address is cached per device index: do not call this again on a device after
+ * cudaDeviceReset (or another teardown of its primary context) in the same process.
+ * Calls share the array: calls that overlap on the GPU race. Asynchronous like every other
+ * call. */
 int nof_jk_static(int naux, int nbf, int nact, const double* B, const double* C, double* J,
                   double* K, void* stream);
 

@@ -4,15 +4,23 @@
 // allocator (a framework's caching pool that has reserved the GPU, or a memory budget enforced
 // by the host program), or code that must not stall or fail on an allocation in the middle of
 // its run. For them this entry point keeps its scratch (the half-transformed tensor T, the fully
-// transformed b and the diagonal d) in one file-scope device array of fixed size, so a call only
-// launches kernels on the caller's stream.
+// transformed b, the diagonal d and the split-K partials of J) in one file-scope device array of
+// fixed size, so a call only launches kernels on the caller's stream.
 //
-// The scratch array is held by every GPU that loads this library until the process exits. Its
-// device address is looked up once per device, on the first call made with that device current
-// (make that first call before any stream capture: the look-up is a runtime call that a capture
-// does not allow). All calls share the array and each call overwrites every element it reads
-// before reading it, so no zeroing is needed; calls that overlap on the GPU (two streams, two
-// threads, or two devices' worth of work enqueued on one device concurrently) race on it.
+// When the array is reserved: this translation unit is its own CUDA module, and CUDA loads
+// modules lazily by default (CUDA_MODULE_LOADING=LAZY), so the 48 MiB are reserved on a device
+// when the module first loads there, which is inside the first nof_jk_static call made with that
+// device current (the address look-up below loads it). With eager loading they are reserved when
+// the library is loaded. Either way they stay reserved until the process exits. A caller that
+// hands the GPU to a pool or a budget afterwards should make one call first, before doing so.
+// The device address is looked up on that first call too; make it before any stream capture
+// (the look-up is a runtime call that a capture does not allow). The address is cached per
+// device index and is not refreshed: do not call this entry point again on a device after
+// cudaDeviceReset (or any other teardown of its primary context) in the same process.
+//
+// All calls share the array and each call overwrites every element it reads before reading it,
+// so no zeroing is needed; calls that overlap on the GPU (two streams, two threads, or two
+// devices' worth of work enqueued on one device concurrently) race on it.
 #include <mutex>
 
 #include "internal.h"
@@ -84,6 +92,14 @@ extern "C" int nof_jk_static(int naux, int nbf, int nact, const double* B, const
                       " doubles (48 MiB)");
         return NOF_EINVAL;
     }
+    // launch-shape limits of the FP64 GEMMs below (64-row tiles of the X n rows of the half
+    // transform and one batch entry per aux function of the full transform in grid.y / grid.z),
+    // checked before anything is queued so that a refused call leaves no partial work behind
+    if (X > 65535 || (X * n + 63) / 64 > 65535) {
+        nof_set_error("nof_jk_static: naux = " + std::to_string(X) + " and naux*nbf = " + std::to_string(X * n) +
+                      " must stay within 65535 and 65535*64 (grid limits of the transforms)");
+        return NOF_EINVAL;
+    }
     double* scratch = nullptr;
     NOF_TRY(static_scratch(&scratch));
     double* T = scratch;           // [X][n][a]
@@ -108,12 +124,15 @@ extern "C" int nof_jk_static(int naux, int nbf, int nact, const double* B, const
     }
     k_static_diag<<<(unsigned)((X * a + 255) / 256), 256, 0, st>>>(b, (int)X, (int)a, d);
     NOF_LAUNCH_CHECK();
-    {   // J = d^T d
+    {   // J = d^T d; the free tail of the array holds the split-K partials that gemm64 takes for a
+        // small a x a output (summed in a fixed order, so the result does not depend on scheduling)
         Gemm64 g;
         g.M = (int)a; g.N = (int)a; g.K = (int)X;
         g.A = d; g.sAm = 1; g.sAk0 = a;
         g.B = d; g.sBn = 1; g.sBk0 = a;
         g.C = J; g.sCm = a; g.sCn = 1;
+        g.work = d + X * a;
+        g.work_cap = (size_t)(kStaticScratchDoubles - need);
         NOF_TRY(gemm64(g, st));
     }
     k_static_ksum<<<(unsigned)((a * a + 255) / 256), 256, 0, st>>>(b, (int)X, (int)a, K);

@@ -64,6 +64,10 @@ def test_argument_checks_of_measurement_and_deployment_entry_points(lib):
     assert lib.nof_jk_static(2000, 600, 200, p, p, p, p, None) == nof.NOF_EINVAL
     assert b"exceeds" in lib.nof_last_error()
     assert lib.nof_jk_static(10, 4, 5, p, p, p, p, None) == nof.NOF_EINVAL  # nact > nbf
+    # within the scratch but beyond the transforms' grid limits: refused before anything is queued
+    assert lib.nof_jk_static(70000, 1, 1, p, p, p, p, None) == nof.NOF_EINVAL
+    assert b"grid limits" in lib.nof_last_error()
+    assert lib.nof_jk_static(60000, 80, 1, p, p, p, p, None) == nof.NOF_EINVAL
 
 
 def test_bad_options_rejected(lib):

@@ -33,18 +33,29 @@ def test_jk_static_matches_nof_jk_on_two_calls(make):
     X, n, a = s["naux"], s["nbf"], s["nact"]
     B = ctx.get_B()
     stream = torch.cuda.current_stream()
-    for seed in (0, 7):  # two calls in a row, different orbitals each time
-        C = _t(sysm.orbitals(seed))
-        J0, K0 = ctx.jk(C)
-        J = torch.full((a, a), float("nan"), dtype=torch.float64, device="cuda")
-        K = torch.full((a, a), float("nan"), dtype=torch.float64, device="cuda")
+    # every tensor of both calls exists before the first call, so that free device memory can only
+    # change inside the library
+    Cs = [_t(sysm.orbitals(seed)) for seed in (0, 7)]  # two calls in a row, different orbitals
+    refs = [ctx.jk(C) for C in Cs]
+    outs = [(torch.full((a, a), float("nan"), dtype=torch.float64, device="cuda"),
+             torch.full((a, a), float("nan"), dtype=torch.float64, device="cuda")) for _ in Cs]
+    torch.cuda.synchronize()
+    free = [torch.cuda.mem_get_info()[0]]
+    for C, (J0, K0), (J, K) in zip(Cs, refs, outs):
         rc = lib.nof_jk_static(X, n, a, ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()),
                                ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(K.data_ptr()),
                                ctypes.c_void_p(stream.cuda_stream))
         assert rc == nof.NOF_OK, lib.nof_last_error()
         torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
         assert torch.max(torch.abs(J - J0)).item() < TOL
         assert torch.max(torch.abs(K - K0)).item() < TOL
+    # the call after the first allocates nothing; the first may reserve the fixed array (the
+    # library's module loads lazily) and never more than the array plus its module's code
+    assert free[2] == free[1]
+    first = free[0] - free[1]
+    print(f"free device memory taken by the first call: {first / 2**20:.1f} MiB")
+    assert 0 <= first <= 64 * 2**20
 
 
 def test_jk_static_rejects_sizes_beyond_its_scratch():
