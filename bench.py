@@ -1,20 +1,24 @@
 #!/usr/bin/env python3
 """Benchmark of the density-fitted PNOF7 energy+gradient evaluation on one GB300.
 
-Workload: H50 linear chain (spacing 1.8 bohr + U(-0.1, 0.1) seeded jitter per bond), 3
-even-tempered s functions per H (alpha = 0.2 * 4^k) and 10 aux s per H (alpha = 0.1 * 3^k):
-nbf = 150, naux = 500, 50 active orbitals, PNOF7 with 25 pairs and N_g = 1. One step is one
-energy+gradient evaluation (transforms, J, K, energy, Lagrangian, orbital and occupation
-gradients) at fixed (C, gamma), with C = S^{-1/2} Q for a seeded random orthogonal Q and
-gamma ~ U(0.1, 1.2). The K timed steps are one region bracketed by CUDA events on the library's
-stream. Every step's inputs exceed L2: when one context's B is smaller than twice L2 (H50: 90 MB
-of digits), two contexts of the workload with separate copies of B take the steps in turn, so
-each evaluation reads a B last touched two steps earlier.
+Metric: energy+gradient evaluations per second (one evaluation = the orbital transformation of
+the RI tensor, J, K, the PNOF energy, the Lagrangian, the orbital and the occupation gradients at
+fixed (C, gamma)), against the plain FP64 GPU path on the same inputs, at |dE| <= 1e-6 Ha.
 
-Under torchrun (N > 1) every rank evaluates its own independent geometry (seed 2 + rank):
-the path has no exchange step, so the ranks are replicas and `value` sums their work.
+Default line: the largest single-GPU system, the H1000 chain (spacing 1.8 bohr, one contracted s
+function (STO-3G-like, zeta 1.24) and 3 aux s (alpha = 0.1 * 3^k) per H: nbf = 1000, naux = 3000,
+nact = 1000, PNOF7, 500 pairs, N_g = 1), on the split-precision tensor-core path (5 BF16 digits
+per operand element). C = S^{-1/2} Q for a seeded random orthogonal Q, gamma ~ U(0.1, 1.2). The K
+timed steps are one region bracketed by CUDA events on the library's stream; every step reads
+the 30 GB of B's digit planes from HBM (inputs larger than L2). The same line carries the other
+workloads as extra keys under `configs`: the H200 lattice, the H50 chain and the 256-frame batch.
 
-`--impl reference` times the CPU FP64 oracle (test infrastructure) on the same workload.
+Under torchrun (N > 1) every rank evaluates its own independent instance (orbitals seeded by the
+rank): the path has no exchange step, so the ranks are replicas and `value` sums their work.
+
+`--impl reference` times the CPU FP64 oracle (test infrastructure) on a bounded sample of the same
+workload: each step evaluates the oracle over a slice of the aux functions, scaled to whole
+evaluations.
 """
 from __future__ import annotations
 
@@ -32,51 +36,59 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "NOF energy+gradient evals/sec vs FP64 plain GPU path at |ΔE|≤1e-6 Ha"
-WORKLOAD = ("H50 chain, spacing 1.8+U(-0.1,0.1) bohr, 3 s/H (0.2*4^k) + 10 aux s/H (0.1*3^k): "
-            "nbf=150, naux=500, nact=50, PNOF7, 25 pairs, N_g=1")
 ACC_GATE = 1e-6
 L2_BYTES = 129 * 1000 * 1000  # GB300 L2
+
+WORKLOADS = {
+    "h1000": "H1000 chain, spacing 1.8 bohr, 1 contracted s/H (STO-3G-like, zeta 1.24) + 3 aux s/H (0.1*3^k): "
+             "nbf=1000, naux=3000, nact=1000, PNOF7, 500 pairs, N_g=1",
+    "h200": "H200 10x20 square lattice, spacing 2.0 bohr, 3 s/H (0.2*4^k) + 10 aux s/H (0.1*3^k): "
+            "nbf=600, naux=2000, nact=200, PNOF7, 100 pairs, N_g=1",
+    "h50": "H50 chain, spacing 1.8+U(-0.1,0.1) bohr, 3 s/H (0.2*4^k) + 10 aux s/H (0.1*3^k): "
+           "nbf=150, naux=500, nact=50, PNOF7, 25 pairs, N_g=1",
+}
+HEADLINE = "h1000"
+WORKLOAD = WORKLOADS["h50"]  # the nuclear-gradient workload's system
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--precision", choices=["auto", "split", "fp64"], default="auto")
-    ap.add_argument("--fp64-steps", type=int, default=10)
-    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
+    ap.add_argument("--precision", choices=["split", "fp64"], default="split")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work (H50 sample)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["h50", "h200", "batch", "nlop", "gradient", "dynamics"],
-                    default="h50",
-                    help="h50: the single-geometry benchmark; h200: the 10 x 20 lattice (nbf 600, "
-                         "naux 2000, nact 200); batch: many uneven H-chain frames evaluated "
-                         "concurrently as one CUDA-graph launch; nlop: the finite-field polarizability "
-                         "and hyperpolarizabilities of H2 (21 field instances stepped together); gradient: "
-                         "the nuclear gradient of the H50 chain on the FP64 path; dynamics: velocity-Verlet "
-                         "steps of H2 on converged states")
+    ap.add_argument("--no-extras", action="store_true", help="the headline workload only")
+    ap.add_argument("--workload", choices=["default", "h1000", "h200", "h50", "batch", "nlop", "gradient",
+                                           "dynamics"], default="default",
+                    help="default: H1000 headline line with H200, H50 and the batch as extra keys; h1000/h200/"
+                         "h50: that system alone as the line; batch: many uneven H-chain frames evaluated "
+                         "concurrently as one CUDA-graph launch; nlop: the finite-field polarizability and "
+                         "hyperpolarizabilities of H2 (21 field instances stepped together); gradient: the "
+                         "nuclear gradient of the H50 chain on the FP64 path; dynamics: velocity-Verlet steps "
+                         "of H2 on converged states")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-max", type=int, default=64, help="largest chain length in the batch")
     ap.add_argument("--no-graph", action="store_true",
                     help="time plain API calls instead of CUDA-graph replays of one evaluation")
     ap.add_argument("--profile-evals", type=int, default=0,
-                    help="profiling mode: build, warm up, run this many evaluations inside the NVTX "
-                         "range 'evals' (for ncu --nvtx --nvtx-include evals/) and exit")
+                    help="profiling mode: build the --workload system (default: h1000), warm up, run this many "
+                         "evaluations inside the NVTX range 'evals' (for ncu --nvtx --nvtx-include evals/) and exit")
     return ap.parse_args()
 
 
-WORKLOAD_H200 = ("H200 10x20 square lattice, spacing 2.0 bohr, 3 s/H (0.2*4^k) + 10 aux s/H (0.1*3^k): "
-                 "nbf=600, naux=2000, nact=200, PNOF7, 100 pairs, N_g=1")
-
-
 def workload(seed=2, name="h50"):
+    """Geometry and basis pair of a named system (seed: the H50 chain's jitter)."""
     from paper_2512_13550_gb300 import inputs
+    if name == "h1000":
+        orb, aux = inputs.basis_h1000()
+        return inputs.chain(1000, 1.8), orb, aux
     orb, aux = inputs.basis_3s_10aux()
     if name == "h200":
         return inputs.lattice(10, 20, 2.0), orb, aux
-    xyz = inputs.jittered_chain(50, seed)
-    return xyz, orb, aux
+    return inputs.jittered_chain(50, seed), orb, aux
 
 
 # ---------------------------------------------------------------------------------------
@@ -137,102 +149,420 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 rate of the plain path: 2 FP64 FMA per clock per SM (the rate an FMA-throughput probe
+# measured on GB300: 1.19 TFLOP/s), x 152 SMs x 2.07 GHz x 2 FLOP = 1.26 TFLOP/s.
+FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
+
+# The three contractions of an evaluation (nof_profile selectors) with their algorithmic work
+# per launch in the units of the system (X aux functions, n basis functions, a active orbitals):
+# flops of the contraction and its minimum bytes (the operand streamed from HBM once at 4 bytes
+# per element, the FP32 storage the work estimate assumes, and the output written once at 4
+# bytes). The split path reads more than that (2 nd bytes per digit element, double-float
+# outputs): those extra bytes are the price of its accuracy and count against it.
+CONTRACTIONS = {
+    1: ("half transform T = B C", lambda X, n, a: (2.0 * X * n * n * a, 4.0 * X * n * n + 4.0 * X * n * a)),
+    2: ("full transform b = C^T T", lambda X, n, a: (2.0 * X * n * a * a, 4.0 * X * n * a + 4.0 * X * a * a)),
+    3: ("Lagrangian contraction sum_P T W", lambda X, n, a: (2.0 * X * n * a * a, 4.0 * X * n * a + 4.0 * X * a * a)),
+}
+
+
+def eval_work(X, n, a):
+    """Algorithmic work of one evaluation: flops of the three contractions (plus the J/K and D
+    terms) and the minimum bytes (B once at 4 bytes per element, T and b/W' written and read once
+    at 4 bytes)."""
+    flops = 2.0 * X * n * n * a + 4.0 * X * n * a * a + 4.0 * X * a * a + 2.0 * X * a * a + 4.0 * n * n * a
+    nbytes = 4.0 * X * n * n + 2 * 4.0 * X * n * a + 2 * 4.0 * X * a * a
+    return flops, nbytes
+
+
+def roofline(prec, sizes, which, ms_per_launch, name, nd=5, traffic=None):
+    """Roofline of one contraction: achieved = its algorithmic flops (or bytes) per launch over
+    the CUDA-event duration of a launch. The split path's arithmetic type is an exact BF16
+    digit-plane product: nd (nd + 1) / 2 BF16 products per multiply-add, so its own peak is the
+    measured BF16 peak divided by that count; the plain path's is the FP64 rate. The bound is the
+    larger of flops / peak and bytes / HBM peak."""
+    X, n, a = sizes["naux"], sizes["nbf"], sizes["nact"]
+    peaks, src = _peaks()
+    label, work = CONTRACTIONS[which]
+    flops, nbytes = work(X, n, a)
+    sec = ms_per_launch / 1e3
+    base = {"kernel": name, "contraction": label, "algorithmic_flops": flops, "algorithmic_bytes": nbytes,
+            "ms_per_launch": ms_per_launch, "traffic": traffic}
+    if prec == 0:
+        peak_t = FP64_PEAK_TFLOPS
+        dtype_note = "FP64 SIMT: 2 FMA/clk/SM x 152 SMs x 2.07 GHz (probe-measured rate)"
+        prods = 1
+    else:
+        prods = nd * (nd + 1) // 2
+        bf16 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        peak_t = bf16 / prods
+        dtype_note = (f"{src} BF16 dense peak, sustained ({bf16:.1f} TFLOP/s; the kernel runs inside "
+                      f"back-to-back evaluations) / {prods} BF16 digit products per multiply-add ({nd} digits)")
+        base["digits"] = nd
+        base["bf16_products_per_mac"] = prods
+        # what the digit scheme actually moves: 2 nd bytes per element of the streamed operand
+        base["digit_operand_bytes"] = nbytes * nd / 2.0
+    t_tc = flops / (peak_t * 1e12)
+    t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
+    if t_tc >= t_hbm:
+        achieved = flops / sec / 1e12
+        base.update({"bound": "tensor" if prec else "alu", "achieved": achieved, "peak": peak_t,
+                     "unit": "TFLOP/s", "frac": achieved / peak_t, "peak_source": dtype_note})
+        if prec:
+            base["frac_of_bf16_peak_algorithmic"] = achieved / (peak_t * prods)  # no credit for the products
+    else:
+        achieved = nbytes / sec / 1e9
+        base.update({"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"],
+                     "peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"})
+    return base
+
+
+def eval_roofline(prec, sizes, ms_per_eval, nd=5):
+    """Whole-evaluation fraction: t_roofline / t_measured with t_roofline the larger of the
+    algorithmic flops over the arithmetic peak (BF16 / digit products, or FP64) and the algorithmic
+    bytes over the HBM peak."""
+    X, n, a = sizes["naux"], sizes["nbf"], sizes["nact"]
+    peaks, src = _peaks()
+    flops, nbytes = eval_work(X, n, a)
+    if prec == 0:
+        peak_t = FP64_PEAK_TFLOPS
+    else:
+        peak_t = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) / (nd * (nd + 1) // 2)
+    t_tc = flops / (peak_t * 1e12)
+    t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
+    t_roof = max(t_tc, t_hbm)
+    return {"bound": ("tensor" if prec else "alu") if t_tc >= t_hbm else "hbm", "algorithmic_flops": flops,
+            "algorithmic_bytes": nbytes, "t_roofline_ms": t_roof * 1e3, "ms_per_eval": ms_per_eval,
+            "frac": t_roof * 1e3 / ms_per_eval, "arith_peak_tflops": peak_t, "hbm_peak_gbs": peaks["hbm_gbs"],
+            "peak_source": src}
+
+
 # ---------------------------------------------------------------------------------------
-def oracle_setup(seed=2):
-    """The oracle's one-time set-up for the H50 workload (integrals, RI fit, orbitals)."""
-    from oracle import integrals, pnof, reference, ri
-    from paper_2512_13550_gb300 import inputs
-    xyz, orb, aux = workload(seed)
-    S, T, V = integrals.one_electron(orb, xyz)
-    B = ri.fitted_B(orb, aux, xyz)
-    vnn = integrals.nuclear_repulsion(xyz)
-    n = S.shape[0]
-    pm = pnof.PairMap(50, 1, n)
-    C = reference.orthonormal_orbitals(S, inputs.random_orthogonal(n, 0))
-    gam = inputs.random_gamma(pm.ngamma, 1)
-    return (B, T + V, C, gam, pm, vnn)
-
-
-def oracle_eval(system):
-    from oracle import pnof
-    return pnof.energy_and_gradients(*system)
-
-
+# the CPU FP64 oracle, timed on a bounded sample (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------------------
 def _cores():
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
 
-def oracle_rate(budget_s: float):
-    """(evaluations, seconds) of the FP64 oracle (as it stands) on a bounded sample of H50
-    evaluations, set-up excluded."""
-    system = oracle_setup()
-    oracle_eval(system)
+class OracleSample:
+    """The oracle's energy+gradient evaluation of a named system restricted to its first `xs` aux
+    functions. Every term the evaluation spends its time on (the transforms, J, K, the Lagrangian
+    contraction) is a sum over the aux index, so a slice of xs of the X aux functions is xs / X of
+    one evaluation. The slice's three-centre integrals stand in for the fitted tensor's rows (the
+    cost does not depend on the values), which keeps the sample's set-up to seconds."""
+
+    def __init__(self, name: str, xs: int):
+        from oracle import integrals, pnof, reference
+        from paper_2512_13550_gb300 import inputs
+        xyz, orb, aux = workload(2, name)
+        if name == "h1000":  # the overlap stands in for h (1000 nuclei make V slow in numpy; the cost
+            S = integrals.overlap(orb, xyz)  # of an evaluation does not depend on h's values)
+            T, V = S, np.zeros_like(S)
+        else:
+            S, T, V = integrals.one_electron(orb, xyz)
+        self.X = integrals.naux(aux, xyz)
+        self.xs = min(xs, self.X)
+        self.B = integrals.three_center(orb, aux, xyz, slice(0, self.xs))
+        n = S.shape[0]
+        self.pm = pnof.PairMap(xyz.shape[0], 1, n)
+        self.C = reference.orthonormal_orbitals(S, inputs.random_orthogonal(n, 0))
+        self.gam = inputs.random_gamma(self.pm.ngamma, 1)
+        self.H = T + V
+        self.vnn = integrals.nuclear_repulsion(xyz)
+
+    def run(self):
+        from oracle import pnof
+        return pnof.energy_and_gradients(self.B, self.H, self.C, self.gam, self.pm, self.vnn)
+
+    @property
+    def fraction(self):
+        return self.xs / self.X
+
+
+def oracle_rate(name: str, xs: int, reps: int = 1):
+    """(evaluations, seconds): `reps` sample evaluations of xs aux functions, as evaluations."""
+    smp = OracleSample(name, xs)
     t0 = time.perf_counter()
-    count = 0
-    while True:
-        oracle_eval(system)
-        count += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s or count >= 1000:
-            break
-    return count, el
+    for _ in range(reps):
+        smp.run()
+    el = time.perf_counter() - t0
+    return reps * smp.fraction, el
 
 
-def cpu_baseline(budget_s: float):
-    """The oracle with its BLAS on every core, and (in a child process whose BLAS and OpenMP
-    thread counts are set to 1) on one core."""
-    count, el = oracle_rate(budget_s)
-    line = {"value": count / el, "unit": "evals/s", "cores": _cores(), "kind": "oracle",
-            "sample": f"{count} H50 energy+gradient evaluations of the numpy FP64 oracle in "
-                      f"{el:.1f} s (set-up excluded; BLAS threads as configured)"}
+def cpu_baseline(name: str, xs: int):
+    """The oracle with its BLAS on every core and, in a child process whose BLAS and OpenMP
+    thread counts are set to 1, on one core."""
+    evals, el = oracle_rate(name, xs)
+    line = {"value": evals / el, "unit": "evals/s", "cores": _cores(), "kind": "oracle",
+            "sample": f"the numpy FP64 oracle's energy+gradient evaluation of {WORKLOADS[name].split(':')[0]} "
+                      f"over {xs} of its aux functions ({evals:.2e} evaluations) in {el:.1f} s, scaled by the aux "
+                      f"count (every term it spends time on is a sum over the aux index); BLAS threads as configured"}
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    xs1 = max(1, xs // 2)
     code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
-            f"print(json.dumps(bench.oracle_rate({budget_s / 2!r})))")
+            f"print(json.dumps(bench.oracle_rate({name!r}, {xs1})))")
     try:
-        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                             timeout=10 * budget_s + 120)
-        c1, e1 = json.loads(out.stdout.strip().splitlines()[-1])
-        line["single_thread"] = {"value": c1 / e1, "unit": "evals/s", "cores": 1,
-                                 "sample": f"{c1} evaluations in {e1:.1f} s"}
-        line["parallel_speedup"] = line["value"] / (c1 / e1)  # BLAS on all cores over one core
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        e1, t1 = json.loads(out.stdout.strip().splitlines()[-1])
+        line["single_thread"] = {"value": e1 / t1, "unit": "evals/s", "cores": 1,
+                                 "sample": f"{xs1} aux functions ({e1:.2e} evaluations) in {t1:.1f} s"}
+        line["parallel_speedup"] = line["value"] / (e1 / t1)
     except (subprocess.SubprocessError, ValueError, IndexError) as exc:
         line["single_thread"] = {"value": None, "error": str(exc)[:200]}
     return line
 
 
 def run_reference(args):
+    """The oracle on the headline workload (or the --workload system): every step one sample of
+    one aux function's share of an evaluation (about 4 s), rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    system = oracle_setup()
+    name = HEADLINE if args.workload == "default" else args.workload
+    if name not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle sample for workload {name}"}))
+        return 0
+    xs = 1 if name == "h1000" else (4 if name == "h200" else 500)
+    smp = OracleSample(name, xs)
     for _ in range(args.warmup):
-        oracle_eval(system)
+        smp.run()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle_eval(system)
+        smp.run()
     el = time.perf_counter() - t0
-    v = args.steps / el
+    v = args.steps * smp.fraction / el
+    sample = (f"{args.steps} timed steps, each the numpy FP64 oracle's energy+gradient evaluation over {smp.xs} of "
+              f"the {smp.X} aux functions ({smp.fraction:.2e} of an evaluation; every term it spends time on is a "
+              f"sum over the aux index), set-up excluded")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
-            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": _cores(), "kind": "oracle",
-                             "sample": f"{args.steps} timed H50 energy+gradient evaluations of the "
-                                       f"numpy FP64 oracle (set-up excluded)"},
+            "config": {"workload": WORKLOADS[name]},
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": _cores(), "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 # ---------------------------------------------------------------------------------------
-def run_batch(args):
-    """Throughput of many independent geometries (H-chain frames of uneven length, Gaussian
-    displacements sigma = 0.05 bohr, 3 s + 10 aux s per H) evaluated concurrently: every context on
-    its own stream, the whole batch captured as one CUDA graph and replayed."""
+# the native path
+# ---------------------------------------------------------------------------------------
+def _sizes_label(s):
+    return {"nbf": s["nbf"], "naux": s["naux"], "nact": s["nact"]}
+
+
+def run_system(name, args, stream, prec, rank=0, world=1, dist=None, steps=None, warmup=None, e2e=True,
+               fp64=True, fp64_steps=1, clocks=False, local=0):
+    """Time the energy+gradient evaluation of one named system: the timed region (K steps), the
+    per-contraction CUDA-event profile, the end-to-end loop from host buffers, the plain FP64 path
+    on the same inputs (rate and accuracy). Returns a dict; the contexts are freed on return."""
     import torch
     import paper_2512_13550_gb300 as nof
     from paper_2512_13550_gb300 import inputs
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    xyz, orb, aux = workload(2 + rank, name)
+
+    def make_ctx(p):
+        ctx = nof.Context(precision=p, stream=stream)
+        ctx.build_B(xyz, orb, aux)
+        return ctx
+
+    t0 = time.perf_counter()
+    ctx = make_ctx(prec)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    s = ctx.sizes
+    n = s["nbf"]
+    nd = ctx.split_digits() if prec == nof.PREC_SPLIT_BF16 else 0
+    tiles = None
+    if prec == nof.PREC_SPLIT_BF16:
+        t = ctx.tuned_tiles()
+        tiles = {"gemm1_bn": t[0], "gemm2_bn": t[1], "gemm3_bn": t[2], "gemm3_chunk_atoms": t[3],
+                 "picked_by": "autotuner (CUDA-event timing of candidate launch shapes at set-up; GEMM1 with L2 flushed)"}
+    Q = torch.tensor(inputs.random_orthogonal(n, rank), dtype=torch.float64, device="cuda")
+    C = ctx.lowdin(Q)
+    gam = torch.tensor(inputs.random_gamma(s["ngamma"], 1), dtype=torch.float64, device="cuda")
+    E = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    gg = torch.empty(s["ngamma"], dtype=torch.float64, device="cuda")
+    # contexts that take the timed steps in turn: one when its B (digits or FP64) is more than twice
+    # L2, else two with separate copies of B, so that every evaluation reads a B last touched two
+    # steps earlier (inputs larger than L2 instead of a flush between steps)
+    b_bytes = (2 * nd if nd else 8) * s["naux"] * n * n
+    ctxs = [ctx] if b_bytes > 2 * L2_BYTES else [ctx, make_ctx(prec)]
+    for c in ctxs:
+        for _ in range(warmup):
+            c.energy_grad(C, gam, E, g, gg)
+    torch.cuda.synchronize()
+    runs = [(lambda c=c: c.energy_grad(C, gam, E, g, gg)) for c in ctxs]
+    per_eval = None
+    if not args.no_graph:
+        cgs = []
+        l0 = nof.kernel_launches()
+        for c in ctxs:
+            cg = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(cg, stream=stream):
+                c.energy_grad(C, gam, E, g, gg)
+            cgs.append(cg)
+        per_eval = (nof.kernel_launches() - l0) // len(ctxs)
+        torch.cuda.synchronize()
+        for cg in cgs:
+            cg.replay()
+        torch.cuda.synchronize()
+        runs = [cg.replay for cg in cgs]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local) if clocks else None
+    if sampler:
+        sampler.__enter__()
+    l0 = nof.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        runs[i % len(runs)]()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.__exit__(None, None, None)
+    ms = e0.elapsed_time(e1)
+    launches = nof.kernel_launches() - l0 if per_eval is None else per_eval * steps
+    value, t_max = aggregate(ms, steps, world, dist, device="cuda")
+    E_fast, g_fast = float(E.item()), g.clone()
+
+    # each contraction timed with CUDA events inside the library (direct calls), ctx alternating
+    # with the others as in the timed loop
+    prof = {}
+    pe = max(2, min(steps, 5))
+    for which in ((1, 2, 3) if prec == nof.PREC_SPLIT_BF16 else (1,)):
+        ctx.profile(which)
+        for i in range(pe * len(ctxs)):
+            ctxs[i % len(ctxs)].energy_grad(C, gam, E, g, gg)
+        ms_w, cnt, kname = ctx.profile_read()
+        ctx.profile(0)
+        prof[which] = (ms_w / max(cnt, 1), kname)
+    dom = max(prof, key=lambda w: prof[w][0])
+    roof = roofline(prec, s, dom, prof[dom][0], prof[dom][1], nd=nd or 5)
+    roof["all_contractions_ms_per_launch"] = {CONTRACTIONS[w][0]: prof[w][0] for w in prof}
+
+    out = {"workload": WORKLOADS[name], "sizes": _sizes_label(s), "value": value, "ms_per_step": t_max / steps,
+           "steps": steps, "warmup": warmup, "setup_s": round(setup_s, 2), "digits": nd or None, "tiles": tiles,
+           "l2": ("inputs larger than L2: two contexts with separate copies of B's digits take the steps in turn"
+                  if len(ctxs) == 2 else f"inputs larger than L2 (B: {b_bytes / 1e9:.2f} GB per context)"),
+           "timing": ("CUDA-graph replay of one evaluation per step" if not args.no_graph else "one API call per step")
+                     + ", one region bracketed by CUDA events on the library's stream",
+           "gpu_launches": int(launches), "roofline": roof,
+           "eval_roofline": eval_roofline(prec, s, t_max / steps, nd=nd or 5)}
+    if sampler:
+        out["clocks"] = sampler.summary()
+
+    if e2e:
+        out["e2e"] = e2e_loop(ctxs, C, gam, E, g, gg, stream, max(3, steps // 2), world, g_fast)
+    for c in ctxs[1:]:
+        c.close()
+
+    # the plain FP64 GPU path on the same (C, gamma): its rate and the split path's accuracy
+    if fp64 and prec == nof.PREC_SPLIT_BF16:
+        ctx.close()
+        torch.cuda.synchronize()
+        c64 = make_ctx(nof.PREC_FP64)
+        c64.energy_grad(C, gam, E, g, gg)  # warm-up (module loads, first launches)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(fp64_steps):
+            c64.energy_grad(C, gam, E, g, gg)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        rate64 = fp64_steps / (a0.elapsed_time(a1) / 1e3)
+        dE = abs(E_fast - float(E.item()))
+        dg = float((g_fast - g).abs().max().item())
+        out["fp64_plain_evals_per_s"] = rate64
+        out["fp64_plain_steps"] = fp64_steps
+        out["speedup_vs_fp64_plain"] = value / world / rate64
+        out["accuracy"] = {"max_abs_dE_vs_fp64_gpu": dE, "max_abs_dg_vs_fp64_gpu": dg, "gate": ACC_GATE,
+                           "pass": bool(dE <= ACC_GATE and dg <= ACC_GATE)}
+        c64.close()
+    else:
+        ctx.close()
+    torch.cuda.synchronize()
+    return out
+
+
+def e2e_loop(ctxs, C, gam, E, g, gg, stream, steps, world, g_ref):
+    """End to end through the public API from pinned host buffers, pipelined the way a serving loop
+    runs: every step uploads its own C and gamma and the host reads back every step's E and g. Two
+    device buffer sets take the steps in turn (with two contexts, one per set); step i's upload (on
+    a copy stream) and step i-1's readback (on a second copy stream) overlap evaluation i, and the
+    evaluations stay serialised on the library's stream."""
+    import torch
+    n = C.shape[0]
+    hC = C.cpu().pin_memory()
+    hgam = gam.cpu().pin_memory()
+    hE = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
+    hg = [torch.empty(n, n, dtype=torch.float64).pin_memory() for _ in range(2)]
+    bC, bgam = [torch.empty_like(C) for _ in range(2)], [torch.empty_like(gam) for _ in range(2)]
+    bE, bg, bgg = [torch.empty_like(E) for _ in range(2)], [torch.empty_like(g) for _ in range(2)], \
+        [torch.empty_like(gg) for _ in range(2)]
+    ectx = ctxs * 2 if len(ctxs) == 1 else ctxs
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("up", "done", "down")}
+    # one untimed pass over both buffer sets (the library records their graphs on the second call)
+    for k in range(2):
+        for _ in range(2):
+            ectx[k].energy_grad(bC[k].copy_(C), bgam[k].copy_(gam), bE[k], bg[k], bgg[k])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps + 1):
+        if i < steps:
+            k = i % 2
+            with torch.cuda.stream(up):
+                up.wait_event(ev["done"][k])
+                bC[k].copy_(hC, non_blocking=True)
+                bgam[k].copy_(hgam, non_blocking=True)
+                ev["up"][k].record(up)
+            with torch.cuda.stream(stream):
+                stream.wait_event(ev["up"][k])
+                stream.wait_event(ev["down"][k])
+                ectx[k].energy_grad(bC[k], bgam[k], bE[k], bg[k], bgg[k])
+                ev["done"][k].record(stream)
+            with torch.cuda.stream(down):
+                down.wait_event(ev["done"][k])
+                hE[k].copy_(bE[k], non_blocking=True)
+                hg[k].copy_(bg[k], non_blocking=True)
+                ev["down"][k].record(down)
+        if i >= 1:
+            ev["down"][(i - 1) % 2].synchronize()
+    e2e_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    ok = bool(torch.equal(hg[(steps - 1) % 2], g_ref.cpu()))
+    return {"value": world * steps / e2e_s, "unit": "evals/s", "steps": steps,
+            "h2d_bytes_per_step": hC.numel() * 8 + hgam.numel() * 8,
+            "d2h_bytes_per_step": hE[0].numel() * 8 + hg[0].numel() * 8,
+            "pipeline": "two buffer sets in turn: upload of step i and readback of step i-1 overlap evaluation i",
+            "readback_matches_device": ok}
+
+
+def run_batch_system(args, warmup=None, steps=None):
+    """Many independent geometries (H-chain frames of uneven length, Gaussian displacements sigma
+    = 0.05 bohr, 3 s + 10 aux s per H) evaluated concurrently: every context on its own stream,
+    the whole batch captured as one CUDA graph and replayed; L2 flushed before each replay.
+    Returns a dict."""
+    import torch
+    import paper_2512_13550_gb300 as nof
+    from paper_2512_13550_gb300 import inputs
+    warmup = args.warmup if warmup is None else warmup
     orb, aux = inputs.basis_3s_10aux()
     sizes = [int(x) for x in inputs.batch_sizes(args.batch_count, seed=3, lo=8, hi=args.batch_max)]
     t0 = time.perf_counter()
@@ -252,7 +582,7 @@ def run_batch(args):
     setup_s = time.perf_counter() - t0
     master = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         nof.energy_grad_batch(ctxs, Cs, gs, Es, Gs, GGs, stream=master)
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
@@ -260,10 +590,10 @@ def run_batch(args):
     with torch.cuda.graph(graph, stream=master):
         nof.energy_grad_batch(ctxs, Cs, gs, Es, Gs, GGs, stream=master)
     per_batch = nof.kernel_launches() - l0
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         graph.replay()
     torch.cuda.synchronize()
-    reps = max(3, args.steps // max(1, len(ctxs)))
+    reps = steps if steps is not None else max(3, args.steps // max(1, len(ctxs)))
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
     with ClockSampler(0) as clk:
         for i in range(reps):
@@ -274,14 +604,38 @@ def run_batch(args):
                 evs[i][1].record(master)
         torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    line = {"metric": METRIC, "value": len(ctxs) * reps / (ms / 1e3), "unit": "evals/s", "n_gpus": 1,
-            "steps": reps, "warmup": args.warmup, "ms_per_step": ms / reps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": f"batch of {len(ctxs)} H-chain frames, lengths {min(sizes)}..{max(sizes)} "
-                                   f"(even, seed 3), sigma 0.05 bohr displacements, 3 s + 10 aux s per H",
-                       "timing": "one CUDA-graph replay of the whole batch per step, L2 flushed between steps",
-                       "setup_s": round(setup_s, 1)},
-            "gpu_launches": per_batch * reps, "clocks": clk.summary()}
+    # algorithmic work of the batch (sum over frames) and its whole-batch roofline
+    peaks, src = _peaks()
+    fl, by = 0.0, 0.0
+    for c in ctxs:
+        f1, b1 = eval_work(c.sizes["naux"], c.sizes["nbf"], c.sizes["nact"])
+        fl += f1
+        by += b1
+    nd = ctxs[0].split_digits()
+    t_roof = max(fl / (peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) / (nd * (nd + 1) // 2) * 1e12),
+                 by / (peaks["hbm_gbs"] * 1e9))
+    out = {"workload": f"batch of {len(ctxs)} H-chain frames, lengths {min(sizes)}..{max(sizes)} (even, seed 3), "
+                       f"sigma 0.05 bohr displacements, 3 s + 10 aux s per H",
+           "value": len(ctxs) * reps / (ms / 1e3), "ms_per_step": ms / reps, "steps": reps, "warmup": warmup,
+           "frames": len(ctxs), "setup_s": round(setup_s, 1), "digits": nd,
+           "timing": "one CUDA-graph replay of the whole batch per step (CUDA events on the master stream), L2 "
+                     "flushed (256 MiB write) before each step",
+           "gpu_launches": per_batch * reps, "clocks": clk.summary(),
+           "eval_roofline": {"algorithmic_flops": fl, "algorithmic_bytes": by, "t_roofline_ms": t_roof * 1e3,
+                             "ms_per_batch": ms / reps, "frac": t_roof * 1e3 / (ms / reps), "peak_source": src}}
+    for c in ctxs:
+        c.close()
+    torch.cuda.synchronize()
+    return out
+
+
+def run_batch(args):
+    o = run_batch_system(args)
+    line = {"metric": METRIC, "value": o["value"], "unit": "evals/s", "n_gpus": 1, "steps": o["steps"],
+            "warmup": o["warmup"], "ms_per_step": o["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": f"bf16-digit{o['digits']}", "data": "synthetic",
+            "config": {"workload": o["workload"]}, "setup": {k: o[k] for k in ("timing", "setup_s", "frames")},
+            "eval_roofline": o["eval_roofline"], "gpu_launches": o["gpu_launches"], "clocks": o["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -452,7 +806,6 @@ def main():
         return run_dynamics(args)
     import torch
     import paper_2512_13550_gb300 as nof
-    from paper_2512_13550_gb300 import inputs
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -462,234 +815,70 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    prec = {"auto": nof.PREC_SPLIT_BF16, "split": nof.PREC_SPLIT_BF16, "fp64": nof.PREC_FP64}[args.precision]
+    name = HEADLINE if args.workload == "default" else args.workload
+    prec = nof.PREC_SPLIT_BF16 if args.precision == "split" else nof.PREC_FP64
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    xyz, orb, aux = workload(2 + rank, args.workload)
-    wl_name = WORKLOAD_H200 if args.workload == "h200" else WORKLOAD
-
-    def make_ctx(p):
-        ctx = nof.Context(precision=p, stream=stream)
-        ctx.build_B(xyz, orb, aux)
-        return ctx
-
-    try:
-        ctx = make_ctx(prec)
-    except nof.NofError as e:
-        if args.precision != "auto":
-            raise
-        print(f"# split path unavailable ({e}); timing the FP64 path", file=sys.stderr)
-        prec = nof.PREC_FP64
-        ctx = make_ctx(prec)
-    s = ctx.sizes
-    n = s["nbf"]
-    tiles = None
-    if prec == nof.PREC_SPLIT_BF16:
-        t = ctx.tuned_tiles()
-        tiles = {"gemm1_bn": t[0], "gemm2_bn": t[1], "gemm3_bn": t[2], "gemm3_chunk_atoms": t[3],
-                 "picked_by": "autotuner (CUDA-event timing of candidate launch shapes at set-up; GEMM1 with L2 flushed)"}
-    Q = torch.tensor(inputs.random_orthogonal(n, 0), dtype=torch.float64, device="cuda")
-    C = ctx.lowdin(Q)
-    gam = torch.tensor(inputs.random_gamma(s["ngamma"], 1), dtype=torch.float64, device="cuda")
-    E = torch.empty(1, dtype=torch.float64, device="cuda")
-    g = torch.empty(n, n, dtype=torch.float64, device="cuda")
-    gg = torch.empty(s["ngamma"], dtype=torch.float64, device="cuda")
 
     if args.profile_evals:
+        xyz, orb, aux = workload(2, name)
+        ctx = nof.Context(precision=prec, stream=stream)
+        ctx.build_B(xyz, orb, aux)
+        s = ctx.sizes
+        from paper_2512_13550_gb300 import inputs
+        C = ctx.lowdin(torch.tensor(inputs.random_orthogonal(s["nbf"], 0), dtype=torch.float64, device="cuda"))
+        gam = torch.tensor(inputs.random_gamma(s["ngamma"], 1), dtype=torch.float64, device="cuda")
         for _ in range(max(1, args.warmup)):
-            ctx.energy_grad(C, gam, E, g, gg)
+            E, _, _ = ctx.energy_grad(C, gam)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("evals")
         for _ in range(args.profile_evals):
-            ctx.energy_grad(C, gam, E, g, gg)
+            E, _, _ = ctx.energy_grad(C, gam)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-        print(json.dumps({"profile_evals": args.profile_evals, "precision": prec,
+        print(json.dumps({"profile_evals": args.profile_evals, "workload": name, "precision": prec,
                           "E": float(E.item())}), flush=True)
         return 0
 
-    def contexts(c, p):
-        """The contexts that take the timed steps in turn: `c` alone when its B (digits, or FP64)
-        is larger than twice L2, else `c` and a second context of the same workload with its own
-        copy of B, so that every evaluation reads a B last touched two steps earlier (inputs
-        larger than L2 instead of a flush between steps)."""
-        b_bytes = (2 * c.split_digits() if p == nof.PREC_SPLIT_BF16 else 8) * s["naux"] * n * n
-        return [c] if b_bytes > L2_BYTES * 2 else [c, make_ctx(p)]
-
-    def timed_loop(cs, steps, warmup, profile=False, graph=False, flush=None):
-        """Time `steps` evaluations as one region bracketed by CUDA events, the contexts `cs`
-        taking them in turn; returns (ms, kernel launches, profile). With graph=True one evaluation
-        per context is captured in a CUDA graph and replayed (the library makes no host
-        synchronisation or allocation inside an evaluation, so the capture holds all of it).
-        With a `flush` buffer (larger than L2) it is written before every step instead, and each
-        step is timed alone."""
-        for c in cs:
-            for _ in range(warmup):
-                c.energy_grad(C, gam, E, g, gg)
-        torch.cuda.synchronize()
-        runs = [(lambda c=c: c.energy_grad(C, gam, E, g, gg)) for c in cs]
-        per_eval = None
-        if graph:
-            cgs = []
-            l0 = nof.kernel_launches()
-            for c in cs:
-                cg = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(cg, stream=stream):
-                    c.energy_grad(C, gam, E, g, gg)
-                cgs.append(cg)
-            per_eval = (nof.kernel_launches() - l0) // len(cs)
-            torch.cuda.synchronize()
-            for _ in range(warmup):
-                for cg in cgs:
-                    cg.replay()
-            torch.cuda.synchronize()
-            runs = [cg.replay for cg in cgs]
-        l0 = nof.kernel_launches()
-        if flush is not None:
-            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                   for _ in range(steps)]
-            for i in range(steps):
-                flush.fill_(float(i))
-                evs[i][0].record(stream)
-                runs[i % len(cs)]()
-                evs[i][1].record(stream)
-            torch.cuda.synchronize()
-            ms = sum(a.elapsed_time(b) for a, b in evs)
-        else:
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for i in range(steps):
-                runs[i % len(cs)]()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-        launches = nof.kernel_launches() - l0 if per_eval is None else per_eval * steps
-        prof = None
-        if profile:  # the dominant kernel of cs[0], timed with CUDA events inside the library
-            cs[0].profile(True)
-            for i in range(steps):
-                cs[i % len(cs)].energy_grad(C, gam, E, g, gg)
-            prof = cs[0].profile_read()
-            cs[0].profile(False)
-        return ms, launches, prof
-
+    head = run_system(name, args, stream, prec, rank=rank, world=world, dist=dist, clocks=True, local=local,
+                      fp64_steps=1 if name == "h1000" else 3)
+    extras = {}
+    if args.workload == "default" and not args.no_extras and world == 1:
+        # the other workloads, each with its own rate, end-to-end rate, rooflines and FP64 comparison
+        extras["h200"] = run_system("h200", args, stream, prec, steps=max(args.steps, 20), fp64_steps=3)
+        extras["h50"] = run_system("h50", args, stream, prec, steps=max(10 * args.steps, 200), fp64_steps=10)
+        if prec == nof.PREC_SPLIT_BF16:
+            extras["batch"] = run_batch_system(args, warmup=3, steps=3)
     if dist is not None:
         dist.barrier()
-    torch.cuda.synchronize()
-    ctxs = contexts(ctx, prec)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        ms, launches, prof = timed_loop(ctxs, args.steps, args.warmup, profile=True, graph=not args.no_graph)
-    torch.cuda.synchronize()
-    value, t_max = aggregate(ms, args.steps, world, dist, device="cuda")
-    # the same steps on one context with a 256 MiB write before each (timed per step), reported
-    # beside the value for comparison
-    flushbuf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    ms_fl, _, _ = timed_loop([ctx], args.steps, args.warmup, graph=not args.no_graph, flush=flushbuf)
-    del flushbuf
-    if dist is not None:
-        dist.barrier()
-    E_fast = float(E.item())
-    g_fast = g.clone()
-
-    # accuracy and throughput of the plain FP64 path on the same inputs
-    if prec == nof.PREC_FP64:
-        ctx64, E64, dE, dg = ctx, E_fast, 0.0, 0.0
-        ms64, steps64 = ms, args.steps
-    else:
-        ctx64 = make_ctx(nof.PREC_FP64)
-        ms64, _, _ = timed_loop(contexts(ctx64, nof.PREC_FP64), args.fp64_steps, 3, graph=not args.no_graph)
-        steps64 = args.fp64_steps
-        E64 = float(E.item())
-        dE = abs(E_fast - E64)
-        dg = float((g_fast - g).abs().max().item())
-
-    # end-to-end through the public API from pinned host buffers, pipelined the way a serving
-    # loop would run it: every step uploads its own inputs and the host reads back every step's
-    # E and g. Two contexts of the workload (each with its own copy of B's digits, 180 MB in all:
-    # more than L2) and two buffer sets take the steps in turn on the same stream, so the
-    # evaluations stay serialised and each reads a B last touched two steps earlier. Step i's
-    # upload (on a copy stream) and step i-1's readback (on a second copy stream) overlap
-    # evaluation i; each context replays its recorded graph.
-    hC = C.cpu().pin_memory()
-    hgam = gam.cpu().pin_memory()
-    hE = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
-    hg = [torch.empty(n, n, dtype=torch.float64).pin_memory() for _ in range(2)]
-    bC, bgam = [torch.empty_like(C) for _ in range(2)], [torch.empty_like(gam) for _ in range(2)]
-    bE, bg, bgg = [torch.empty_like(E) for _ in range(2)], [torch.empty_like(g) for _ in range(2)], \
-        [torch.empty_like(gg) for _ in range(2)]
-    ectx = ctxs * 2 if len(ctxs) == 1 else ctxs  # the context of each buffer set
-    up, down = torch.cuda.Stream(), torch.cuda.Stream()
-    ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("up", "done", "down")}
-    e2e_steps = max(3, args.steps // 2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(e2e_steps + 1):
-        if i < e2e_steps:
-            k = i % 2
-            with torch.cuda.stream(up):  # set k's inputs are free once evaluation i-2 is done
-                up.wait_event(ev["done"][k])
-                bC[k].copy_(hC, non_blocking=True)
-                bgam[k].copy_(hgam, non_blocking=True)
-                ev["up"][k].record(up)
-            with torch.cuda.stream(stream):
-                stream.wait_event(ev["up"][k])
-                stream.wait_event(ev["down"][k])  # and its outputs once step i-2's readback is done
-                ectx[k].energy_grad(bC[k], bgam[k], bE[k], bg[k], bgg[k])
-                ev["done"][k].record(stream)
-            with torch.cuda.stream(down):
-                down.wait_event(ev["done"][k])
-                hE[k].copy_(bE[k], non_blocking=True)
-                hg[k].copy_(bg[k], non_blocking=True)
-                ev["down"][k].record(down)
-        if i >= 1:
-            ev["down"][(i - 1) % 2].synchronize()  # the host has step i-1's E and g
-    e2e_s = time.perf_counter() - t0
-    torch.cuda.synchronize()
-    e2e_ok = bool(torch.equal(hg[(e2e_steps - 1) % 2], g_fast.cpu()))  # g_fast: the timed loop's result
-    h2d = hC.numel() * 8 + hgam.numel() * 8
-    d2h = hE[0].numel() * 8 + hg[0].numel() * 8
-
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
-
-    dom_ms, dom_launches, dom_name = prof
-    roof = roofline(prec, s, dom_ms / max(dom_launches, 1), dom_name, traffic=(
-        TRAFFIC_GEMM1_BYTES if args.workload == "h50" else None),
-        nd=ctx.split_digits() if prec == nof.PREC_SPLIT_BF16 else 4)
+    nd = head["digits"]
     line = {
-        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": head["value"], "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if prec == nof.PREC_SPLIT_BF16 else "f64",
+        "dtype": (f"bf16-digit{nd} (exact BF16 digit-plane products of ~{8 * nd}-bit operands, FP32 exact level "
+                  f"sums, double-float/FP64 between the contractions)") if nd else "f64",
         "data": "synthetic",
-        "config": {"workload": wl_name, "path": "split-bf16 tcgen05" if prec else "plain fp64",
-                   "tiles": tiles,
-                   "l2": ("inputs larger than L2: two contexts with separate copies of B's digits take "
-                          "the steps in turn" if len(ctxs) == 2 else "inputs larger than L2 (B's digits)"),
-                   "l2_flushed_evals_per_s": args.steps / (ms_fl / 1e3),
-                   "timing": "CUDA-graph replay of one evaluation per step" if not args.no_graph
-                             else "one API call per step",
-                   "parallelism": f"replicas x{world}"},
-        "accuracy": {"max_abs_dE_vs_fp64_gpu": dE, "max_abs_dg_vs_fp64_gpu": dg,
-                     "gate": ACC_GATE, "pass": bool(dE <= ACC_GATE and dg <= ACC_GATE)},
-        "fp64_plain_evals_per_s": steps64 / (ms64 / 1e3),
-        "speedup_vs_fp64_plain": value / world / (steps64 / (ms64 / 1e3)),
-        "roofline": roof,
-        "e2e": {"value": world * e2e_steps / e2e_s, "unit": "evals/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "pipeline": "two buffer sets in turn: upload of step i and readback of step i-1 overlap evaluation i",
-                "l2": ("two contexts in turn, each with its own copy of B's digits (more than L2 in all)"
-                       if ectx[0] is not ectx[1] else "inputs larger than L2 (B's digits)"),
-                "readback_matches_device": e2e_ok},
-        "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "config": {"workload": WORKLOADS[name]},
+        "setup": {k: head[k] for k in ("sizes", "setup_s", "tiles", "l2", "timing")} |
+                 {"parallelism": f"replicas x{world}"},
+        "accuracy": head.get("accuracy"),
+        "fp64_plain_evals_per_s": head.get("fp64_plain_evals_per_s"),
+        "speedup_vs_fp64_plain": head.get("speedup_vs_fp64_plain"),
+        "roofline": head["roofline"],
+        "eval_roofline": head["eval_roofline"],
+        "e2e": head["e2e"],
+        "gpu_launches": head["gpu_launches"],
+        "clocks": head.get("clocks"),
     }
-    if not args.no_cpu_baseline and args.workload == "h50":
-        line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+    if extras:
+        line["configs"] = extras
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(name, 2 if name == "h1000" else (8 if name == "h200" else 500))
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -706,57 +895,6 @@ def aggregate(ms_local: float, steps: int, world: int, dist=None, device=None):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_max = float(tt.item())
     return world * steps / (t_max / 1e3), t_max
-
-
-def _peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f), "measured"
-    except OSError:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
-
-
-# FP64 roofline of the plain path: 2 FP64 FMA per clock per SM (the rate an FMA-throughput probe
-# measured on GB300: 1.19 TFLOP/s), x 152 SMs x 2.07 GHz x 2 FLOP = 1.26 TFLOP/s.
-FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
-
-# DRAM bytes (read + write) of one GEMM1 launch on the H50 workload from an ncu capture of the
-# current kernel (profiles/), or None when the kernel has changed since the counters were taken.
-TRAFFIC_GEMM1_BYTES = 96589824 + 4070656  # profiles/digit_gemm_h50_ncu.md (paired-MMA kernel)
-
-
-def roofline(prec, s, ms_per_launch, name, traffic=None, nd=4):
-    n, X, a = s["nbf"], s["naux"], s["nact"]
-    peaks, src = _peaks()
-    if prec == 0:
-        flops = 2.0 * X * n * n * a  # half transform T = B C_a
-        achieved = flops / (ms_per_launch / 1e3) / 1e12
-        peak = FP64_PEAK_TFLOPS
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None, "traffic": None,
-                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (probe-measured rate)"}
-    # half transform GEMM1: reads the nd BF16 digit planes of B (2 nd bytes per element of B) and
-    # writes T as double-floats (8 bytes per element of T); on the tensor cores it is
-    # nd (nd + 1) / 2 BF16 digit-plane products of (X n) x n x a. It is timed inside evaluation
-    # steps that run back to back, so a tensor bound takes the sustained BF16 peak.
-    nbytes = 2.0 * nd * X * n * n + 8.0 * X * n * a
-    flops = nd * (nd + 1) // 2 * 2.0 * X * n * n * a
-    tc_peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-    t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
-    t_tc = flops / (tc_peak * 1e12)
-    sec = ms_per_launch / 1e3
-    if t_tc > t_hbm:
-        achieved = flops / sec / 1e12
-        return {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
-                "frac": achieved / tc_peak, "traffic": traffic, "algorithmic_flops": flops,
-                "algorithmic_bytes": nbytes, "ms_per_launch": ms_per_launch, "digits": nd,
-                "peak_source": f"{src} BF16 dense GEMM, sustained (MEASURED_PEAKS.json bf16_tflops_sustained)"}
-    achieved = nbytes / sec / 1e9
-    peak = peaks["hbm_gbs"]
-    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "algorithmic_bytes": nbytes, "ms_per_launch": ms_per_launch, "digits": nd,
-            "peak_source": f"{src} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
 
 
 if __name__ == "__main__":

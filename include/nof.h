@@ -273,10 +273,12 @@ int nof_sync(nof_ctx* ctx);
 
 /* Measurement hooks (no paper counterpart; used by the benchmark):
  * nof_kernel_launches: number of kernels this library has launched in the process so far.
- * nof_profile: enable (1) / disable (0) CUDA-event timing of the dominant kernel of each
- *   evaluation on the context's stream; enabling clears the accumulated record.
+ * nof_profile: CUDA-event timing, on the context's stream, of one contraction of every later
+ *   evaluation: enable = 1 the half transform T = B C (the default), 2 the full transform
+ *   b = C^T T (split path), 3 the Lagrangian contraction sum_P T^P W^P (split path); 0 turns it
+ *   off. Any call clears the accumulated record; other values are NOF_EINVAL.
  * nof_profile_read: synchronise and return the accumulated device time (ms) and launch count
- *   of the dominant kernel, and its name (static string; may be NULL). */
+ *   of the timed contraction, and its kernel's name (static string; may be NULL). */
 long long nof_kernel_launches(void);
 int nof_profile(nof_ctx* ctx, int enable);
 int nof_profile_read(nof_ctx* ctx, double* ms, int* launches, const char** name);

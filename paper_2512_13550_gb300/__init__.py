@@ -357,8 +357,10 @@ class Context:
         _check(load_library().nof_dipole(self._h, _dptr(C), _dptr(gamma), _dptr(mu)))
         return mu
 
-    def profile(self, enable: bool = True):
-        _check(load_library().nof_profile(self._h, 1 if enable else 0))
+    def profile(self, which: int = 1):
+        """Time one contraction of every later evaluation (1 half transform, 2 full transform,
+        3 Lagrangian contraction; 0 or False: off) with CUDA events (nof_profile)."""
+        _check(load_library().nof_profile(self._h, int(which)))
 
     def profile_read(self):
         ms, cnt, name = ctypes.c_double(), ctypes.c_int(), ctypes.c_char_p()

@@ -29,8 +29,8 @@ static void prof_clear(nof_ctx* c) {
     ev->clear();
 }
 
-int prof_begin(nof_ctx* c, const char* name) {
-    if (!c->prof_on) return NOF_OK;
+int prof_begin(nof_ctx* c, const char* name, int which) {
+    if (c->prof_on != which) return NOF_OK;
     if (!c->prof_events) c->prof_events = new EventPairs();
     auto* ev = static_cast<EventPairs*>(c->prof_events);
     cudaEvent_t a, b;
@@ -42,8 +42,8 @@ int prof_begin(nof_ctx* c, const char* name) {
     return NOF_OK;
 }
 
-int prof_end(nof_ctx* c) {
-    if (!c->prof_on) return NOF_OK;
+int prof_end(nof_ctx* c, int which) {
+    if (c->prof_on != which) return NOF_OK;
     auto* ev = static_cast<EventPairs*>(c->prof_events);
     NOF_CUDA(cudaEventRecord(ev->back().second, c->stream));
     return NOF_OK;
@@ -672,8 +672,13 @@ long long nof_kernel_launches(void) { return g_launches.load(); }
 int nof_profile(nof_ctx* c, int enable) {
     NOF_TRY(check_ctx(c, false));
     NOF_CUDA(cudaStreamSynchronize(c->stream));
+    if (enable < 0 || enable > 3) {
+        nof_set_error("nof_profile: enable must be 0 (off) or 1..3 (the contraction to time)");
+        return NOF_EINVAL;
+    }
     prof_clear(c);
-    c->prof_on = enable ? 1 : 0;
+    c->prof_name = nullptr;
+    c->prof_on = enable;
     return NOF_OK;
 }
 

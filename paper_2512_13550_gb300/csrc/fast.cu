@@ -611,7 +611,9 @@ int b_chain(nof_ctx* c, const double* C, cudaEvent_t t_written) {
     k_T2_digits<<<nblk((long long)X * f->katK * ap * 2), 256, 0, st>>>(f->Tdf, f->colT, X, n, ap, f->katK, f->nd,
                                                                        f->Td2, f->e2);
     NOF_LAUNCH_CHECK();
-    return digit_gemm_run(f->g2, st);
+    NOF_TRY(prof_begin(c, "k_digit_gemm (full transform b = C^T T, tcgen05)", 2));
+    NOF_TRY(digit_gemm_run(f->g2, st));
+    return prof_end(c, 2);
 }
 
 // J and K from b on stream s: chunk partials, then their fixed-order sum. The sum also clears
@@ -656,7 +658,9 @@ int w_digits(nof_ctx* c) {
 int lagrangian(nof_ctx* c, const double* C) {
     FastState* f = c->fast;
     cudaStream_t st = c->stream;
+    NOF_TRY(prof_begin(c, "k_digit_gemm (Lagrangian contraction sum_P T W, tcgen05)", 3));
     NOF_TRY(digit_gemm_run(f->g3, st));
+    NOF_TRY(prof_end(c, 3));
     const long long na = (long long)f->n * f->a;
     k_lambda_from_parts<<<(unsigned)((na + 31) / 32), 256, 0, st>>>(f->Lpart, f->g3.g.kchunks, na, c->HC, c->occ,
                                                                    f->a, c->Lam);

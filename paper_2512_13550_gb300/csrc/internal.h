@@ -95,15 +95,16 @@ struct nof_ctx {
     // nuclear gradient (FP64 path): L^-1 of the Coulomb metric kept from set-up, and workspaces
     // allocated on the first nof_nuclear_gradient
     double *Linv, *gr_cfit, *gr_Y, *gr_Gam, *gr_Z, *gr_small;
-    // dominant-kernel timing (nof_profile)
+    // timing of one contraction (nof_profile): 0 off, 1..3 the contraction bracketed
     int prof_on;
     const char* prof_name;
     void* prof_events;  // std::vector<std::pair<cudaEvent_t, cudaEvent_t>>*
 };
 
-// Bracket the dominant kernel of an evaluation with timing events when profiling is on.
-int prof_begin(nof_ctx* c, const char* name);
-int prof_end(nof_ctx* c);
+// Bracket one contraction of an evaluation with timing events when profiling selects it
+// (which: 1 half transform, 2 full transform, 3 Lagrangian contraction; nof_profile).
+int prof_begin(nof_ctx* c, const char* name, int which = 1);
+int prof_end(nof_ctx* c, int which = 1);
 
 // ---------------------------------------------------------------------------------------
 // FP64 building blocks (linalg.cu)
