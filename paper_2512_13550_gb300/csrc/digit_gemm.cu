@@ -1,19 +1,23 @@
 // Exact digit-plane GEMM on the 5th-generation tensor cores (tcgen05 + TMEM, bulk copies), sm_103a.
 //
 // Operands are "digit planes": a real matrix X with a power-of-two scale 2^e per row is written
-// as X = 2^e sum_{i<nd} d_i 256^{-(i+1)} with integer digits |d_0| <= 256, |d_i| <= 128 (i > 0),
-// nd = 4 or 5, each plane stored as BF16 (integers up to 256 are exact in BF16). For A (M x K)
-// and B (N x K),
+// as X = 2^e sum_{i<nd} d_i 256^{-(i+1)} with integer digits |d_i| <= 128 for i > 0 and
+// |d_0| <= digit_top(nd) (128 with nd = 5, where the scale leaves one bit of headroom; 256 with
+// nd = 4), nd = 4 or 5, each plane stored as BF16 (integers up to 256 are exact in BF16). For
+// A (M x K) and B (N x K),
 //   sum_k A_mk B_nk = 2^{e_m + f_n} 2^{-16} sum_{lvl<nd} 256^{-lvl} S_lvl,
 //   S_lvl = sum_{i+j=lvl} sum_k dA_i[m][k] dB_j[n][k],
-// truncated at digit order nd - 1 (10 plane products for nd = 4, 15 for nd = 5). Every product
-// is exact and every partial sum is an integer below 2^24 as long as one accumulation covers
-// K <= 160 (nd = 4) or K <= 128 (nd = 5), so the FP32 TMEM accumulators hold the level sums
-// exactly. The epilogue returns the exact integer V = sum_l S_l 256^{nd-1-l}, value
-// 2^{e_m + f_n - 8 (nd + 1)} V.
-// Output modes: the exact int64 V (stored, or added atomically for split-K), the scaled value as
+// truncated at digit order nd - 1 (10 plane products for nd = 4, 15 for nd = 5), a truncation of
+// relative order 256^{1-nd}. Every product is an exact integer. The FP32 TMEM accumulators hold
+// the sums of the leading levels 0 .. nd - 3 exactly: one accumulation ("part") covers at most
+// digit_part_atoms_max(nd) K atoms (20 with 5 digits, 16 with 4), over which those levels stay
+// integers below 2^24. The last two levels, weighted 256^{2-nd} and 256^{1-nd} relative to level
+// 0, may round once a part's sum passes 2^24 (an error near 2^-40 relative with 5 digits and 2^-32
+// with 4, the order of the truncation); their sums stay below 2^31. The epilogue returns
+// V = sum_l S_l 256^{nd-1-l} (exact in the leading levels), value 2^{e_m + f_n - 8 (nd + 1)} V.
+// Output modes: the int64 V (stored, or added atomically for split-K), the scaled value as
 // a double-float, or, when each row of A and B carries its own scale on every part of K
-// (kPartAtoms atoms), the sum over parts of 2^{e_m,part + f_n,part - 8 (nd + 1)} V_part as FP64
+// (part_atoms atoms), the sum over parts of 2^{e_m,part + f_n,part - 8 (nd + 1)} V_part as FP64
 // (added atomically, or stored per K chunk for a fixed-order reduction).
 //
 // Storage: digit_gemm.h's tile-major swizzled layout, so one pipeline stage (2 K atoms x 4
@@ -572,7 +576,9 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
     if ((nd != 4 && nd != 5) || !digit_bn_ok(BN, nd) || M <= 0 || Nvalid <= 0 || katoms_total < 1 ||
         chunk_atoms < 1 || nout != 1 || (o.outf && ((o.ldo & 1) || !o.erow || !o.ecol || o.atomic)) ||
         o.ldo < Nvalid || (o.colmax && (o.group_rows < 1 || !o.outf)) || (partsc != (o.epB != nullptr)) ||
-        (partsc && (!o.outd || chunk_atoms % kPartAtoms)) || (o.outd && !partsc) ||
+        (partsc && (!o.outd || o.part_atoms < 2 || (o.part_atoms & 1) || o.part_atoms > digit_part_atoms_max(nd) ||
+                    chunk_atoms % o.part_atoms)) ||
+        (o.outd && !partsc) ||
         (o.chunk_stride && (!o.outd || o.atomic || o.chunk_stride < (long long)M * o.ldo))) {
         nof_set_error("digit_gemm: unsupported shape or output mode");
         return NOF_EINVAL;
@@ -598,7 +604,16 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
     g.Nvalid = Nvalid;
     g.katoms = chunk_atoms < katoms_total ? chunk_atoms : katoms_total;
     g.katoms_total = katoms_total;
-    g.apart = (partsc || nd == 5) ? kPartAtoms : 10;
+    // atoms per part: the per-part scales' length, or as few balanced parts as the exactness of
+    // the leading levels allows (an even count: a pipeline stage holds two atoms)
+    if (partsc) {
+        g.apart = o.part_atoms;
+    } else {
+        const int amax = digit_part_atoms_max(nd);
+        const int nparts = (g.katoms + amax - 1) / amax;
+        const int per = (g.katoms + nparts - 1) / nparts;
+        g.apart = (per + 1) / 2 * 2;
+    }
     g.nbuf = digit_nbuf(BN, nd);
     int cols = 32;
     while (cols < g.nbuf * nd * BN) cols *= 2;
@@ -751,8 +766,9 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
     return x;
 }
-// element (row r, k, plane) of a digit tensor with nd planes: plane 0 digits in [-256, 256],
-// others in [-128, 128]; rows >= valid_rows are zero
+// element (row r, k, plane) of a digit tensor with nd planes: leading digits in
+// [-digit_top(nd), digit_top(nd)], the others in [-128, 128] (the range the digitisers produce);
+// rows >= valid_rows are zero
 __global__ void k_random_digits(uint16_t* P, int RT, int rows_pad, int valid_rows, int katoms, int nd,
                                 uint32_t seed) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -762,7 +778,7 @@ __global__ void k_random_digits(uint16_t* P, int RT, int rows_pad, int valid_row
     long long rem = idx - plane * per_plane;
     long long r = rem / (katoms * 16);
     long long k = rem - r * (katoms * 16);
-    int range = plane == 0 ? 513 : 257;
+    const int range = plane == 0 ? 2 * digit_top(nd) + 1 : 257;
     int v = (int)(hash32((uint32_t)idx * 2654435761u + seed) % (uint32_t)range) - range / 2;
     if (r >= valid_rows) v = 0;
     __nv_bfloat16 b = __int2bfloat16_rn(v);
@@ -886,12 +902,13 @@ extern "C" int nof_bench_digit_gemm(int M, int N, int bn, int nd, int katoms, in
     mode &= 3;
     if (!us_per_launch || M <= 0 || N <= 0 || (nd != 4 && nd != 5) || !digit_bn_ok(bn, nd) || katoms <= 0 ||
         chunk_atoms <= 0 || bad_bits || mode > 2 || reps <= 0 ||
-        (mode == 2 && chunk_atoms % kPartAtoms) || (mode != 0 && mode != 2 && chunk_atoms < katoms)) {
+        (mode == 2 && chunk_atoms % digit_scale_part_atoms(nd)) || (mode != 0 && mode != 2 && chunk_atoms < katoms)) {
         nof_set_error("nof_bench_digit_gemm: bad arguments");
         return NOF_EINVAL;
     }
     const long long na = digit_elems(128, M, katoms, nd), nb = digit_elems(bn, N, katoms, nd);
-    const long long nkp = (katoms + kPartAtoms - 1) / kPartAtoms, kch = (katoms + chunk_atoms - 1) / chunk_atoms;
+    const int patoms = digit_scale_part_atoms(nd);
+    const long long nkp = (katoms + patoms - 1) / patoms, kch = (katoms + chunk_atoms - 1) / chunk_atoms;
     const long long nout = (long long)M * N * (mode == 2 ? kch : 1);
     uint16_t *A = nullptr, *B = nullptr;
     void* out = nullptr;
@@ -929,6 +946,7 @@ extern "C" int nof_bench_digit_gemm(int M, int N, int bn, int nd, int katoms, in
             o.chunk_stride = (long long)M * N;
             o.epA = erow;
             o.epB = ecol;
+            o.part_atoms = patoms;
         }
         DigitGemmPlan p;
         r = digit_gemm_plan(&p, A, B, M, N, bn, nd, katoms, chunk_atoms, 0, o, status);

@@ -22,8 +22,8 @@ struct DigitGemmArgs {
     int Nvalid;        // output columns written (<= tiles_n * BN)
     int katoms;        // K atoms (16 each) per split-K chunk; the last chunk may be shorter
     int katoms_total;  // K atoms of the operands (storage stride)
-    int apart;         // atoms per exact accumulation (even; <= 10 with 4 digits, <= 8 with 5: every
-                       // FP32 partial sum stays an integer below 2^24); parts are summed in the epilogue
+    int apart;         // atoms per accumulation (even; <= digit_part_atoms_max(nd): the leading levels'
+                       // FP32 partial sums stay integers below 2^24); parts are summed in the epilogue
     int tmem_cols;     // TMEM columns allocated (power of two >= nbuf * 4 * BN)
     long long* out;    // int64 fixed-point output, row-major with leading dimension ldo
     long long ldo;
@@ -101,14 +101,27 @@ struct DigitGemmOut {
     bool atomic = false;
     const int* erow = nullptr;
     const int* ecol = nullptr;
-    const int* epA = nullptr;  // per-part scales [parts][M] and [parts][Nvalid]; parts of 8 atoms
+    const int* epA = nullptr;  // per-part scales [parts][M] and [parts][Nvalid]; parts of part_atoms
     const int* epB = nullptr;
     unsigned* colmax = nullptr;
     int group_rows = 1;
+    int part_atoms = 0;  // per-part scales: K atoms per part (digit_scale_part_atoms; a chunk is whole parts)
     int* tile_counter = nullptr;  // dynamic tiles (DigitGemmArgs::tctr); one counter per plan in use
 };
-// K atoms per part when each operand row carries a scale per part of K
-constexpr int kPartAtoms = 8;
+// Digit contract. Every digit lies in [-128, 128] except the leading one, which lies in
+// [-digit_top(nd), digit_top(nd)]: with 5 digits the row scale leaves one bit of headroom so that
+// the leading digit is bounded like the others (39 significant bits), with 4 digits it does not
+// (32 bits, |d_0| <= 256). digit_headroom(nd) is that extra bit of the scale exponent.
+__host__ __device__ inline int digit_headroom(int nd) { return nd == 5 ? 1 : 0; }
+__host__ __device__ inline int digit_top(int nd) { return nd == 5 ? 128 : 256; }
+// Longest accumulation in K atoms: the leading levels 0 .. nd - 3 must stay exact, i.e. below 2^24.
+// Level 2 (5 digits) receives at most 3 128^2 per K element: 341 elements, 20 atoms (even). Level 1
+// (4 digits) receives at most 2 256 128: 256 elements, 16 atoms.
+inline int digit_part_atoms_max(int nd) { return nd == 5 ? 20 : 16; }
+// K atoms of one part of the per-part scales (the Lagrangian contraction, whose K runs over every
+// aux index): longer parts mean fewer accumulator drains, shorter ones finer scales; 4 digits,
+// which have less precision to spare, take the finer scales.
+inline int digit_scale_part_atoms(int nd) { return nd == 5 ? 16 : 8; }
 
 // A launch plan (pointers and shapes fixed at set-up).
 struct DigitGemmPlan {

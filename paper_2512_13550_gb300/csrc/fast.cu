@@ -8,13 +8,15 @@
 //
 //   GEMM1  T^P_{mu p}  = sum_nu B^P_{mu nu} C_{nu p}       rows (P, mu), digits of B per row
 //   GEMM2  b^P_{p q}   = sum_mu T^P_{mu p} C_{mu q}        rows (P, p), digits of T per (P, p)
-//   GEMM3  Lam'_{mu p} = sum_{P, r} T^P_{mu r} W^P_{r p}   split-K over (P, r), integer atomics
+//   GEMM3  Lam'_{mu p} = sum_{P, r} T^P_{mu r} W^P_{r p}   split-K over (P, r), FP64 chunk partials
 // with W^P_rp = delta_rp D^P_p - B_pr b^P_rp, D^P = A d^P, d^P_p = b^P_pp (Eq. PNOF coefficients).
-// Each operand carries 4 signed base-256 digits (about 32 significant bits) under a power-of-two
-// scale per row (GEMM1, GEMM2) or per row and part of 128 K elements (GEMM3, whose K runs over
-// all aux indices, across which |T| and |W| vary by orders of magnitude); each exact part sum V
-// has value 2^{e_row + e_col - 40} V. GEMM1's epilogue also records the maxima of |T| per (P, p)
-// over mu that set the digit scales of T for GEMM2.
+// Each operand carries nd = 4 or 5 signed base-256 digits (about 32 or 39 significant bits; see
+// digit_gemm.h for the digit contract) under a power-of-two scale per row (GEMM1, GEMM2) or per row
+// and part of 16 digit_scale_part_atoms(nd) K elements (GEMM3, whose K runs over all aux indices,
+// across which |T| and |W| vary by orders of magnitude); each part sum V has value
+// 2^{e_row + e_col - 8 (nd + 1)} V.
+// GEMM1's epilogue also records the maxima of |T| per (P, p) over mu that set the digit scales of
+// T for GEMM2.
 // Tile widths, pipeline depth and the split-K chunk of each GEMM come from the autotuner.
 #include <cuda_bf16.h>
 
@@ -25,7 +27,7 @@
 #include "internal.h"
 
 struct FastState {
-    int n, X, a, ap, katK, nkp, nd;
+    int n, X, a, ap, katK, nkp, nd, patoms;
     int bn1, bn2, bn3, nchunkJK;
     int* tctr = nullptr;        // [3] tile counters of the three digit GEMMs (dynamic tiles)
     uint16_t* Bd;  int* eB;     // [4][katK][X n][16], per row (P, mu)
@@ -144,10 +146,13 @@ __device__ __forceinline__ void put8_df(uint16_t* planes, int RT, int katoms, in
             *reinterpret_cast<uint4*>(planes + base + i * ps) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
 }
 
-__device__ __forceinline__ int exp_of(float mx) {
+// Scale exponent of a digit row or part whose largest magnitude is mx: e with
+// mx < 2^{e - digit_headroom(nd)}, so that the scaled integer Y = x 2^{8 nd - e} has
+// |Y| <= digit_top(nd) 256^{nd-1} and its signed base-256 digits meet the digit GEMM's contract.
+__device__ __forceinline__ int exp_of(float mx, int nd) {
     int e = 0;
     if (mx > 0.f) frexpf(mx, &e);
-    return e;  // mx < 2^e
+    return e + digit_headroom(nd);
 }
 
 
@@ -162,6 +167,7 @@ __global__ void k_digits_f64(const double* src, long long s_row, long long s_col
     for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);
+    e += digit_headroom(nd);  // |Y| <= digit_top(nd) 256^{nd-1}
     if (lane == 0) exps[w] = e;
     for (int k = lane; k < ncols; k += 32) {
         long long Y = __double2ll_rn(ldexp(src[w * s_row + k * s_col], 8 * nd - e));
@@ -201,7 +207,7 @@ __global__ void k_T2_digits(const float2* Tdf, const unsigned* colT, int X, int 
     const int p = (int)(u % ap);
     const long long w = u / ap;
     const int atom = (int)(w % katK), P = (int)(w / katK);
-    const int e = exp_of(__uint_as_float(colT[P * ap + p]));
+    const int e = exp_of(__uint_as_float(colT[P * ap + p]), nd);
     if (atom == 0 && half == 0) e2[P * ap + p] = e;
     const int mu0 = atom * 16 + half * 8;
     const float2* T = Tdf + (long long)P * n * ap + p;
@@ -216,16 +222,19 @@ __global__ void k_T2_digits(const float2* Tdf, const unsigned* colT, int X, int 
     put8_df(Td2, 128, katK, nd, (long long)P * ap + p, (long long)mu0, v, sh);
 }
 
-// GEMM3's A operand: rows mu, K = (P, r) padded to nkp parts of 128, a scale per (part, mu). A
-// block of 128 threads takes 8 rows (mu0..mu0+7) and one part: thread (g, i), i = row, g = group of
-// 8 K elements. The 16 threads of a row combine their maxima in shared memory; the 16 threads of
-// one K atom write its 8 rows as one contiguous 256-byte swizzled block per plane.
-__global__ void __launch_bounds__(128) k_T3_digits(const float2* Tdf, int X, int n, int ap, int nkp, int nd,
-                                                   uint16_t* Td3, int* epT) {
-    __shared__ float mx[16][9];
+// GEMM3's A operand: rows mu, K = (P, r) padded to nkp parts of PA atoms (PA 16 K elements), a
+// scale per (part, mu). A block of 16 PA threads takes 8 rows (mu0..mu0+7) and one part: thread
+// (g, i), i = row, g = group of 8 K elements. The 2 PA threads of a row combine their maxima in
+// shared memory; the 16 threads of one K atom write its 8 rows as one contiguous 256-byte swizzled
+// block per plane.
+template <int PA>
+__global__ void __launch_bounds__(16 * PA) k_T3_digits(const float2* Tdf, int X, int n, int ap, int nkp, int nd,
+                                                       uint16_t* Td3, int* epT) {
+    constexpr int kPartK = PA * 16, kPartGroups = 2 * PA;
+    __shared__ float mx[kPartGroups][9];
     const int part = blockIdx.x, i = threadIdx.x & 7, g = threadIdx.x >> 3;
     const int mu = blockIdx.y * 8 + i;
-    const long long K = (long long)part * 128 + g * 8;
+    const long long K = (long long)part * kPartK + g * 8;
     float2 v[8];
     float m = 0.f;
 #pragma unroll
@@ -243,14 +252,14 @@ __global__ void __launch_bounds__(128) k_T3_digits(const float2* Tdf, int X, int
     __syncthreads();
     float mr = 0.f;
 #pragma unroll
-    for (int gg = 0; gg < 16; ++gg) mr = fmaxf(mr, mx[gg][i]);
+    for (int gg = 0; gg < kPartGroups; ++gg) mr = fmaxf(mr, mx[gg][i]);
     if (mu >= n) return;
-    const int e = exp_of(mr);
+    const int e = exp_of(mr, nd);
     if (g == 0) epT[(long long)part * n + mu] = e;
     int sh[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) sh[j] = 8 * nd - e;
-    put8_df(Td3, 128, nkp * kPartAtoms, nd, mu, K, v, sh);
+    put8_df(Td3, 128, nkp * PA, nd, mu, K, v, sh);
 }
 
 // b^P_pq as a double-float (GEMM2's scaled output)
@@ -328,14 +337,17 @@ __device__ __forceinline__ float2 w_val(const float2* bdf, const float2* Bcdf, c
     return w;
 }
 
-// GEMM3's B operand: rows p < a (tiles of RT), K = (P, r) padded to nkp parts of 128, a scale per
-// (part, p); W is recomputed from b and D (no W array). Block and thread layout as k_T3_digits.
-__global__ void __launch_bounds__(128) k_W_digits(const float2* bdf, const float2* Bcdf, const float2* D, int X,
-                                                  int a, int ap, int nkp, int nd, int RT, uint16_t* Wd3, int* epW) {
-    __shared__ float mx[16][9];
+// GEMM3's B operand: rows p < a (tiles of RT), K = (P, r) padded to nkp parts of PA atoms, a scale
+// per (part, p); W is recomputed from b and D (no W array). Block and thread layout as k_T3_digits.
+template <int PA>
+__global__ void __launch_bounds__(16 * PA) k_W_digits(const float2* bdf, const float2* Bcdf, const float2* D, int X,
+                                                      int a, int ap, int nkp, int nd, int RT, uint16_t* Wd3,
+                                                      int* epW) {
+    constexpr int kPartK = PA * 16, kPartGroups = 2 * PA;
+    __shared__ float mx[kPartGroups][9];
     const int part = blockIdx.x, i = threadIdx.x & 7, g = threadIdx.x >> 3;
     const int p = blockIdx.y * 8 + i;
-    const long long K = (long long)part * 128 + g * 8;
+    const long long K = (long long)part * kPartK + g * 8;
     float2 v[8];
     float m = 0.f;
 #pragma unroll
@@ -352,14 +364,14 @@ __global__ void __launch_bounds__(128) k_W_digits(const float2* bdf, const float
     __syncthreads();
     float mr = 0.f;
 #pragma unroll
-    for (int gg = 0; gg < 16; ++gg) mr = fmaxf(mr, mx[gg][i]);
+    for (int gg = 0; gg < kPartGroups; ++gg) mr = fmaxf(mr, mx[gg][i]);
     if (p >= a) return;
-    const int e = exp_of(mr);
+    const int e = exp_of(mr, nd);
     if (g == 0) epW[(long long)part * a + p] = e;
     int sh[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) sh[j] = 8 * nd - e;
-    put8_df(Wd3, RT, nkp * kPartAtoms, nd, p, K, v, sh);
+    put8_df(Wd3, RT, nkp * PA, nd, p, K, v, sh);
 }
 
 template <class T>
@@ -442,8 +454,10 @@ int fast_prepare(nof_ctx* c) {
     const int nd = c->opt.digits ? c->opt.digits : ((long long)X * a > 80000 ? 5 : 4);
     f->nd = nd;
     const long long rowsB = (long long)X * n, rows2 = (long long)X * ap;
-    const int nkp = (int)((rows2 / 16 + kPartAtoms - 1) / kPartAtoms);  // parts of GEMM3's K = (P, r)
-    const int kat3 = nkp * kPartAtoms;
+    const int patoms = digit_scale_part_atoms(nd);  // atoms per part of GEMM3's per-part scales
+    const int nkp = (int)((rows2 / 16 + patoms - 1) / patoms);  // parts of GEMM3's K = (P, r)
+    const int kat3 = nkp * patoms;
+    f->patoms = patoms;
     f->nkp = nkp;
     // N-side operands (C digits, W digits) hold whole tiles of every candidate width BN
     long long npad = ap;
@@ -528,7 +542,7 @@ int fast_prepare(nof_ctx* c) {
             // half a wave of tiles (longer chunks mean fewer partials and less per-tile overhead)
             const long long tmn = (long long)((n + 127) / 128) * ((a + bns[i] - 1) / bns[i]);
             int all[24], na2 = 0;
-            for (long long ch = kPartAtoms; na2 < 24; ch *= 2) {
+            for (long long ch = patoms; na2 < 24; ch *= 2) {
                 all[na2++] = (int)(ch < kat3 ? ch : kat3);
                 if (ch >= kat3) break;
             }
@@ -554,6 +568,7 @@ int fast_prepare(nof_ctx* c) {
         NOF_TRY(falloc(&f->Lpart, (size_t)(maxch * na)));
         DigitGemmOut o;
         o.outd = f->Lpart; o.ldo = a; o.chunk_stride = na; o.epA = f->epT; o.epB = f->epW;
+        o.part_atoms = patoms;
         o.tile_counter = f->tctr + 2;
         for (int i = 0; i < k; ++i)
             NOF_TRY(digit_gemm_plan(&cand[i], f->Td3, f->Wd3, n, a, bnk[i], nd, kat3, chk[i], 0, o, c->status));
@@ -633,8 +648,11 @@ int jk_from_b(nof_ctx* c, cudaStream_t s) {
 // Digits of T for the Lagrangian contraction (GEMM3's M side), on stream s.
 int t3_digits(nof_ctx* c, cudaStream_t s) {
     FastState* f = c->fast;
-    k_T3_digits<<<dim3(f->nkp, (f->n + 7) / 8), 128, 0, s>>>(f->Tdf, f->X, f->n, f->ap, f->nkp, f->nd, f->Td3,
-                                                             f->epT);
+    const dim3 grid(f->nkp, (f->n + 7) / 8);
+    if (f->patoms == 16)
+        k_T3_digits<16><<<grid, 256, 0, s>>>(f->Tdf, f->X, f->n, f->ap, f->nkp, f->nd, f->Td3, f->epT);
+    else
+        k_T3_digits<8><<<grid, 128, 0, s>>>(f->Tdf, f->X, f->n, f->ap, f->nkp, f->nd, f->Td3, f->epT);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
@@ -647,8 +665,11 @@ int w_digits(nof_ctx* c) {
     cudaStream_t st = c->stream;
     k_D_df<<<dim3((a + 15) / 16, (X + 15) / 16), 256, 0, st>>>(f->Adf, f->bdf, X, a, ap, f->Ddf);
     NOF_LAUNCH_CHECK();
-    k_W_digits<<<dim3(f->nkp, (a + 7) / 8), 128, 0, st>>>(f->bdf, f->Bcdf, f->Ddf, X, a, ap, f->nkp, f->nd, f->bn3,
-                                                          f->Wd3, f->epW);
+    const dim3 grid(f->nkp, (a + 7) / 8);
+    if (f->patoms == 16)
+        k_W_digits<16><<<grid, 256, 0, st>>>(f->bdf, f->Bcdf, f->Ddf, X, a, ap, f->nkp, f->nd, f->bn3, f->Wd3, f->epW);
+    else
+        k_W_digits<8><<<grid, 128, 0, st>>>(f->bdf, f->Bcdf, f->Ddf, X, a, ap, f->nkp, f->nd, f->bn3, f->Wd3, f->epW);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
