@@ -84,6 +84,45 @@ def overlap(basis, xyz):
     return S
 
 
+def kinetic(basis, xyz):
+    """T alone (the second matrix of one_electron): T_ab = mu (3 - 2 mu |AB|^2) S_ab per primitive
+    pair, mu = ab/p."""
+    fi, cen, ex, co = _prim_table(basis, xyz)
+    n = nbf(basis, xyz)
+    a = ex[:, None]
+    b = ex[None, :]
+    p = a + b
+    mu = a * b / p
+    AB2 = np.sum((cen[:, None, :] - cen[None, :, :]) ** 2, axis=-1)
+    Tp = mu * (3.0 - 2.0 * mu * AB2) * (np.pi / p) ** 1.5 * np.exp(-mu * AB2)
+    T = np.zeros((n, n))
+    np.add.at(T, (fi[:, None], fi[None, :]), co[:, None] * co[None, :] * Tp)
+    return T
+
+
+def nuclear_attraction(basis, xyz, Z=None, centres=None):
+    """The nuclear-attraction part of one_electron's V from the nuclei listed in `centres` only
+    (all by default): V_ab = -sum_C Z_C (2 pi / p) K_AB F0(p |PC|^2) per primitive pair. Summed over
+    a partition of the nuclei it gives V (the sum over C split into slices)."""
+    natom = xyz.shape[0]
+    Z = np.ones(natom) if Z is None else np.asarray(Z, np.float64)
+    centres = range(natom) if centres is None else centres
+    fi, cen, ex, co = _prim_table(basis, xyz)
+    n = nbf(basis, xyz)
+    a = ex[:, None]
+    b = ex[None, :]
+    p = a + b
+    Kab = np.exp(-a * b / p * np.sum((cen[:, None, :] - cen[None, :, :]) ** 2, axis=-1))
+    Pc = (a[..., None] * cen[:, None, :] + b[..., None] * cen[None, :, :]) / p[..., None]
+    Vp = np.zeros_like(Kab)
+    for C in centres:
+        PC2 = np.sum((Pc - xyz[C]) ** 2, axis=-1)
+        Vp += -Z[C] * (2.0 * np.pi / p) * Kab * boys_f0(p * PC2)
+    V = np.zeros((n, n))
+    np.add.at(V, (fi[:, None], fi[None, :]), co[:, None] * co[None, :] * Vp)
+    return V
+
+
 def one_electron(basis, xyz, Z=None):
     """S, T and V (nuclear attraction of all nuclei) as n x n FP64 matrices."""
     natom = xyz.shape[0]

@@ -14,6 +14,9 @@ Only the order of work differs, so that memory stays O(X n a) instead of O(X n^2
   lambda_{qp} = n_p h_{qp} + sum_P b^P_{qp} D^P_p - sum_{P, r} b^P_{qr} B_{pr} b^P_{rp},
   with h_{qp} = (C^T H C)_{qp}, d^P_p = b^P_{pp}, D^P = A d^P.
 
+The *_blocked / *_inplace variants compute the same quantities with the aux index taken a block at a
+time, so that the only array of size X n a is b itself (the H1000 chain: 24 GB in FP64).
+
 Parity: pinned against pnof.energy_and_gradients (itself pinned to closed forms, brute force and
 finite differences) on small systems in tests/test_oracle_large.py.
 """
@@ -57,5 +60,46 @@ def energy_and_gradients_mo(bfull, H, C, gamma, pm: pnof.PairMap, vnn: float, ip
     # sum_{P, r} b^P_{qr} (B_{pr} b^P_{rp}): one (n x a)(a x a) product per P
     Wt = Bc.T[None, :, :] * b                       # [P][r][p] = B_pr b^P_rp
     lam[:, :a] -= np.matmul(bfull, Wt).sum(axis=0)
+    return dict(E=E, J=J, K=K, hpp=hpp, lam=lam, g=pnof.orbital_gradient(lam),
+                g_gamma=pnof.gamma_gradient(hpp, J, K, gamma, pm, ipnof))
+
+
+def fit_inplace(Q3, V, cols: int = 1 << 18):
+    """b^P_{qp} = sum_Q (V^{-1/2})_{PQ} (Q|q p) written over the stacked (Q|q p) [X][n][nact],
+    a block of `cols` (q, p) columns at a time."""
+    X = Q3.shape[0]
+    flat = Q3.reshape(X, -1)
+    W = ri.inverse_sqrt_metric(V)
+    for c0 in range(0, flat.shape[1], cols):
+        flat[:, c0:c0 + cols] = W @ flat[:, c0:c0 + cols]
+    return Q3
+
+
+def energy_and_gradients_mo_blocked(bfull, H, C, gamma, pm: pnof.PairMap, vnn: float, ipnof: int = 7,
+                                    block: int = 32):
+    """energy_and_gradients_mo with every sum over the aux index P taken `block` aux functions at a
+    time (same definitions; only the order of the P sum differs)."""
+    a = pm.nact
+    n_bf = C.shape[0]
+    X = bfull.shape[0]
+    d = np.stack([np.diagonal(bfull[P, :a, :]) for P in range(X)])  # d^P_p = b^P_pp  [X][a]
+    J = d.T @ d
+    K = np.zeros((a, a))
+    for P0 in range(0, X, block):
+        b = bfull[P0:P0 + block, :a, :]
+        K += np.einsum("Ppq,Ppq->pq", b, b)
+    hmo = C.T @ H @ C[:, :a]
+    hpp = np.diag(hmo[:a, :]).copy()
+    E = pnof.energy_from_jk(hpp, J, K, gamma, pm, vnn, ipnof)
+    A, Bc = pnof.coefficients(gamma, pm, ipnof)
+    nocc = pnof.occupation_numbers(gamma, pm)
+    D = d @ A.T
+    lam = np.zeros((n_bf, n_bf))
+    lam[:, :a] = hmo * nocc[None, :]
+    for P0 in range(0, X, block):
+        bf = bfull[P0:P0 + block]
+        lam[:, :a] += np.einsum("Pqp,Pp->qp", bf, D[P0:P0 + block])
+        Wt = Bc.T[None, :, :] * bf[:, :a, :]       # [P][r][p] = B_pr b^P_rp
+        lam[:, :a] -= np.matmul(bf, Wt).sum(axis=0)
     return dict(E=E, J=J, K=K, hpp=hpp, lam=lam, g=pnof.orbital_gradient(lam),
                 g_gamma=pnof.gamma_gradient(hpp, J, K, gamma, pm, ipnof))

@@ -19,24 +19,44 @@ def _slice(args):
 
 
 def fitted_mo(orb, aux, xyz, C, nact, workers=None):
-    """b^P_{qp} [X][n][nact] of the oracle, (P|q p) computed in parallel slices."""
+    """b^P_{qp} [X][n][nact] of the oracle, (P|q p) computed in parallel slices, written into one
+    preallocated array and fitted in place (one array of X n nact doubles)."""
     X = integrals.naux(aux, xyz)
+    n = C.shape[0]
     workers = workers or max(1, min(16, os.cpu_count() or 1))
     step = max(1, -(-X // (4 * workers)))
     jobs = [(orb, aux, xyz, C, nact, lo, min(X, lo + step)) for lo in range(0, X, step)]
+    Q3 = np.empty((X, n, nact))
     saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
     for k in saved:
         os.environ[k] = "1"
     try:
         with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
-            Q3 = np.concatenate(list(ex.map(_slice, jobs)))
+            for (_, _, _, _, _, lo, hi), part in zip(jobs, ex.map(_slice, jobs)):
+                Q3[lo:hi] = part
     finally:
         for k, v in saved.items():
             if v is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    return large.fitted_mo(Q3, integrals.two_center(aux, xyz))
+    return large.fit_inplace(Q3, integrals.two_center(aux, xyz))
+
+
+def _nuclear_slice(args):
+    orb, xyz, lo, hi = args
+    return integrals.nuclear_attraction(orb, xyz, None, range(lo, hi))
+
+
+def core_hamiltonian(orb, xyz, workers=None):
+    """S and H = T + V of the oracle, V summed over slices of nuclei computed in parallel."""
+    natom = xyz.shape[0]
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    step = max(1, -(-natom // workers))
+    jobs = [(orb, xyz, lo, min(natom, lo + step)) for lo in range(0, natom, step)]
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        V = sum(ex.map(_nuclear_slice, jobs))
+    return integrals.overlap(orb, xyz), integrals.kinetic(orb, xyz) + V
 
 
 def _slice_cols(args):

@@ -1,16 +1,26 @@
 """The H1000 chain (spacing 1.8 bohr, 1 contracted s + 3 aux s per H: nbf 1000, naux 3000,
-nact 1000) on the split path, checked by properties that hold at any size (the oracle's
-integrals are too slow at this size): the invariants of J and K, and the orbital and occupation
-gradients against fourth-order finite differences of the energy. The orbitals are the oracle's
-Loewdin orbitals of its overlap matrix."""
+nact 1000) on the split path through the C ABI:
+
+* against the oracle's orbital-basis route (oracle/large.py, P-blocked, pinned to the plain route):
+  E, J, K, the orbital gradient and the occupation gradient element by element at 1e-6. The
+  oracle's integrals run in spawned worker processes (nuclear attraction over slices of nuclei,
+  three-centre integrals over slices of aux functions); its fitted tensor in the orbital basis
+  is one array of 24 GB on the host;
+* properties that hold at any size: the invariants of J and K, and the gradients against
+  fourth-order finite differences of the split path's own energy.
+
+The orbitals are the oracle's Loewdin orbitals of its overlap matrix."""
 import numpy as np
 import pytest
 
-from oracle import integrals, reference
+import oracle_pool
+from oracle import integrals, large, pnof, reference
 from paper_2512_13550_gb300 import inputs
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+GATE = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -22,16 +32,37 @@ def h1000():
     C = reference.orthonormal_orbitals(S, inputs.random_orthogonal(S.shape[0], 0))
     ctx = nof.Context(precision=nof.PREC_SPLIT_BF16)
     ctx.build_B(xyz, orb, aux)
-    return dict(ctx=ctx, C=C, n=S.shape[0])
+    yield dict(ctx=ctx, C=C, n=S.shape[0], orb=orb, aux=aux, xyz=xyz)
+    ctx.close()
 
 
 def _t(x):
     return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
 
+def test_h1000_matches_oracle(h1000):
+    ctx, C = h1000["ctx"], h1000["C"]
+    s = ctx.sizes
+    assert (s["nbf"], s["naux"], s["nact"], ctx.split_digits()) == (1000, 3000, 1000, 5)
+    gam = inputs.random_gamma(s["ngamma"], 1)
+    J, K = ctx.jk(_t(C))
+    E, g, gg = ctx.energy_grad(_t(C), _t(gam))
+    torch.cuda.synchronize()
+    got = dict(E=E.item(), J=J.cpu().numpy(), K=K.cpu().numpy(), g=g.cpu().numpy(), g_gamma=gg.cpu().numpy())
+    orb, aux, xyz = h1000["orb"], h1000["aux"], h1000["xyz"]
+    S, H = oracle_pool.core_hamiltonian(orb, xyz)
+    pm = pnof.PairMap(1000, 1, s["nbf"])
+    bfull = oracle_pool.fitted_mo(orb, aux, xyz, C, pm.nact)
+    ref = large.energy_and_gradients_mo_blocked(bfull, H, C, gam, pm, integrals.nuclear_repulsion(xyz))
+    del bfull
+    dev = {key: float(np.max(np.abs(np.asarray(got[key]) - ref[key]))) for key in ("E", "J", "K", "g", "g_gamma")}
+    print("H1000 split path vs oracle, max |difference|:", dev)
+    for key, d in dev.items():
+        assert d < GATE, key
+
+
 def test_h1000_jk_invariants(h1000):
     ctx = h1000["ctx"]
-    assert (ctx.sizes["nbf"], ctx.sizes["naux"], ctx.sizes["nact"]) == (1000, 3000, 1000)
     J, K = ctx.jk(_t(h1000["C"]))
     torch.cuda.synchronize()
     J, K = J.cpu().numpy(), K.cpu().numpy()

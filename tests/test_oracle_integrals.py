@@ -146,3 +146,18 @@ def test_ri_ill_conditioned_metric_is_refused():
 def test_overlap_alone_equals_one_electron_overlap():
     for orb, xyz in [(inputs.basis_h4()[0], inputs.chain(4, 1.8)), (inputs.basis_3s_10aux()[0], inputs.chain(6, 1.8))]:
         np.testing.assert_allclose(integrals.overlap(orb, xyz), integrals.one_electron(orb, xyz)[0], atol=1e-15)
+
+
+def test_separate_one_electron_matrices_equal_one_electron():
+    """overlap, kinetic and nuclear_attraction (summed over a partition of the nuclei) equal the
+    matrices of one_electron, on a non-collinear geometry with a nuclear charge of 2."""
+    from paper_2512_13550_gb300 import inputs
+    orb, _ = inputs.basis_3s_10aux()
+    xyz = np.array([[0.0, 0.0, 0.0], [1.4, 0.2, 0.0], [0.3, 1.7, 0.4], [2.1, 1.5, -0.6], [-1.2, 0.4, 0.9]])
+    Z = np.array([1.0, 2.0, 1.0, 1.0, 1.0])
+    S, T, V = integrals.one_electron(orb, xyz, Z)
+    np.testing.assert_allclose(integrals.overlap(orb, xyz), S, atol=1e-14, rtol=0)
+    np.testing.assert_allclose(integrals.kinetic(orb, xyz), T, atol=1e-13, rtol=0)
+    parts = [integrals.nuclear_attraction(orb, xyz, Z, c) for c in ([0, 1], [2], [3, 4])]
+    np.testing.assert_allclose(sum(parts), V, atol=1e-12, rtol=0)
+    np.testing.assert_allclose(integrals.nuclear_attraction(orb, xyz, Z), V, atol=1e-13, rtol=0)
