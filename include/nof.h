@@ -170,6 +170,59 @@ int nof_energy_grad(nof_ctx* ctx, const double* C, const double* gamma, double* 
  * ||y||_F > 4096 is reported by nof_sync as NOF_ENOTCONV. */
 int nof_step(nof_ctx* ctx, double* C, double* gamma, double* m, double* v, int* t, double* out);
 
+/* ---- Converged optimisation loop --------------------------------------------------------- */
+
+/* Parameters of nof_optimize (defaults from nof_default_opt_params). */
+typedef struct {
+    int maxit;        /* outer iterations at most (default 1000) */
+    int maxloop;      /* ADAM orbital steps per outer iteration (default 10) */
+    double gtol;      /* stop when ||g||_F < gtol ... (default 1e-5) */
+    double etol;      /* ... and |E_k - E_{k-1}| < etol (default 1e-8 Ha) */
+    double lr;        /* initial ADAM rate (default 0.02) */
+    double lr_min;    /* also stop once the rate falls below this (default 1e-12) */
+    double on_tol;    /* ON optimisation: max |dE/dgamma| at convergence (default 1e-8) */
+    int on_maxit;     /* ON optimisation: BFGS steps at most per outer iteration (default 500) */
+    double eps_rel;   /* ADAM's epsilon in a block is max(the context's eps, eps_rel ||g_k||_F) (default 0) */
+    double lr_grow;   /* the rate is multiplied by this (>= 1) after a block that found better orbitals
+                         (default 1) */
+    int orbopt;       /* orbital steps: 0 ADAM blocks only; 1 L-BFGS only; 2 (default) ADAM blocks until
+                         the rate falls below lr * lbfgs_after, then L-BFGS steps */
+    int memory;       /* L-BFGS pairs kept (1..64, default 20) */
+    double lbfgs_after; /* see orbopt (default 1/64) */
+} nof_opt_params;
+
+void nof_default_opt_params(nof_opt_params* p);
+
+/* The converged ON / NO optimisation: the paper optimises the ONs and the orbitals separately
+ * (Theory section, after Eq. sum1), the orbitals by rotations with ADAM on g = 4(lambda - lambda^T)
+ * (Natural Orbital Optimization subsection), until the lambda-symmetry and energy thresholds hold
+ * (NTHRESHL / NTHRESHE, Single Point Energy section). The ADAM details are delegated by the paper;
+ * this loop is the reading the oracle implements. Outer iteration k:
+ *   1. J, K, h_pp at C_k; the ONs converged at fixed J, K: BFGS on gamma with an Armijo step
+ *      control to max |dE/dgamma| < on_tol (one CUDA block);
+ *   2. E_k, lambda, g_k at (C_k, gamma_k); stop when ||g_k||_F < gtol and |E_k - E_{k-1}| < etol;
+ *   3. maxloop ADAM steps on the orbitals from zero moments (the context's b1, b2, eps) with
+ *      gamma_k fixed, each a full evaluation; the best orbitals (energy lower by more than etol,
+ *      or equal within etol with ||g|| at most 0.9 of the best) become C_{k+1}; if no step is
+ *      better than (E_k, ||g_k||) the rate halves, and the loop ends once the rate is below
+ *      lr_min. With orbopt 2, once the rate is below lr * lbfgs_after (ADAM's normalised steps
+ *      then make little progress), every outer iteration takes instead one L-BFGS step on the
+ *      rotation generators (two-loop recursion over the last `memory` pairs, <A,B> = sum_{p<q}
+ *      A_pq B_pq; step length halved from 1 until an Armijo decrease, or, where the predicted
+ *      decrease is below etol, a smaller ||g|| with the energy within etol; a failed search
+ *      retries from steepest descent, then halves the rate). orbopt 1 takes L-BFGS steps from
+ *      the start (the first one -g lr / max|g|).
+ * C (device, nbf x nbf) and gamma (device, ngamma) are the start and receive the final state.
+ * history: host [maxit][3] of (E_k, ||g_k||_F, lr_k) per outer iteration, or NULL.
+ * result: host [8]: final E, ||g||_F, max |lambda - lambda^T|, outer iterations, evaluations,
+ * converged (1 or 0), final rate, total ON (BFGS) steps. Synchronises the context's stream after
+ * every evaluation (three doubles read back). Workspaces (6 nbf^2 + ngamma^2 + 6 ngamma doubles)
+ * are allocated on the first call and freed with the context. Errors: NOF_EINVAL (null pointer,
+ * bad parameter), NOF_ESTATE, NOF_ENOMEM, NOF_ENONFINITE (a NaN or Inf energy or gradient; the
+ * device status word is cleared, since the return value reports it). */
+int nof_optimize(nof_ctx* ctx, double* C, double* gamma, const nof_opt_params* params, double* history,
+                 double* result);
+
 /* Batched evaluation (the batching of many geometries): `count` independent contexts, each built
  * with its own geometry and created on its own stream, evaluate nof_energy_grad concurrently.
  * The call forks from `stream` (a cudaStream_t) onto every context's stream with events and joins
@@ -306,6 +359,15 @@ int nof_selftest_digit_gemm(int M, int N, int bn, int nd, int katoms, int chunk_
  * its own buffers (the flush buffer is kept for the life of the process). */
 int nof_bench_digit_gemm(int M, int N, int bn, int nd, int katoms, int chunk_atoms, int mode, int reps,
                          double* us_per_launch);
+
+/* Failure detection of the digit GEMM (no paper counterpart): one launch of the M x N x 16 katoms
+ * product whose producer issues no copies, so that its consumers' bounded waits run out. Every
+ * mbarrier wait of the kernel is bounded by limit_ms (0 < limit_ms <= 1000); on a timeout the
+ * kernel sets its status word and returns, and nothing it issued is left in flight. Returns
+ * NOF_ETIMEOUT when the kernel reported the timeout (the expected outcome), with the launch's
+ * device time in *elapsed_ms (host). Allocates and frees its own buffers; synchronises. */
+int nof_selftest_digit_gemm_timeout(int M, int N, int bn, int nd, int katoms, double limit_ms,
+                                    double* elapsed_ms);
 
 /* J and K exactly as nof_jk computes them in FP64, without a context and without allocating
  * any device memory (the paper has no counterpart; this is a deployment variant).

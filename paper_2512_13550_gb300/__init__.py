@@ -42,6 +42,14 @@ class Options(ctypes.Structure):
                 ("eps", ctypes.c_double), ("digits", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
+class OptParams(ctypes.Structure):
+    _fields_ = [("maxit", ctypes.c_int), ("maxloop", ctypes.c_int), ("gtol", ctypes.c_double),
+                ("etol", ctypes.c_double), ("lr", ctypes.c_double), ("lr_min", ctypes.c_double),
+                ("on_tol", ctypes.c_double), ("on_maxit", ctypes.c_int), ("eps_rel", ctypes.c_double),
+                ("lr_grow", ctypes.c_double), ("orbopt", ctypes.c_int), ("memory", ctypes.c_int),
+                ("lbfgs_after", ctypes.c_double)]
+
+
 class CBasis(ctypes.Structure):
     _fields_ = [("nshell", ctypes.c_int), ("nprim", ctypes.POINTER(ctypes.c_int)),
                 ("exps", ctypes.POINTER(ctypes.c_double)), ("coefs", ctypes.POINTER(ctypes.c_double))]
@@ -68,6 +76,8 @@ SIGNATURES = {
     "nof_energy_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "nof_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "nof_sync": (ctypes.c_int, [_P]),
+    "nof_default_opt_params": (None, [ctypes.POINTER(OptParams)]),
+    "nof_optimize": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(OptParams), _P, _P]),
     "nof_energy_grad_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P]),
     "nof_kernel_launches": (ctypes.c_longlong, []),
     "nof_profile": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -75,6 +85,7 @@ SIGNATURES = {
     "nof_selftest_digit_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_uint, _P]),
     "nof_bench_digit_gemm": (ctypes.c_int, [ctypes.c_int] * 8 + [_P]),
+    "nof_selftest_digit_gemm_timeout": (ctypes.c_int, [ctypes.c_int] * 5 + [ctypes.c_double, _P]),
     "nof_jk_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]),
     "nof_mlp_param_count": (ctypes.c_longlong, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "nof_mlp_work_size": (ctypes.c_longlong, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -335,6 +346,27 @@ class Context:
         _check(load_library().nof_step(self._h, _dptr(C), _dptr(gamma), _dptr(m), _dptr(v),
                                        None if device_counter else ctypes.byref(self.t), _dptr(out)))
         return out
+
+    def optimize(self, C, gamma, **params):
+        """The converged ON / NO loop (nof_optimize) from (C, gamma), in place. params: fields of
+        nof_opt_params. Returns dict(E, gnorm, lam_asym, iterations, evaluations, converged, lr,
+        on_steps, history [iterations][3] of (E_k, ||g_k||, lr_k))."""
+        lib = load_library()
+        p = OptParams()
+        lib.nof_default_opt_params(ctypes.byref(p))
+        known = {name for name, _ in OptParams._fields_}
+        for k, v in params.items():
+            if k not in known:
+                raise ValueError(f"unknown parameter {k!r}; the parameters are {sorted(known)}")
+            setattr(p, k, v)
+        hist = np.zeros((p.maxit, 3))
+        res = np.zeros(8)
+        _check(lib.nof_optimize(self._h, _dptr(C), _dptr(gamma), ctypes.byref(p),
+                                hist.ctypes.data_as(ctypes.c_void_p), res.ctypes.data_as(ctypes.c_void_p)))
+        it = int(res[3])
+        return dict(E=float(res[0]), gnorm=float(res[1]), lam_asym=float(res[2]), iterations=it,
+                    evaluations=int(res[4]), converged=bool(res[5]), lr=float(res[6]), on_steps=int(res[7]),
+                    history=hist[:it].copy())
 
     def nuclear_gradient(self, C, gamma, grad=None):
         """dE/dR [natom][3] at (C, gamma) along the orbital connection (nof_nuclear_gradient)."""

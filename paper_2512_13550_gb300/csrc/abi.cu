@@ -109,6 +109,8 @@ void free_system(nof_ctx* c) {
     dfree(c->y); dfree(c->U); dfree(c->U2); dfree(c->tmpn); dfree(c->gwork);
     dfree(c->Dip); dfree(c->H0); dfree(c->vnn0); dfree(c->dipw); dfree(c->tdev);
     dfree(c->Linv); dfree(c->gr_cfit); dfree(c->gr_Y); dfree(c->gr_Gam); dfree(c->gr_Z); dfree(c->gr_small);
+    dfree(c->opt_buf);
+    c->opt_cap = 0;
     c->built = 0;
 }
 

@@ -45,7 +45,7 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kStageAtoms = 2;
-constexpr unsigned long long kTimeoutNs = 4000000000ull;  // 4 s per wait
+constexpr unsigned long long kTimeoutNs = 4000000000ull;  // default limit of one wait: 4 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -71,14 +71,14 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t phase) {
     return ok != 0;
 }
 // Bounded wait: false (and NOF_DEV_TIMEOUT set) if the phase did not complete in time.
-__device__ bool mbar_wait(uint32_t a, uint32_t phase, int* status) {
+__device__ bool mbar_wait(uint32_t a, uint32_t phase, int* status, unsigned long long limit_ns) {
     unsigned long long t0 = 0;
     for (uint32_t it = 0;; ++it) {
         if (mbar_try(a, phase)) return true;
         if ((it & 1023u) == 0u) {
             unsigned long long t = globaltimer();
             if (t0 == 0) t0 = t;
-            else if (t - t0 > kTimeoutNs) {
+            else if (t - t0 > limit_ns) {
                 atomicOr(status, NOF_DEV_TIMEOUT);
                 return false;
             }
@@ -261,7 +261,7 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
         const int slot = qi % kTileQ;
         int t = ntiles, okl = 1;
         if (lane == 0) {
-            okl = mbar_wait(qfull0 + 8 * slot, (qi / kTileQ) & 1, g.status) ? 1 : 0;
+            okl = mbar_wait(qfull0 + 8 * slot, (qi / kTileQ) & 1, g.status, g.timeout_ns) ? 1 : 0;
             if (okl) {
                 t = tq_id[slot];
                 mbar_arrive(qempty0 + 8 * slot);
@@ -292,7 +292,7 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
             for (int qi = 0; ok; ++qi) {
                 if (dyn) {  // hand the tile index to the MMA and epilogue warps
                     const int slot = qi % kTileQ;
-                    if (qi >= kTileQ) ok = mbar_wait(qempty0 + 8 * slot, ((qi / kTileQ) - 1) & 1, g.status);
+                    if (qi >= kTileQ) ok = mbar_wait(qempty0 + 8 * slot, ((qi / kTileQ) - 1) & 1, g.status, g.timeout_ns);
                     if (!ok) break;
                     tq_id[slot] = tile;
                     mbar_arrive(qfull0 + 8 * slot);
@@ -304,12 +304,13 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                 const int nst = (tk + kStageAtoms - 1) / kStageAtoms;
                 for (int st = 0; st < nst && ok; ++st, ++it) {
                     const int s = it % S;
-                    if (it >= S) ok = mbar_wait(empty0 + 8 * s, ((it / S) - 1) & 1, g.status);
+                    if (it >= S) ok = mbar_wait(empty0 + 8 * s, ((it / S) - 1) & 1, g.status, g.timeout_ns);
                     if (!ok) break;
                     const int ka = k0 + st * kStageAtoms;
                     const int atoms = min(kStageAtoms, tk - st * kStageAtoms);
                     const uint32_t abytes = (uint32_t)atoms * ND * kBM * 32u;
                     const uint32_t bbytes = (uint32_t)atoms * ND * (uint32_t)BN * 32u;
+                    if (g.no_copies) continue;  // failure-detection test: the stage never fills
                     mbar_expect_tx(full0 + 8 * s, abytes + bbytes);
                     // each operand's stage block is one contiguous run of bytes
                     bulk_load(smem_u32(sA + s * a_stage_bytes),
@@ -350,7 +351,7 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                 const int nparts = (tk + g.apart - 1) / g.apart;
                 for (int part = 0; part < nparts && ok; ++part, ++unit) {
                     const int b = unit % NB, use = unit / NB;
-                    if (use > 0) ok = mbar_wait(tempty0 + 8 * b, (use - 1) & 1, g.status);
+                    if (use > 0) ok = mbar_wait(tempty0 + 8 * b, (use - 1) & 1, g.status, g.timeout_ns);
                     if (!ok) break;
                     tc_fence_after();
                     uint32_t accl[ND];  // TMEM column of each level of this set
@@ -360,7 +361,7 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                     const int nst = (pa + kStageAtoms - 1) / kStageAtoms;
                     for (int st = 0; st < nst && ok; ++st, ++it) {
                         const int s = it % S;
-                        ok = mbar_wait(full0 + 8 * s, (it / S) & 1, g.status);
+                        ok = mbar_wait(full0 + 8 * s, (it / S) & 1, g.status, g.timeout_ns);
                         if (!ok) break;
                         tc_fence_after();
                         const int atoms = min(kStageAtoms, pa - st * kStageAtoms);
@@ -426,7 +427,7 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                 const int erp = (partsc && row < g.M) ? g.epA[gp * g.M + row] - kOff : er;
                 const int* ec = partsc ? g.epB + gp * g.Nvalid : g.ecol;
                 const int ecl = ints ? 0 : ec[min(col0 + lane, g.Nvalid - 1)];
-                ok = mbar_wait(tfull0 + 8 * b, use & 1, g.status);
+                ok = mbar_wait(tfull0 + 8 * b, use & 1, g.status, g.timeout_ns);
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t acc = tmem + lane_base + (uint32_t)(b * ND * BN);
@@ -631,6 +632,8 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
     g.colmax = o.colmax;
     g.group_rows = o.group_rows;
     g.status = status;
+    g.timeout_ns = kTimeoutNs;
+    g.no_copies = 0;
     g.stages = stages;
     g.tiles_m = (M + kBM - 1) / kBM;
     g.kchunks = (katoms_total + g.katoms - 1) / g.katoms;
@@ -987,5 +990,67 @@ extern "C" int nof_bench_digit_gemm(int M, int N, int bn, int nd, int katoms, in
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(A); cudaFree(B); cudaFree(out); cudaFree(erow); cudaFree(ecol); cudaFree(status); cudaFree(ctr);
+    return r;
+}
+
+// ---------------------------------------------------------------------------------------
+// Failure detection: a launch whose producer issues no copies, so that the MMA warp's wait for
+// its first stage, the producer's wait for a free slot and the epilogue's wait for an
+// accumulator all run out; every wait is bounded by `limit_ms`, after which the kernel sets
+// NOF_DEV_TIMEOUT and returns (nothing was issued, so nothing is in flight).
+// ---------------------------------------------------------------------------------------
+extern "C" int nof_selftest_digit_gemm_timeout(int M, int N, int bn, int nd, int katoms, double limit_ms,
+                                               double* elapsed_ms) {
+    if (!elapsed_ms || M <= 0 || N <= 0 || (nd != 4 && nd != 5) || !digit_bn_ok(bn, nd) || katoms <= 0 ||
+        !(limit_ms > 0.0) || limit_ms > 1000.0) {
+        nof_set_error("nof_selftest_digit_gemm_timeout: bad arguments (limit 0 < limit_ms <= 1000)");
+        return NOF_EINVAL;
+    }
+    const long long na = digit_elems(128, M, katoms, nd), nb = digit_elems(bn, N, katoms, nd);
+    uint16_t *A = nullptr, *B = nullptr;
+    long long* C1 = nullptr;
+    int* status = nullptr;
+    int r = NOF_OK;
+    auto fail = [&](cudaError_t e, const char* w) { r = nof_cuda_fail(e, w, __FILE__, __LINE__); };
+    cudaError_t e;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaMalloc(&A, 2ull * na)) != cudaSuccess) fail(e, "malloc A");
+    if (r == NOF_OK && (e = cudaMalloc(&B, 2ull * nb)) != cudaSuccess) fail(e, "malloc B");
+    if (r == NOF_OK && (e = cudaMalloc(&C1, 8ull * M * N)) != cudaSuccess) fail(e, "malloc C");
+    if (r == NOF_OK && (e = cudaMalloc(&status, 4)) != cudaSuccess) fail(e, "malloc status");
+    if (r == NOF_OK) {
+        cudaMemset(A, 0, 2ull * na);
+        cudaMemset(B, 0, 2ull * nb);
+        cudaMemset(status, 0, 4);
+        DigitGemmOut o;
+        o.out = C1;
+        o.ldo = N;
+        DigitGemmPlan p;
+        r = digit_gemm_plan(&p, A, B, M, N, bn, nd, katoms, katoms, 0, o, status);
+        if (r == NOF_OK) {
+            p.g.timeout_ns = (unsigned long long)(limit_ms * 1e6);
+            p.g.no_copies = 1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, 0);
+            r = digit_gemm_run(p, 0);
+            cudaEventRecord(e1, 0);
+            if (r == NOF_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) fail(e, "event sync");
+            float ms = 0.f;
+            if (r == NOF_OK) cudaEventElapsedTime(&ms, e0, e1);
+            *elapsed_ms = ms;
+        }
+    }
+    if (r == NOF_OK) {
+        int hs = 0;
+        if ((e = cudaMemcpy(&hs, status, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) fail(e, "copy status");
+        else if (hs & NOF_DEV_TIMEOUT) {
+            nof_set_error("digit GEMM: a bounded wait timed out (producer issued no copies)");
+            r = NOF_ETIMEOUT;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(A); cudaFree(B); cudaFree(C1); cudaFree(status);
     return r;
 }

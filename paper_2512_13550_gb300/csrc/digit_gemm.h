@@ -47,6 +47,8 @@ struct DigitGemmArgs {
     unsigned* colmax;
     int group_rows;
     int* status;       // device status word (NOF_DEV_TIMEOUT on a timed-out wait)
+    unsigned long long timeout_ns;  // limit of every mbarrier wait (%globaltimer ns; 4 s by default)
+    int no_copies;     // failure-detection test only: the producer issues no copies, so waits run out
     int stages;        // shared-memory ring slots (each 2 K atoms of A and B, nd planes)
     int nbuf;          // TMEM accumulator sets
     int tiles_m;       // 128-row blocks

@@ -92,6 +92,9 @@ struct nof_ctx {
     double *Dip, *H0, *vnn0, *dipw;
     // ADAM step counter on the device for nof_step with t == NULL (zero after nof_build_B)
     int* tdev;
+    // converged loop (nof_optimize): one allocation made on its first call, freed by nof_destroy
+    double* opt_buf;
+    size_t opt_cap;
     // nuclear gradient (FP64 path): L^-1 of the Coulomb metric kept from set-up, and workspaces
     // allocated on the first nof_nuclear_gradient
     double *Linv, *gr_cfit, *gr_Y, *gr_Gam, *gr_Z, *gr_small;
@@ -168,6 +171,9 @@ int pnof_lambda_and_g(nof_ctx* c, const double* C, double* g_out, bool assembled
 int pnof_jk_from_b(nof_ctx* c);
 int pnof_build_W(nof_ctx* c);
 int pnof_on_update(nof_ctx* c, double* gamma);
+int pnof_on_converge(nof_ctx* c, double* gamma, double tol, int maxit, double lr0, double* w, double* info);
+int pnof_adam_y(nof_ctx* c, const double* g, double* m, double* v, double* y, int t, double lr, double eps);
+int pnof_step_stats(nof_ctx* c, const double* g, double* out);
 int pnof_adam_rotate(nof_ctx* c, double* C, double* m, double* v, int* t, double* out);
 
 // Split-precision path (fast.cu)

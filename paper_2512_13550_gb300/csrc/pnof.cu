@@ -299,12 +299,16 @@ __device__ double gamma_chain_one(int k, const double* s, const double* t, const
 
 __global__ void k_gamma_chain(const double* s, const double* t, const double* ds, const double* dt,
                               const int* slot, const double* parts, int npair, int ncwo, int a,
-                              const double* vnn, double* E, double* out) {
+                              const double* vnn, double* E, double* out, int* status) {
     if (blockIdx.x == 0 && threadIdx.x < 32) {
         double e = 0.0;
         for (int p = threadIdx.x; p < a; p += 32) e += parts[3 * a + p];
         for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        if (threadIdx.x == 0) *E = e + *vnn;
+        if (threadIdx.x == 0) {
+            *E = e + *vnn;
+            // a NaN or Inf in C, gamma or any stage before reaches the energy: flag it for nof_sync
+            if (!isfinite(e)) atomicOr(status, NOF_DEV_NONFINITE);
+        }
     }
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= npair * ncwo) return;
@@ -340,6 +344,206 @@ __global__ void __launch_bounds__(1024) k_on_update_fused(double* gamma, int npa
         __syncthreads();
         for (int k = tid; k < ng; k += blockDim.x) gamma[k] -= lr * ggam[k];
         __syncthreads();
+    }
+}
+
+// ---- ONs converged at fixed J, K, h_pp (the converged loop's first step) ------------------------
+// Deterministic block reduction: every thread contributes its partial, shared memory sums them in a
+// fixed tree; the result is returned to every thread.
+__device__ double block_sum(double v, double* red) {
+    const int tid = threadIdx.x;
+    red[tid] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (tid < o) red[tid] += red[tid + o];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+__device__ double block_max(double v, double* red) {
+    const int tid = threadIdx.x;
+    red[tid] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (tid < o) red[tid] = fmax(red[tid], red[tid + o]);
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// Energy row and partial derivatives of orbital p (as dE_parts_warp) with A and B formed on the fly
+// from s = sqrt(n) and t = sqrt(1 - n) instead of read from the coefficient arrays.
+__device__ void on_parts_warp(int p, int lane, const double* s, const double* t, const int* pair, const int* slot,
+                              const double* hpp, const double* J, const double* K, int a, int ipnof, double* out) {
+    const double np = s[p] * s[p], cp = slot[p] == 0 ? s[p] : -s[p], fp = s[p] * t[p];
+    double sn = 0.0, sc = 0.0, sf = 0.0, se = 0.0;
+    for (int q = lane; q < a; q += 32) {
+        const long long pq = (long long)p * a + q;
+        const double Jpq = J[pq], Kpq = K[pq];
+        const double nq = s[q] * s[q];
+        if (q == p) {
+            se += np * Jpq;
+        } else if (pair[q] != pair[p]) {
+            const double fq = s[q] * t[q];
+            const double bv = np * nq + (ipnof == 7 ? fp * fq : 0.0);
+            se += 2.0 * np * nq * Jpq - bv * Kpq;
+            sn += nq * (2.0 * Jpq - Kpq);
+            sf += fq * Kpq;
+        } else {
+            const double cq = slot[q] == 0 ? s[q] : -s[q];
+            se += cp * cq * Kpq;
+            sc += cq * Kpq;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        sn += __shfl_xor_sync(0xffffffffu, sn, o);
+        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        sf += __shfl_xor_sync(0xffffffffu, sf, o);
+        se += __shfl_xor_sync(0xffffffffu, se, o);
+    }
+    if (lane == 0) {
+        out[p] = 2.0 * hpp[p] + J[(long long)p * a + p] + 2.0 * sn;
+        out[a + p] = 2.0 * sc;
+        out[2 * a + p] = (ipnof == 7) ? -2.0 * sf : 0.0;
+        out[3 * a + p] = 2.0 * np * hpp[p] + se;
+    }
+}
+
+// E(x) (without V_nn) and dE/dgamma at x into grad, by the whole block; returns E to every thread.
+__device__ double on_eval_block(const double* x, double* grad, int npair, int ncwo, int isoftmax, double* s,
+                                double* t, double* ds, double* dt, const int* pair, const int* slot, int a, int ipnof,
+                                const double* hpp, const double* J, const double* K, double* parts, double* red) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    for (int g = tid; g < npair; g += blockDim.x) {
+        if (isoftmax) occupations_softmax(g, x, npair, ncwo, s, t, ds, dt);
+        else occupations_trig(g, x, npair, ncwo, s, t, ds, dt);
+    }
+    __syncthreads();
+    for (int p = warp; p < a; p += nw) on_parts_warp(p, lane, s, t, pair, slot, hpp, J, K, a, ipnof, parts);
+    __syncthreads();
+    for (int k = tid; k < npair * ncwo; k += blockDim.x)
+        grad[k] = gamma_chain_one(k, s, t, ds, dt, slot, parts, npair, ncwo, a);
+    double e = 0.0;
+    for (int p = tid; p < a; p += blockDim.x) e += parts[3 * a + p];
+    return block_sum(e, red);  // its barriers also publish grad
+}
+
+// ONs optimised at fixed J, K, h_pp by BFGS with an Armijo step control, in one block (the
+// algorithm and its constants are the oracle's: see oracle/optimize.py, on_converge). gamma is
+// updated in place; w holds 6 ng + ng^2 doubles (trial point, gradients, s, y, H y, H);
+// info[0] = accepted steps, info[1] = max |dE/dgamma| at the end (doubles).
+__global__ void __launch_bounds__(1024) k_on_bfgs(double* gamma, int npair, int ncwo, int isoftmax, double* s,
+                                                 double* t, double* ds, double* dt, const int* pair, const int* slot,
+                                                 int a, int ipnof, const double* hpp, const double* J, const double* K,
+                                                 double* parts, double* w, double tol, int maxit, double lr0,
+                                                 double* info) {
+    __shared__ double red[1024];
+    __shared__ int hinit;
+    const int tid = threadIdx.x, ng = npair * ncwo;
+    double* xt = w;
+    double* gc = w + ng;
+    double* gt = w + 2 * ng;
+    double* sv = w + 3 * ng;
+    double* yv = w + 4 * ng;
+    double* d = w + 5 * ng;
+    double* Hinv = w + 6 * ng;
+    if (tid == 0) hinit = 0;
+    double E = on_eval_block(gamma, gc, npair, ncwo, isoftmax, s, t, ds, dt, pair, slot, a, ipnof, hpp, J, K,
+                             parts, red);
+    int it = 0;
+    double gmax = 0.0;
+    while (true) {
+        double m = 0.0;
+        for (int k = tid; k < ng; k += blockDim.x) m = fmax(m, fabs(gc[k]));
+        gmax = block_max(m, red);
+        if (!(gmax >= tol) || it >= maxit) break;  // also stops on a NaN gradient
+        // direction: -lr0 g before the first curvature pair, else -H g
+        const int hi = hinit;
+        for (int k = tid; k < ng; k += blockDim.x) {
+            double v;
+            if (!hi) {
+                v = -lr0 * gc[k];
+            } else {
+                v = 0.0;
+                for (int j = 0; j < ng; ++j) v -= Hinv[(long long)k * ng + j] * gc[j];
+            }
+            d[k] = v;
+        }
+        __syncthreads();
+        double part = 0.0;
+        for (int k = tid; k < ng; k += blockDim.x) part += d[k] * gc[k];
+        double dg = block_sum(part, red);
+        if (dg >= 0.0) {  // not a descent direction: restart from the gradient
+            if (tid == 0) hinit = 0;
+            for (int k = tid; k < ng; k += blockDim.x) d[k] = -lr0 * gc[k];
+            __syncthreads();
+            part = 0.0;
+            for (int k = tid; k < ng; k += blockDim.x) part += d[k] * gc[k];
+            dg = block_sum(part, red);
+        }
+        double alpha = 1.0, Et = 0.0;
+        bool failed = false;
+        while (true) {
+            for (int k = tid; k < ng; k += blockDim.x) xt[k] = gamma[k] + alpha * d[k];
+            __syncthreads();
+            Et = on_eval_block(xt, gt, npair, ncwo, isoftmax, s, t, ds, dt, pair, slot, a, ipnof, hpp, J, K, parts,
+                               red);
+            if (Et <= E + 1e-4 * alpha * dg || alpha * fabs(dg) < 1e-13 * fmax(1.0, fabs(E))) break;
+            alpha *= 0.5;
+            if (alpha < 1e-12) {
+                failed = true;
+                break;
+            }
+        }
+        if (failed) break;
+        // curvature pair and the BFGS update of H
+        double psy = 0.0, pyy = 0.0;
+        for (int k = tid; k < ng; k += blockDim.x) {
+            sv[k] = xt[k] - gamma[k];
+            yv[k] = gt[k] - gc[k];
+            psy += sv[k] * yv[k];
+            pyy += yv[k] * yv[k];
+        }
+        const double sy = block_sum(psy, red), yy = block_sum(pyy, red);
+        if (sy > 0.0) {
+            if (!hinit) {
+                for (long long i = tid; i < (long long)ng * ng; i += blockDim.x)
+                    Hinv[i] = (i / ng == i % ng) ? sy / yy : 0.0;
+                __syncthreads();
+                if (tid == 0) hinit = 1;
+            }
+            const double rho = 1.0 / sy;
+            // H y into d (the direction is no longer needed)
+            for (int k = tid; k < ng; k += blockDim.x) {
+                double v = 0.0;
+                for (int j = 0; j < ng; ++j) v += Hinv[(long long)k * ng + j] * yv[j];
+                d[k] = v;
+            }
+            __syncthreads();
+            part = 0.0;
+            for (int k = tid; k < ng; k += blockDim.x) part += yv[k] * d[k];
+            const double yHy = block_sum(part, red);
+            const double cs = rho * rho * yHy + rho;
+            for (long long i = tid; i < (long long)ng * ng; i += blockDim.x) {
+                const int k = (int)(i / ng), j = (int)(i % ng);
+                Hinv[i] += -rho * (sv[k] * d[j] + d[k] * sv[j]) + cs * sv[k] * sv[j];
+            }
+        }
+        for (int k = tid; k < ng; k += blockDim.x) {
+            gamma[k] = xt[k];
+            gc[k] = gt[k];
+        }
+        __syncthreads();
+        E = Et;
+        ++it;
+    }
+    if (tid == 0) {
+        info[0] = (double)it;
+        info[1] = gmax;
     }
 }
 
@@ -439,7 +643,7 @@ int pnof_gamma_grad(nof_ctx* c, double* out, cudaStream_t st) {
     NOF_LAUNCH_CHECK();
     k_gamma_chain<<<nblk(c->ngamma, 128), 128, 0, st>>>(c->s, c->t, c->ds, c->dt, c->slot,
                                                                 c->part, c->npair, c->opt.ncwo, a, c->vnn,
-                                                                c->E, out);
+                                                                c->E, out, c->status);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
@@ -578,6 +782,32 @@ int pnof_on_update(nof_ctx* c, double* gamma) {
         k_gamma_descent<<<nblk(c->ngamma, 128), 128, 0, st>>>(gamma, c->ggam, c->opt.on_lr, c->ngamma);
         NOF_LAUNCH_CHECK();
     }
+    return NOF_OK;
+}
+
+// ADAM moments and the rotation generator y from gradient g at step t (host counter, t >= 1).
+int pnof_adam_y(nof_ctx* c, const double* g, double* m, double* v, double* y, int t, double lr, double eps) {
+    const long long nn = (long long)c->nbf * c->nbf;
+    const double c1 = 1.0 - std::pow(c->opt.b1, t), c2 = 1.0 - std::pow(c->opt.b2, t);
+    k_adam<<<nblk(nn), 256, 0, c->stream>>>(g, m, v, y, nn, c->opt.b1, c->opt.b2, c1, c2, lr, eps, nullptr);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+// out[0] = E, out[1] = ||g||_F, out[2] = max |lambda - lambda^T| of the context's last evaluation.
+int pnof_step_stats(nof_ctx* c, const double* g, double* out) {
+    k_step_stats<<<1, 256, 0, c->stream>>>(c->E, g, c->lam, c->nbf, c->nact, out);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+// ONs converged at the J, K and h_pp of the context's last transform (see k_on_bfgs); w: 6 ng + ng^2
+// doubles of scratch, info: 2 device doubles.
+int pnof_on_converge(nof_ctx* c, double* gamma, double tol, int maxit, double lr0, double* w, double* info) {
+    k_on_bfgs<<<1, 1024, 0, c->stream>>>(gamma, c->npair, c->opt.ncwo, c->opt.isoftmax, c->s, c->t, c->ds, c->dt,
+                                         c->pair, c->slot, c->nact, c->opt.ipnof, c->hpp, c->J, c->K, c->part, w, tol,
+                                         maxit, lr0, info);
+    NOF_LAUNCH_CHECK();
     return NOF_OK;
 }
 

@@ -86,3 +86,33 @@ def fitted_columns(orb, aux, xyz, Cs, workers=None):
                 os.environ[k] = v
     k = Q3.shape[1]
     return (ri.inverse_sqrt_metric(integrals.two_center(aux, xyz)) @ Q3.reshape(X, k * k)).reshape(X, k, k)
+
+
+def _frame(args):
+    orb, aux, xyz, Q, gam = args
+    S, T, V = integrals.one_electron(orb, xyz)
+    B = ri.fitted_B(orb, aux, xyz)
+    from oracle import pnof, reference
+    n = S.shape[0]
+    pm = pnof.PairMap(xyz.shape[0], 1, n)
+    C = reference.orthonormal_orbitals(S, Q)
+    r = pnof.energy_and_gradients(B, T + V, C, gam, pm, integrals.nuclear_repulsion(xyz))
+    return C, r["E"], r["g"], r["g_gamma"]
+
+
+def frames(jobs, workers=None):
+    """The oracle's (C, E, g, g_gamma) for every (orb, aux, xyz, Q, gamma) job, C = S^{-1/2} Q, in
+    spawned worker processes with single-threaded BLAS."""
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_frame, jobs, chunksize=4))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v

@@ -68,6 +68,17 @@ def test_argument_checks_of_measurement_and_deployment_entry_points(lib):
     assert lib.nof_jk_static(70000, 1, 1, p, p, p, p, None) == nof.NOF_EINVAL
     assert b"grid limits" in lib.nof_last_error()
     assert lib.nof_jk_static(60000, 80, 1, p, p, p, p, None) == nof.NOF_EINVAL
+    # the wait-limit test hook refuses a missing output, a bad tile or a limit outside (0, 1000] ms
+    assert lib.nof_selftest_digit_gemm_timeout(128, 64, 64, 4, 4, 2.0, None) == nof.NOF_EINVAL
+    assert lib.nof_selftest_digit_gemm_timeout(128, 64, 24, 4, 4, 2.0, ctypes.byref(d)) == nof.NOF_EINVAL
+    assert lib.nof_selftest_digit_gemm_timeout(128, 64, 64, 4, 4, 0.0, ctypes.byref(d)) == nof.NOF_EINVAL
+    assert lib.nof_selftest_digit_gemm_timeout(128, 64, 64, 4, 4, 5000.0, ctypes.byref(d)) == nof.NOF_EINVAL
+    # the converged loop refuses bad parameters before any device work
+    prm = nof.OptParams()
+    lib.nof_default_opt_params(ctypes.byref(prm))
+    assert (prm.maxit, prm.maxloop, prm.gtol, prm.lr, prm.lr_grow) == (1000, 10, 1e-5, 0.02, 1.0)
+    res = (ctypes.c_double * 8)()
+    assert lib.nof_optimize(None, p, p, ctypes.byref(prm), None, res) == nof.NOF_EINVAL
 
 
 def test_bad_options_rejected(lib):

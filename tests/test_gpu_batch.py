@@ -2,6 +2,8 @@
 import numpy as np
 import pytest
 
+import oracle_pool
+
 from oracle import integrals, pnof, reference, ri
 from paper_2512_13550_gb300 import inputs
 
@@ -86,3 +88,41 @@ def test_batch_captured_in_one_graph():
     torch.cuda.synchronize()
     for (xyz, C, gam, ref), E in zip(frames, Es):
         assert abs(E.item() - ref["E"]) < GATE
+
+
+@pytest.mark.slow
+def test_full_batch_of_256_frames_matches_oracle_per_instance():
+    """The benchmark's batch: 256 displaced chains H8..H64 (lengths seed 3, displacements
+    sigma = 0.05 bohr), split precision, evaluated by one nof_energy_grad_batch call; every
+    instance's E, orbital gradient and occupation gradient against the oracle at 1e-6."""
+    import paper_2512_13550_gb300 as nof
+    orb, aux = inputs.basis_3s_10aux()
+    sizes = [int(x) for x in inputs.batch_sizes(256, seed=3, lo=8, hi=64)]
+    assert min(sizes) == 8 and max(sizes) == 64
+    geoms = [inputs.displaced_chain(N, seed=4 * 1000003 + i) for i, N in enumerate(sizes)]
+    jobs = [(orb, aux, xyz, inputs.random_orthogonal(3 * N, 5000 + i), inputs.random_gamma(N // 2, 6000 + i))
+            for i, (N, xyz) in enumerate(zip(sizes, geoms))]
+    refs = oracle_pool.frames(jobs)
+    ctxs, Cs, gs, Es, Gs, GGs = [], [], [], [], [], []
+    for (_, _, xyz, _, gam), (C, _, _, _) in zip(jobs, refs):
+        ctx = nof.Context(precision=nof.PREC_SPLIT_BF16, stream=torch.cuda.Stream())
+        ctx.build_B(xyz, orb, aux)
+        ctxs.append(ctx)
+        n, ng = ctx.sizes["nbf"], ctx.sizes["ngamma"]
+        Cs.append(_t(C)); gs.append(_t(gam))
+        Es.append(torch.empty(1, dtype=torch.float64, device="cuda"))
+        Gs.append(torch.empty(n, n, dtype=torch.float64, device="cuda"))
+        GGs.append(torch.empty(ng, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    nof.energy_grad_batch(ctxs, Cs, gs, Es, Gs, GGs)
+    torch.cuda.synchronize()
+    worst = {"E": 0.0, "g": 0.0, "g_gamma": 0.0}
+    for (_, E_ref, g_ref, gg_ref), E, G, GG in zip(refs, Es, Gs, GGs):
+        worst["E"] = max(worst["E"], abs(E.item() - E_ref))
+        worst["g"] = max(worst["g"], float(np.max(np.abs(G.cpu().numpy() - g_ref))))
+        worst["g_gamma"] = max(worst["g_gamma"], float(np.max(np.abs(GG.cpu().numpy() - gg_ref))))
+    print("256-frame batch vs oracle, worst max |difference|:", worst)
+    for key, d in worst.items():
+        assert d < GATE, key
+    for c in ctxs:
+        c.close()
