@@ -312,6 +312,14 @@ int nof_step_batch(nof_ctx* const* ctxs, int count, double* const* C, double* co
  * nof_mlp_loss_grad writes loss = mean over the batch of sum_o (y - t)^2 (device scalar, may be
  * NULL) and its gradient (packed like theta). nof_mlp_adam takes one bias-corrected Adam step
  * with decoupled weight decay wd (t >= 1 is the step count) on P parameters in place. */
+/* BF16 inference on the tensor cores: nof_mlp_to_bf16 converts the P packed FP32 parameters to BF16
+ * (theta_bf16: device, P 16-bit values, owned by the caller); nof_mlp_forward_bf16 then computes Y
+ * like nof_mlp_forward with every layer a BF16 x BF16 product (mma.sync m16n8k16, FP32
+ * accumulation; activations rounded to BF16 as each layer loads them, biases in FP32 from theta).
+ * work: device scratch of 2 B H floats. */
+int nof_mlp_to_bf16(long long P, const float* theta, void* theta_bf16, void* stream);
+int nof_mlp_forward_bf16(int B, int F, int H, int O, const void* theta_bf16, const float* theta, const float* X,
+                         float* Y, float* work, void* stream);
 long long nof_mlp_param_count(int F, int H, int O);
 long long nof_mlp_work_size(int B, int H, int O);
 int nof_mlp_forward(int B, int F, int H, int O, const float* theta, const float* X, float* Y, float* work,

@@ -92,6 +92,9 @@ SIGNATURES = {
     "nof_mlp_forward": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]),
     "nof_mlp_loss_grad": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P,
                                          _P, _P]),
+    "nof_mlp_to_bf16": (ctypes.c_int, [ctypes.c_longlong, _P, _P, _P]),
+    "nof_mlp_forward_bf16": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
+                                            _P, _P]),
     "nof_mlp_adam": (ctypes.c_int, [ctypes.c_longlong, _P, _P, _P, _P, ctypes.c_int, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
     "nof_nuclear_gradient": (ctypes.c_int, [_P, _P, _P, _P]),

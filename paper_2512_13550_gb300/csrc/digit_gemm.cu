@@ -118,17 +118,6 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                  : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -169,6 +158,15 @@ __device__ __forceinline__ float2 levels_to_df(const float* S, int e) {
     return make_float2((hi * s1) * s2, (lo * s1) * s2);
 }
 
+// a double-float in the bits of one 64-bit register (hi in the low word, lo in the high word)
+__device__ __forceinline__ long long pack_df(float2 x) {
+    return (long long)(((unsigned long long)__float_as_uint(x.y) << 32) | (unsigned long long)__float_as_uint(x.x));
+}
+__device__ __forceinline__ float2 unpack_df(long long v) {
+    const unsigned long long u = (unsigned long long)v;
+    return make_float2(__uint_as_float((unsigned)(u & 0xffffffffull)), __uint_as_float((unsigned)(u >> 32)));
+}
+
 // sum of two double-floats
 __device__ __forceinline__ float2 df2_add(float2 a, float2 b) {
     float s = a.x + b.x;
@@ -189,18 +187,19 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
 // shared-memory slots that carries over from one tile to the next; warp 1 lane 0 issues the
 // digit-product MMAs (6 per K atom with 4 digits, 9 with 5: pairs of products share one MMA of
 // width 2 BN) of a part into one of g.nbuf TMEM accumulator sets (nd levels x BN columns); the
-// epilogue warps drain each finished part into a shared-memory staging tile (exact
-// int64 sums, or double-float sums of the scaled values), hand the set back, and after the last
-// part of a tile write the staged rows as contiguous segments. With two sets the drain of one part
-// overlaps the MMAs of the next.
+// epilogue warps drain each finished part into running sums held in registers (int64 sums, or
+// double-float sums of the scaled values: each lane owns one row and up to 32 columns), hand the
+// set back, and after the last part of a tile write their rows from those registers. With two sets
+// the drain of one part overlaps the MMAs of the next; with no staging tile in shared memory the
+// ring holds one or two more stages.
 // Tiles go to CTAs round-robin, or, with a tile counter, dynamically: after its first tile
 // (blockIdx.x) the producer takes each next tile by a fetch-and-add and hands every index to the
 // MMA and epilogue warps through a small queue in shared memory. A CTA that starts late (its SM still busy with another stream's blocks) then
 // takes fewer tiles instead of holding up the whole launch.
 constexpr int kEpiWarps = 8;  // two per TMEM lane group, each owning half of the columns
+constexpr int kMaxCols = 32;  // columns of one epilogue warp: BN / 2 for BN >= 32, BN for BN 16
 constexpr int kTileQ = 4;     // tile-index queue slots (dynamic tiles)
 
-__host__ __device__ constexpr int stage_pitch(int BN) { return (BN >= 32 ? BN / 2 : 16) + 1; }
 
 template <int ND>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
@@ -217,9 +216,6 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
     uint64_t* bars = (uint64_t*)(sB + S * b_stage_bytes);
     uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 4 + 2 * kTileQ);
     volatile int* tq_id = (volatile int*)(tmem_slot + 4);  // queued tile indices (dynamic tiles)
-    // per epilogue warp: 32 rows x (its columns + 1 pad) of int64 or double-float partial sums
-    const int SP = stage_pitch(BN);
-    float2* stage_out = (float2*)(((uintptr_t)(tq_id + kTileQ) + 15) & ~(uintptr_t)15);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[S]),
                    tfull0 = smem_u32(&bars[2 * S]), tempty0 = smem_u32(&bars[2 * S + 2]),
@@ -399,10 +395,8 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
         // column halves for BN >= 32; for BN = 16 the second warp of each lane group has no columns
         const int cbeg = BN >= 32 ? h * (BN / 2) : 0;
         const int cend = BN >= 32 ? cbeg + BN / 2 : (h ? 0 : BN);
-        const int cw = cend - cbeg;
+        const int cw = cend - cbeg;  // <= kMaxCols
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        float2* st = stage_out + (warp - 2) * 32 * SP;  // this warp's 32 x SP staging tile
-        long long* stI = reinterpret_cast<long long*>(st);
         int unit = 0;
         for (int qi = 0; ok; ++qi) {  // qi: this CTA's tile sequence (q is the lane group)
             const int tile = consumer_tile(qi, 0xffffffffu);
@@ -412,12 +406,15 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
             const int tk = min(g.katoms, g.katoms_total - kc * g.katoms);
             const int nparts = (tk + g.apart - 1) / g.apart;
             const int rbase = tm * kBM + q * 32;
-            const int row = rbase + lane;
-            const int col0 = tn * BN + cbeg;  // global column of staging column 0
+            const int row = rbase + lane;  // this lane's output row
+            const int col0 = tn * BN + cbeg;  // global column of this warp's column 0
             const bool partsc = g.epA != nullptr;
             const bool ints = !g.outf && !partsc;  // exact int64 sums
             constexpr int kOff = 8 * (ND + 1);  // value = 2^{e_row + e_col - 8 (ND + 1)} V
             const int er = (g.outf && row < g.M) ? g.erow[row] - kOff : 0;
+            // running sums of this lane's row over the parts, in registers: the int64 V, or the bits
+            // of a double-float (hi in the low word, lo in the high word)
+            long long acc[kMaxCols];
             for (int part = 0; part < nparts && ok; ++part, ++unit) {
                 const int b = unit % NB, use = unit / NB;
                 const long long gp = (long long)(kc * g.katoms) / g.apart + part;  // part index along K
@@ -430,42 +427,39 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                 ok = mbar_wait(tfull0 + 8 * b, use & 1, g.status, g.timeout_ns);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t acc = tmem + lane_base + (uint32_t)(b * ND * BN);
-                for (int c0 = 0; c0 < cw; c0 += 16) {
-                    const int w = min(16, cw - c0);  // 16, or 8 for the last chunk of a 24-column half
-                    float v[ND][16];
+                const uint32_t acct = tmem + lane_base + (uint32_t)(b * ND * BN);
+#pragma unroll
+                for (int c0 = 0; c0 < kMaxCols; c0 += 8) {  // constant indices keep acc in registers
+                    if (c0 >= cw) break;  // cw is a multiple of 8
+                    // 8 columns of every level at a time: the register budget of a 10-warp CTA (about
+                    // 170 per thread: three warps share a sub-partition's 16K registers) holds the 32
+                    // running sums and ND x 8 loaded values without spilling
+                    float v[ND][8];
                     const uint32_t col = (uint32_t)(cbeg + c0);
-                    if (w == 16) {
 #pragma unroll
-                        for (int l = 0; l < ND; ++l) tmem_ld16(acc + (uint32_t)(l * BN) + col, v[l]);
-                    } else {
-#pragma unroll
-                        for (int l = 0; l < ND; ++l) tmem_ld8(acc + (uint32_t)(l * BN) + col, v[l]);
-                    }
+                    for (int l = 0; l < ND; ++l) tmem_ld8(acct + (uint32_t)(l * BN) + col, v[l]);
                     tmem_wait_ld();
                     if (ints) {
-                        // level sums are exact integers below 2^24: 32-bit conversions and a 64-bit
-                        // integer sum (64-bit int <-> float conversions run at the FP64 rate here)
+                        // the leading level sums are exact integers below 2^24 and the last two stay
+                        // below 2^31: 32-bit conversions and a 64-bit integer sum (64-bit int <-> float
+                        // conversions run at the FP64 rate here)
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            if (j >= w) break;
+                        for (int j = 0; j < 8; ++j) {
                             long long Vp = 0;
 #pragma unroll
                             for (int l = 0; l < ND; ++l) Vp += (long long)__float2int_rn(v[l][j]) << (8 * (ND - 1 - l));
-                            long long& s = stI[lane * SP + c0 + j];
-                            s = part ? s + Vp : Vp;
+                            acc[c0 + j] = part ? acc[c0 + j] + Vp : Vp;
                         }
                     } else {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            if (j >= w) break;
+                        for (int j = 0; j < 8; ++j) {
                             const int e = erp + __shfl_sync(0xffffffffu, ecl, c0 + j);
                             float S[ND];
 #pragma unroll
                             for (int l = 0; l < ND; ++l) S[l] = v[l][j];
-                            const float2 x = levels_to_df<ND>(S, e);
-                            float2& s = st[lane * SP + c0 + j];
-                            s = part ? df2_add(s, x) : x;
+                            float2 x = levels_to_df<ND>(S, e);
+                            if (part) x = df2_add(unpack_df(acc[c0 + j]), x);
+                            acc[c0 + j] = pack_df(x);
                         }
                     }
                 }
@@ -475,65 +469,67 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                 if (lane == 0) mbar_arrive(tempty0 + 8 * b);
             }
             if (!ok) break;
-            __syncwarp();
-            const int ncol = min(cw, g.Nvalid - col0);  // valid staged columns
-            // lanes cover whole rows of the staging tile: row lane / L, column lane % L, with L the
-            // number of lanes per row (cw elements, or cw / 2 pairs) and 32 / L rows per pass
-            if (ncol > 0) {
+            const int ncol = min(cw, g.Nvalid - col0);  // valid columns of this warp (warp-uniform)
+            // each lane writes its own row: 16-byte stores of column pairs (double-floats) or one
+            // element at a time (int64, FP64 partials, atomics)
+            if (ncol > 0 && row < g.M) {
                 if (g.out) {
-                    const int rpp = 32 / cw, lr = lane / cw, cc = lane - lr * cw;
-                    for (int rr = lr; lr < rpp && rr < 32; rr += rpp) {
-                        const int grow = rbase + rr;
-                        if (grow >= g.M || cc >= ncol) continue;
-                        long long* dst = g.out + (long long)grow * g.ldo + col0 + cc;
-                        const long long V = stI[rr * SP + cc];
-                        if (g.atomic) atomicAdd((unsigned long long*)dst, (unsigned long long)V);
-                        else *dst = V;
+                    long long* dst = g.out + (long long)row * g.ldo + col0;
+#pragma unroll
+                    for (int c = 0; c < kMaxCols; ++c) {
+                        if (c >= ncol) break;
+                        if (g.atomic) atomicAdd((unsigned long long*)(dst + c), (unsigned long long)acc[c]);
+                        else dst[c] = acc[c];
                     }
                 } else if (g.outd) {
-                    const int rpp = 32 / cw, lr = lane / cw, cc = lane - lr * cw;
-                    for (int rr = lr; lr < rpp && rr < 32; rr += rpp) {
-                        const int grow = rbase + rr;
-                        if (grow >= g.M || cc >= ncol) continue;
-                        double* dst = g.outd + (long long)kc * g.chunk_stride + (long long)grow * g.ldo + col0 + cc;
-                        const float2 x = st[rr * SP + cc];
+                    double* dst = g.outd + (long long)kc * g.chunk_stride + (long long)row * g.ldo + col0;
+#pragma unroll
+                    for (int c = 0; c < kMaxCols; ++c) {
+                        if (c >= ncol) break;
+                        const float2 x = unpack_df(acc[c]);
                         const double v = (double)x.x + (double)x.y;
-                        if (g.atomic) atomicAdd(dst, v);
-                        else *dst = v;
+                        if (g.atomic) atomicAdd(dst + c, v);
+                        else dst[c] = v;
                     }
                 } else {
-                    // pairs of columns as 16-byte stores, consecutive lanes along a row
-                    const int hp = cw / 2;
-                    const int rpp = 32 / hp, lr = lane / hp, cc = 2 * (lane - lr * hp);
-                    for (int rr = lr; lr < rpp && rr < 32; rr += rpp) {
-                        const int grow = rbase + rr;
-                        if (grow >= g.M || cc >= ncol) continue;
-                        float2* dst = g.outf + (long long)grow * g.ldo + col0 + cc;
-                        const float2 x0 = st[rr * SP + cc];
-                        if (cc + 1 < ncol) {
-                            const float2 x1 = st[rr * SP + cc + 1];
-                            *reinterpret_cast<float4*>(dst) = make_float4(x0.x, x0.y, x1.x, x1.y);
+                    float2* dst = g.outf + (long long)row * g.ldo + col0;  // ldo and col0 even: 16-byte aligned
+#pragma unroll
+                    for (int c = 0; c < kMaxCols; c += 2) {
+                        if (c >= ncol) break;
+                        const float2 x0 = unpack_df(acc[c]);
+                        if (c + 1 < ncol) {
+                            const float2 x1 = unpack_df(acc[c + 1]);
+                            *reinterpret_cast<float4*>(dst + c) = make_float4(x0.x, x0.y, x1.x, x1.y);
                         } else {
-                            *dst = x0;
+                            dst[c] = x0;
                         }
                     }
-                    // column maxima per group (atomics without a return value: nothing waits on them)
-                    if (g.colmax && lane < ncol && rbase < g.M) {  // lane = column: runs of rows of a group
-                        int grp = rbase / g.group_rows;
-                        int next = (grp + 1) * g.group_rows;  // first row of the next group
-                        const int rend = min(32, g.M - rbase);
-                        float m = 0.f;
-                        for (int rr = 0; rr < rend; ++rr) {
-                            if (rbase + rr == next) {
-                                atomicMax(g.colmax + (long long)grp * g.Nvalid + col0 + lane, __float_as_uint(m));
-                                m = 0.f;
-                                ++grp;
-                                next += g.group_rows;
-                            }
-                            m = fmaxf(m, fabsf(st[rr * SP + lane].x));
-                        }
-                        atomicMax(g.colmax + (long long)grp * g.Nvalid + col0 + lane, __float_as_uint(m));
+                }
+            }
+            // column maxima of |value| per group of rows (GEMM1: per aux function), by a segmented
+            // reduction over the lanes: groups are runs of consecutive rows, so after steps 1, 2, 4,
+            // 8, 16 that only take a lane's value from a lane of the same group, the first lane of
+            // each run holds the run's maximum (atomics without a return value: nothing waits)
+            if (g.outf && g.colmax && ncol > 0 && rbase < g.M) {
+                const int grp = row / g.group_rows;
+                unsigned same = 0;
+#pragma unroll
+                for (int i2 = 0; i2 < 5; ++i2) {
+                    const int og = __shfl_down_sync(0xffffffffu, grp, 1 << i2);
+                    if (lane + (1 << i2) < 32 && og == grp) same |= 1u << i2;
+                }
+                const int gprev = __shfl_up_sync(0xffffffffu, grp, 1);
+                const bool leader = (lane == 0 || gprev != grp) && row < g.M;
+#pragma unroll
+                for (int c = 0; c < kMaxCols; ++c) {
+                    if (c >= ncol) break;
+                    float m = row < g.M ? fabsf(unpack_df(acc[c]).x) : 0.f;
+#pragma unroll
+                    for (int i2 = 0; i2 < 5; ++i2) {
+                        const float o = __shfl_down_sync(0xffffffffu, m, 1 << i2);
+                        if (same & (1u << i2)) m = fmaxf(m, o);
                     }
+                    if (leader) atomicMax(g.colmax + (long long)grp * g.Nvalid + col0 + c, __float_as_uint(m));
                 }
             }
             __syncwarp();
@@ -556,17 +552,18 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
 
 constexpr size_t kSmemLimit = 227 * 1024;
 
+// the ring of stages, the barriers, the TMEM address slot and the tile queue (the epilogue keeps its
+// sums in registers and writes from them: no staging tile)
 size_t smem_bytes(int BN, int stages, int nd) {
     return (size_t)stages * nd * kStageAtoms * 32 * (kBM + BN) + 8 * (2 * stages + 4 + 2 * kTileQ) + 16 +
-           4 * kTileQ + 16 +
-           (size_t)kEpiWarps * 32 * stage_pitch(BN) * sizeof(float2) + 256;
+           4 * kTileQ + 16 + 256;
 }
 
 }  // namespace
 
 int digit_gemm_max_stages(int BN, int nd) {
     int s = 2;
-    while (s < 6 && smem_bytes(BN, s + 1, nd) <= kSmemLimit) ++s;
+    while (s < 8 && smem_bytes(BN, s + 1, nd) <= kSmemLimit) ++s;
     return s;
 }
 
