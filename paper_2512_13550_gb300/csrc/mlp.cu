@@ -7,6 +7,8 @@
 // over the batch of sum_o (y - t)^2. Parameters packed as W1 [H][F], b1 [H], W2 [H][H], b2 [H],
 // W3 [O][H], b3 [O]. Work buffer (floats): Z1 [B][H], Z2 [B][H], Y [B][O], dZ2 [B][H], dZ1 [B][H],
 // dY [B][O].
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace {
@@ -159,6 +161,56 @@ int mlp_forward(const MlpLayout& L, const float* X, int B, int F, int H, int O, 
 
 bool bad_sizes(int B, int F, int H, int O) { return B <= 0 || F <= 0 || H <= 0 || O <= 0; }
 
+// ---- BF16 inference on the tensor cores ---------------------------------------------------------
+// One layer Y = act(X W^T + b): X [B][K] FP32 activations (rounded to BF16 as they are loaded),
+// W [N][K] BF16 (the converted parameters), b [N] FP32, FP32 accumulation. One warp per 16 x 8
+// output tile, mma.sync m16n8k16 over K in steps of 16; rows >= B, columns >= N and K >= Kdim are
+// zero-filled on load and not stored.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x (low 16 bits) = lo
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ uint32_t load_bf16x2(const __nv_bfloat16* W, long long ld, int n, int k, int N, int K) {
+    const unsigned short lo = (n < N && k < K) ? __bfloat16_as_ushort(W[(long long)n * ld + k]) : 0;
+    const unsigned short hi = (n < N && k + 1 < K) ? __bfloat16_as_ushort(W[(long long)n * ld + k + 1]) : 0;
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+__global__ void __launch_bounds__(32) k_layer_bf16(const float* X, int B, int K, const __nv_bfloat16* W,
+                                                   const float* bias, int N, int relu, float* Y) {
+    const int lane = threadIdx.x, grp = lane >> 2, tig = lane & 3;
+    const int m0 = blockIdx.x * 16, n0 = blockIdx.y * 8;
+    auto xa = [&](int r, int k) { return (r < B && k < K) ? X[(long long)r * K + k] : 0.f; };
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        const int ka = k0 + 2 * tig;
+        const uint32_t a0 = pack_bf16x2(xa(m0 + grp, ka), xa(m0 + grp, ka + 1));
+        const uint32_t a1 = pack_bf16x2(xa(m0 + grp + 8, ka), xa(m0 + grp + 8, ka + 1));
+        const uint32_t a2 = pack_bf16x2(xa(m0 + grp, ka + 8), xa(m0 + grp, ka + 9));
+        const uint32_t a3 = pack_bf16x2(xa(m0 + grp + 8, ka + 8), xa(m0 + grp + 8, ka + 9));
+        const uint32_t b0 = load_bf16x2(W, K, n0 + grp, ka, N, K);
+        const uint32_t b1 = load_bf16x2(W, K, n0 + grp, ka + 8, N, K);
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};\n"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    }
+    // d0, d1: row grp, columns 2 tig, 2 tig + 1; d2, d3: row grp + 8
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = m0 + grp + (i >= 2 ? 8 : 0), c = n0 + 2 * tig + (i & 1);
+        if (r < B && c < N) {
+            float v = d[i] + bias[c];
+            if (relu) v = fmaxf(v, 0.f);
+            Y[(long long)r * N + c] = v;
+        }
+    }
+}
+__global__ void k_to_bf16(const float* a, long long n, __nv_bfloat16* out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __float2bfloat16_rn(a[i]);
+}
+
 }  // namespace
 
 extern "C" {
@@ -218,6 +270,43 @@ int nof_mlp_loss_grad(int B, int F, int H, int O, const float* theta, const floa
     // gW1 = dZ1^T X, gb1 = colsum(dZ1)
     NOF_TRY(gemm32(mk(H, F, B, L.dZ1, 1, H, 0, X, F, 1, 0, gW1, F, 1), st));
     k_colsum<<<(unsigned)((H * 32 + 255) / 256), 256, 0, st>>>(L.dZ1, B, H, gb1);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+int nof_mlp_to_bf16(long long P, const float* theta, void* theta_bf16, void* stream) {
+    if (P <= 0 || !theta || !theta_bf16) {
+        nof_set_error("nof_mlp_to_bf16: bad arguments");
+        return NOF_EINVAL;
+    }
+    k_to_bf16<<<(unsigned)((P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(theta, P, (__nv_bfloat16*)theta_bf16);
+    NOF_LAUNCH_CHECK();
+    return NOF_OK;
+}
+
+int nof_mlp_forward_bf16(int B, int F, int H, int O, const void* theta_bf16, const float* theta, const float* X,
+                         float* Y, float* work, void* stream) {
+    if (bad_sizes(B, F, H, O) || !theta_bf16 || !theta || !X || !Y || !work) {
+        nof_set_error("nof_mlp_forward_bf16: bad sizes or null pointer");
+        return NOF_EINVAL;
+    }
+    if ((long long)(B + 15) / 16 > 2147483647LL || (H + 7) / 8 > 65535 || (O + 7) / 8 > 65535) {
+        nof_set_error("nof_mlp_forward_bf16: sizes beyond the launch grid");
+        return NOF_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const __nv_bfloat16* Wb = (const __nv_bfloat16*)theta_bf16;
+    // parameter offsets of the packed layout (the biases are read in FP32)
+    const long long oW1 = 0, ob1 = (long long)H * F, oW2 = ob1 + H, ob2 = oW2 + (long long)H * H, oW3 = ob2 + H,
+                    ob3 = oW3 + (long long)O * H;
+    float* Z1 = work;
+    float* Z2 = work + (long long)B * H;
+    const unsigned gm = (unsigned)((B + 15) / 16);
+    k_layer_bf16<<<dim3(gm, (H + 7) / 8), 32, 0, st>>>(X, B, F, Wb + oW1, theta + ob1, H, 1, Z1);
+    NOF_LAUNCH_CHECK();
+    k_layer_bf16<<<dim3(gm, (H + 7) / 8), 32, 0, st>>>(Z1, B, H, Wb + oW2, theta + ob2, H, 1, Z2);
+    NOF_LAUNCH_CHECK();
+    k_layer_bf16<<<dim3(gm, (O + 7) / 8), 32, 0, st>>>(Z2, B, H, Wb + oW3, theta + ob3, O, 0, Y);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }

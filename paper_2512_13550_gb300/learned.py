@@ -1,4 +1,4 @@
-"""Learned starting guess for the occupation angles (a machine-learning add-on; the paper has none).
+"""Learned starting guess for the occupations and orbitals (a machine-learning add-on; the paper has none).
 
 A perceptron (x -> relu 256 -> relu 256 -> y) maps per-pair features to y = sin^2 gamma_g (twice the
 weak occupation of subspace g; unlike gamma itself it is unique, since the trigonometric mapping is
@@ -222,7 +222,13 @@ def main(argv=None):
     ap.add_argument("--basis", choices=["3s10aux", "h1000"], default="3s10aux",
                     help="3s10aux: 3 s + 10 aux s per H; h1000: 1 contracted s + 3 aux s per H")
     ap.add_argument("--straight-eval", action="store_true", help="evaluate on straight 1.8-bohr chains")
+    ap.add_argument("--converged", action="store_true",
+                    help="train on converged solutions (occupations and pair rotation angles, nof_optimize) "
+                         "and compare learned and core-guess starts to convergence on held-out chains")
+    ap.add_argument("--gtol", type=float, default=1e-4)
     args = ap.parse_args(argv)
+    if args.converged:
+        return study(args)
     orb, aux = inputs.basis_h1000() if args.basis == "h1000" else inputs.basis_3s_10aux()
     t0 = time.perf_counter()
     X, y = generate(inputs.batch_sizes(args.train_chains, seed=21, lo=args.min_len, hi=args.max_len), orb, aux,
@@ -254,6 +260,185 @@ def main(argv=None):
                       "val_rmse": float(np.sqrt(np.mean((pv - yv) ** 2))),
                       "val_rmse_mean_predictor": float(np.sqrt(np.mean((y.mean() - yv) ** 2))),
                       "eval": rows}))
+
+
+# ----------------------------------------------------------------------------------------------
+# Occupations and orbital rotations from converged solutions (the loop of nof_optimize)
+# ----------------------------------------------------------------------------------------------
+NOUT = 2  # per pair: sin^2 gamma_g and the rotation angle between orbitals g and p(g)
+
+
+def pair_partner(npair: int, g: int) -> int:
+    """Weak orbital p(g) of subspace g for N_g = 1 (Fig. 1 pairing: HOMO-LUMO, HOMO-1 - LUMO+1, ...)."""
+    return 2 * npair - 1 - g
+
+
+def rotation_targets(C0: np.ndarray, C: np.ndarray, S: np.ndarray, npair: int) -> np.ndarray:
+    """theta_g: the plane rotation of the core-guess orbitals g and p(g) closest to the converged
+    ones. With U = C0^T S C (C = C0 U), the 2 x 2 block of U on (g, p(g)) is matched by the rotation
+    [[cos, sin], [-sin, cos]] that maximises the trace of its product with the block (orthogonal
+    Procrustes): theta = atan2(U_pg - U_gp, U_gg + U_pp). The energy does not change when a
+    converged orbital changes sign, so both sign choices of column p(g) are tried and the one whose
+    block a rotation fits best (the larger Procrustes trace, the norm of the atan2 arguments) is
+    kept; changing both signs is a rotation by pi, so the angle is reduced to (-pi/2, pi/2]."""
+    U = C0.T @ S @ C
+    out = np.zeros(npair)
+    for g in range(npair):
+        p = pair_partner(npair, g)
+        fits = []
+        for sp in (1.0, -1.0):
+            y, x = U[p, g] - sp * U[g, p], U[g, g] + sp * U[p, p]
+            fits.append((np.hypot(x, y), np.arctan2(y, x)))
+        th = max(fits)[1]
+        out[g] = (th + 0.5 * np.pi) % np.pi - 0.5 * np.pi
+    return out
+
+
+class BF16Net:
+    """The trained network's parameters converted once to BF16 for inference on the tensor cores
+    (nof_mlp_forward_bf16); the standardisation of the features is the training one."""
+
+    def __init__(self, net: MLP):
+        import torch
+        self.net = net
+        self.wb = torch.empty(net.P, dtype=torch.int16, device="cuda")
+        _check(load_library().nof_mlp_to_bf16(net.P, _fptr(net.theta), ctypes.c_void_p(self.wb.data_ptr()),
+                                              _stream()))
+
+    def __call__(self, feats: np.ndarray) -> np.ndarray:
+        import torch
+        net = self.net
+        X = torch.tensor((feats - net.mu) / net.sd, dtype=torch.float32, device="cuda")
+        B = X.shape[0]
+        Y = torch.empty(B, net.O, dtype=torch.float32, device="cuda")
+        work = torch.empty(2 * B * net.H, dtype=torch.float32, device="cuda")
+        _check(load_library().nof_mlp_forward_bf16(B, net.F, net.H, net.O, ctypes.c_void_p(self.wb.data_ptr()),
+                                                   _fptr(net.theta), _fptr(X), _fptr(Y), _fptr(work), _stream()))
+        return Y.cpu().numpy().astype(np.float64)
+
+
+def converged_solutions(sizes, orb, aux, seed=31, gtol=1e-4, etol=1e-7, maxit=3000, precision=1):
+    """Per-pair features and targets (sin^2 gamma*, theta*) from converged solutions of displaced
+    H chains: nof_optimize from the core guess and gamma = 0.3 to ||g|| < gtol. Returns (X, T,
+    records) with one record per chain (N, iterations, evaluations, converged, seconds)."""
+    import time
+
+    import torch
+
+    from . import Context
+    feats, targs, recs = [], [], []
+    for i, N in enumerate(sizes):
+        N = int(N)
+        xyz = inputs.displaced_chain(N, seed=seed * 100003 + i)
+        ctx = Context(precision=precision)
+        ctx.build_B(xyz, orb, aux)
+        S, _ = ctx.get_SH()
+        C0, eps = ctx.core_guess()
+        C = C0.clone()
+        gam = torch.full((ctx.sizes["ngamma"],), 0.3, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        r = ctx.optimize(C, gam, gtol=gtol, etol=etol, maxit=maxit)
+        dt = time.perf_counter() - t0
+        npair = N // 2
+        g = gam.cpu().numpy()[:npair]
+        th = rotation_targets(C0.cpu().numpy(), C.cpu().numpy(), S.cpu().numpy(), npair)
+        feats.append(pair_features(xyz, eps.cpu().numpy(), N))
+        targs.append(np.stack([np.sin(g) ** 2, th], axis=1))
+        recs.append((N, r["iterations"], r["evaluations"], r["converged"], round(dt, 3), r["E"]))
+        ctx.close()
+    return np.concatenate(feats), np.concatenate(targs), recs
+
+
+def learned_start(bnet: BF16Net, xyz, eps: np.ndarray, C0, ngamma: int, gamma0: float = 0.3):
+    """The learned starting point: gamma_g from the predicted sin^2 gamma, and C0 exp(Y) with
+    Y_{g, p(g)} = -Y_{p(g), g} the predicted pair angles (BF16 inference). Returns (C, gamma) as
+    device tensors."""
+    import torch
+    from scipy.linalg import expm
+    N = xyz.shape[0]
+    npair = N // 2
+    y = bnet(pair_features(xyz, eps, N))
+    gam = np.full(ngamma, gamma0)
+    gam[:npair] = angles(y[:, 0])
+    n = C0.shape[0]
+    Y = np.zeros((n, n))
+    for g in range(npair):  # exp(Y) rotates the plane (g, p(g)) by theta_g: C_g -> cos C_g + sin C_p
+        p = pair_partner(npair, g)
+        Y[p, g] = y[g, 1]
+        Y[g, p] = -y[g, 1]
+    C = torch.tensor(C0.cpu().numpy() @ expm(Y), dtype=torch.float64, device="cuda")
+    return C, torch.tensor(gam, dtype=torch.float64, device="cuda")
+
+
+def choose_start(ctx, learned, core):
+    """The automatic fallback: the learned start unless the core guess has the lower energy after
+    its ONs are converged (one outer iteration of nof_optimize from each, on copies)."""
+    es = []
+    for C, gam in (learned, core):
+        r = ctx.optimize(C.clone(), gam.clone(), maxit=1, maxloop=1)
+        es.append(r["history"][0, 0])
+    return (learned[0].clone(), learned[1].clone()) if es[0] <= es[1] else (core[0].clone(), core[1].clone())
+
+
+def compare_starts(bnet: BF16Net, sizes, orb, aux, seed=41, gtol=1e-4, etol=1e-7, maxit=3000, precision=1):
+    """Held-out displaced chains, optimised to convergence from the core guess (gamma = 0.3) and from
+    the learned start: per chain (N, E_start and evaluations, seconds, E_final for each start)."""
+    import time
+
+    import torch
+
+    from . import Context
+    out = []
+    for i, N in enumerate(sizes):
+        N = int(N)
+        xyz = inputs.displaced_chain(N, seed=seed * 100003 + i)
+        ctx = Context(precision=precision)
+        ctx.build_B(xyz, orb, aux)
+        C0, eps = ctx.core_guess()
+        row = {"N": N}
+        starts = {"core": (C0.clone(), torch.full((ctx.sizes["ngamma"],), 0.3, dtype=torch.float64, device="cuda")),
+                  "learned": learned_start(bnet, xyz, eps.cpu().numpy(), C0, ctx.sizes["ngamma"])}
+        starts["learned_or_core"] = choose_start(ctx, starts["learned"], starts["core"])
+        for name, (C, gam) in starts.items():
+            t0 = time.perf_counter()
+            r = ctx.optimize(C, gam, gtol=gtol, etol=etol, maxit=maxit)
+            dt = time.perf_counter() - t0
+            row[name] = {"E_start": float(r["history"][0, 0]), "E_final": r["E"], "iterations": r["iterations"],
+                         "evaluations": r["evaluations"], "converged": r["converged"], "seconds": round(dt, 3)}
+        out.append(row)
+        ctx.close()
+    return out
+
+def study(args):
+    """Converged training data, training, BF16 inference and the comparison of starts; one JSON line."""
+    import json
+    import time
+
+    import torch
+    orb, aux = inputs.basis_h1000() if args.basis == "h1000" else inputs.basis_3s_10aux()
+    t0 = time.perf_counter()
+    X, T, recs = converged_solutions(inputs.batch_sizes(args.train_chains, seed=21, lo=args.min_len, hi=args.max_len),
+                                     orb, aux, seed=31, gtol=args.gtol)
+    Xv, Tv, _ = converged_solutions(inputs.batch_sizes(max(8, args.train_chains // 8), seed=22, lo=args.min_len,
+                                                       hi=args.max_len), orb, aux, seed=32, gtol=args.gtol)
+    t_data = time.perf_counter() - t0
+    net = MLP(NFEAT, 256, NOUT, seed=0)
+    t0 = time.perf_counter()
+    hist = train(net, X, T, iters=args.iters, lr=1e-3, wd=0.3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    bnet = BF16Net(net)
+    pv = bnet(Xv)
+    rmse = np.sqrt(np.mean((pv - Tv) ** 2, axis=0))
+    base = np.sqrt(np.mean((T.mean(0) - Tv) ** 2, axis=0))
+    rows = compare_starts(bnet, args.eval_sizes, orb, aux, gtol=args.gtol)
+    print(json.dumps({"basis": args.basis, "train_chains": len(recs), "train_pairs": int(X.shape[0]),
+                      "converged_fraction": float(np.mean([r[3] for r in recs])),
+                      "mean_evaluations_per_training_chain": float(np.mean([r[2] for r in recs])),
+                      "data_s": round(t_data, 1), "train_s": round(t_train, 2), "loss_first": hist[0],
+                      "loss_last": hist[-1], "val_rmse_bf16": rmse.tolist(), "val_rmse_mean_predictor": base.tolist(),
+                      "eval": rows}))
+    return 0
 
 
 if __name__ == "__main__":

@@ -63,3 +63,44 @@ def test_learned_guess_trains_on_method_solutions():
     # the learned start is a valid occupation guess (angles in [0, pi/2])
     g0 = learned.angles(pred)
     assert np.all(g0 >= 0) and np.all(g0 <= np.pi / 2 + 1e-12)
+
+
+def test_bf16_inference_matches_oracle_forward():
+    """BF16 tensor-core inference (mma.sync, FP32 accumulation) against the FP64 oracle forward
+    pass: inputs, activations and weights rounded to BF16 (relative 2^-9 each) give outputs
+    within 2e-2 of the output scale, and the same network's FP32 forward agrees at that level."""
+    from paper_2512_13550_gb300 import learned
+    F, H, O, B = 8, 256, 2, 333  # a ragged batch: 21 tiles of 16 rows, the last one partial
+    net = learned.MLP(F, H, O, seed=4)
+    theta = net.theta.double().cpu().numpy()
+    X = inputs.normal(41, B * F).reshape(B, F)
+    ref = omlp.forward(theta, X, F, H, O)[0]
+    bnet = learned.BF16Net(net)
+    net.mu, net.sd = np.zeros(F), np.ones(F)
+    Y = bnet(X)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(Y - ref)) < 2e-2 * scale
+    assert np.max(np.abs(Y - ref)) > 0.0  # it is a BF16 computation, not the FP32 path
+    Y32 = learned.mlp_forward(net, torch.tensor(X, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    assert np.max(np.abs(Y32 - ref)) < 1e-5 * scale
+
+
+def test_learned_start_from_converged_solutions():
+    """Trained on converged solutions of displaced chains (occupations and pair rotation angles from
+    nof_optimize), the BF16 network proposes starts on held-out chains; every start converges, the
+    start with the automatic fallback is never above the core guess's first energy, and the
+    evaluations each start needed are reported."""
+    from paper_2512_13550_gb300 import learned
+    orb, aux = inputs.basis_3s_10aux()
+    X, T, recs = learned.converged_solutions(inputs.batch_sizes(24, seed=21, lo=6, hi=20), orb, aux, seed=31)
+    assert all(r[3] for r in recs)
+    net = learned.MLP(learned.NFEAT, 256, learned.NOUT, seed=0)
+    hist = learned.train(net, X, T, iters=800, lr=1e-3, wd=0.3)
+    assert hist[-1] < 0.5 * hist[0]
+    rows = learned.compare_starts(learned.BF16Net(net), [12, 16, 20], orb, aux)
+    for r in rows:
+        print(r)
+        assert r["core"]["converged"] and r["learned"]["converged"] and r["learned_or_core"]["converged"]
+        assert r["learned_or_core"]["E_start"] <= r["core"]["E_start"] + 1e-9
+    print("evaluations, core / learned / with fallback:",
+          [(r["core"]["evaluations"], r["learned"]["evaluations"], r["learned_or_core"]["evaluations"]) for r in rows])
