@@ -346,13 +346,17 @@ int nof_profile_read(nof_ctx* ctx, double* ms, int* launches, const char** name)
 
 /* Self-test of the exact BF16 digit-plane tensor-core GEMM (no paper counterpart): random
  * digit planes (M x K and N x K, K = 16 katoms, nd = 4 or 5 digits) multiplied on tcgen05 with
- * N tiles of `bn` columns (16, 32, 48 or 64) and K chunks of
+ * N tiles of `bn` columns (16, 32, 48, 64 or 80) and K chunks of
  * `chunk_atoms` atoms (integer atomics when chunk_atoms < katoms; the last chunk may be
  * shorter), and by a SIMT integer reference; *max_abs_diff (host) receives the largest
  * difference of the exact fixed-point results (0 when correct). The same product then runs twice
  * more with tiles taken dynamically from a fetch-and-add counter (the second launch checks that
- * the first left the counter at zero), each entering the same comparison. Allocates and frees its
- * own buffers; synchronises the device. */
+ * the first left the counter at zero), each entering the same comparison. With one K chunk and
+ * an even N the product is also written in the scaled double-float mode (random row and column
+ * exponents in [-6, 6]), and, when katoms is a multiple of digit_scale_part_atoms(nd), in the
+ * per-part FP64 mode with every part's exponents equal to those: a scaled value further than
+ * 2^-38 of the largest |V| the shape allows from the exact V sets *max_abs_diff to 2^62.
+ * Allocates and frees its own buffers; synchronises the device. */
 int nof_selftest_digit_gemm(int M, int N, int bn, int nd, int katoms, int chunk_atoms, unsigned int seed,
                             long long* max_abs_diff);
 
@@ -360,7 +364,7 @@ int nof_selftest_digit_gemm(int M, int N, int bn, int nd, int katoms, int chunk_
  * measurement only): M x N output, N tiles of bn, nd digits, K = 16 katoms in chunks of
  * chunk_atoms. mode 0: exact int64 output (split-K atomics when chunk_atoms < katoms);
  * 1: scaled double-float output (one chunk); 2: per-part scales with an FP64 partial per K chunk
- * (chunk_atoms a multiple of 8). Flags added to `mode`: 4 = each launch timed alone after a
+ * (chunk_atoms a multiple of digit_scale_part_atoms: 16 atoms with 5 digits, 8 with 4). Flags added to `mode`: 4 = each launch timed alone after a
  * 256 MiB write (L2 flushed, operands from HBM); 8 = tiles taken dynamically from a
  * fetch-and-add counter instead of round-robin. One warm-up, then the mean of `reps` launches
  * timed with CUDA events on the default stream into *us_per_launch (host). Allocates and frees

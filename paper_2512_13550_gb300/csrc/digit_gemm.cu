@@ -197,7 +197,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
 // MMA and epilogue warps through a small queue in shared memory. A CTA that starts late (its SM still busy with another stream's blocks) then
 // takes fewer tiles instead of holding up the whole launch.
 constexpr int kEpiWarps = 8;  // two per TMEM lane group, each owning half of the columns
-constexpr int kMaxCols = 32;  // columns of one epilogue warp: BN / 2 for BN >= 32, BN for BN 16
+constexpr int kMaxCols = 40;  // columns of one epilogue warp: BN / 2 for BN >= 32, BN for BN 16
 constexpr int kTileQ = 4;     // tile-index queue slots (dynamic tiles)
 
 
@@ -419,11 +419,12 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                 const int b = unit % NB, use = unit / NB;
                 const long long gp = (long long)(kc * g.katoms) / g.apart + part;  // part index along K
                 // this part's exponents, loaded before the wait so that their latency overlaps it:
-                // the row's, and one column's per lane (column col0 + lane, cw <= 32), handed to the
-                // other lanes by shuffles
+                // the row's, and the columns' (column col0 + lane, and col0 + 32 + lane when the
+                // warp has more than 32 columns), handed to the other lanes by shuffles
                 const int erp = (partsc && row < g.M) ? g.epA[gp * g.M + row] - kOff : er;
                 const int* ec = partsc ? g.epB + gp * g.Nvalid : g.ecol;
                 const int ecl = ints ? 0 : ec[min(col0 + lane, g.Nvalid - 1)];
+                const int ech = (ints || cw <= 32) ? 0 : ec[min(col0 + 32 + lane, g.Nvalid - 1)];
                 ok = mbar_wait(tfull0 + 8 * b, use & 1, g.status, g.timeout_ns);
                 if (!ok) break;
                 tc_fence_after();
@@ -453,7 +454,8 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                     } else {
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            const int e = erp + __shfl_sync(0xffffffffu, ecl, c0 + j);
+                            const int e =
+                                erp + __shfl_sync(0xffffffffu, c0 + j < 32 ? ecl : ech, (c0 + j) & 31);
                             float S[ND];
 #pragma unroll
                             for (int l = 0; l < ND; ++l) S[l] = v[l][j];
@@ -803,6 +805,23 @@ __global__ void k_ref_digit_gemm(const uint16_t* A, const uint16_t* B, int NB, i
     for (int l = 0; l < nd; ++l) V = V * 256 + S[l];
     out[(long long)m * N + n] = V;
 }
+// small random exponents in [-6, 6] (row or column scales of the scaled output modes)
+__global__ void k_random_exps(int* e, int n, uint32_t seed) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) e[i] = (int)(hash32((uint32_t)i * 2246822519u + seed) % 13u) - 6;
+}
+// The scaled outputs against the exact V: |value 2^-e - V| must stay below tolV (value = hi + lo of a
+// double-float, or an FP64 sum over parts whose scales are all erow[m] + ecol[n]); a larger
+// deviation marks the comparison failed by raising the running maximum to 2^62.
+__global__ void k_check_scaled(const long long* V, const float2* outf, const double* outd, const int* erow,
+                               const int* ecol, int M, int N, int nd, double tolV, unsigned long long* out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)M * N) return;
+    const int m = (int)(i / N), n = (int)(i - (long long)m * N);
+    const double got = outf ? (double)outf[i].x + (double)outf[i].y : outd[i];
+    const double back = ldexp(got, -(erow[m] + ecol[n] - 8 * (nd + 1)));
+    if (!(fabs(back - (double)V[i]) <= tolV)) atomicMax(out, 1ull << 62);
+}
 __global__ void k_max_absdiff(const long long* a, const long long* b, long long n, unsigned long long* out) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -873,6 +892,58 @@ extern "C" int nof_selftest_digit_gemm(int M, int N, int bn, int nd, int katoms,
         }
     }
     cudaFree(ctr);
+    // the scaled double-float output (row and column exponents), and, when K is whole parts of
+    // the per-part scales, the FP64 per-part output with every part's scales equal to the row's
+    // and column's: both against the exact V within 2^-38 of the largest |V| the shape allows
+    // (far below any wrong exponent or column, far above the double-float rounding)
+    if (r == NOF_OK && chunk_atoms >= katoms) {
+        int *er = nullptr, *ecl = nullptr, *epA = nullptr, *epB = nullptr;
+        float2* outf = nullptr;
+        double* outd = nullptr;
+        const int patoms = digit_scale_part_atoms(nd);
+        const bool parts = katoms % patoms == 0;
+        const int nparts = parts ? katoms / patoms : 0;
+        if ((e = cudaMalloc(&er, 4ull * M)) != cudaSuccess) fail(e, "malloc erow");
+        if (r == NOF_OK && (e = cudaMalloc(&ecl, 4ull * N)) != cudaSuccess) fail(e, "malloc ecol");
+        if (r == NOF_OK && (e = cudaMalloc(&outf, 8ull * M * N)) != cudaSuccess) fail(e, "malloc outf");
+        if (r == NOF_OK && parts && (e = cudaMalloc(&outd, 8ull * M * N)) != cudaSuccess) fail(e, "malloc outd");
+        if (r == NOF_OK && parts && (e = cudaMalloc(&epA, 4ull * M * nparts)) != cudaSuccess) fail(e, "malloc epA");
+        if (r == NOF_OK && parts && (e = cudaMalloc(&epB, 4ull * N * nparts)) != cudaSuccess) fail(e, "malloc epB");
+        const double tolV = std::ldexp(16.0 * katoms * 1.004 * 65536.0 * std::pow(256.0, nd - 1), -38);
+        if (r == NOF_OK) {
+            k_random_exps<<<(M + 255) / 256, 256>>>(er, M, seed * 3u + 1u);
+            k_random_exps<<<(N + 255) / 256, 256>>>(ecl, N, seed * 5u + 2u);
+            for (int q = 0; q < nparts; ++q) {  // every part carries the row's and column's scale
+                cudaMemcpy(epA + (size_t)q * M, er, 4ull * M, cudaMemcpyDeviceToDevice);
+                cudaMemcpy(epB + (size_t)q * N, ecl, 4ull * N, cudaMemcpyDeviceToDevice);
+            }
+            DigitGemmOut o;
+            o.outf = outf;
+            o.ldo = N + (N & 1);  // even leading dimension (16-byte pairs)
+            o.erow = er;
+            o.ecol = ecl;
+            DigitGemmPlan p;
+            if (o.ldo == N) {
+                r = digit_gemm_plan(&p, A, B, M, N, bn, nd, katoms, katoms, 0, o, status);
+                if (r == NOF_OK) r = digit_gemm_run(p, 0);
+                if (r == NOF_OK)
+                    k_check_scaled<<<nblkMN, 256>>>(C2, outf, nullptr, er, ecl, M, N, nd, tolV, dmax);
+            }
+            if (r == NOF_OK && parts) {
+                DigitGemmOut od;
+                od.outd = outd;
+                od.ldo = N;
+                od.epA = epA;
+                od.epB = epB;
+                od.part_atoms = patoms;
+                r = digit_gemm_plan(&p, A, B, M, N, bn, nd, katoms, katoms, 0, od, status);
+                if (r == NOF_OK) r = digit_gemm_run(p, 0);
+                if (r == NOF_OK)
+                    k_check_scaled<<<nblkMN, 256>>>(C2, nullptr, outd, er, ecl, M, N, nd, tolV, dmax);
+            }
+        }
+        cudaFree(er); cudaFree(ecl); cudaFree(outf); cudaFree(outd); cudaFree(epA); cudaFree(epB);
+    }
     if (r == NOF_OK) {
         unsigned long long h = 0;
         int hs = 0;

@@ -4,20 +4,22 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-// Tile widths along N the kernel supports: 16, 32, 48, 64 (the epilogue splits BN >= 32 into two
-// column halves, read from TMEM in chunks of 16 columns and, for 48, one of 8). The TMEM accumulators (nd levels x BN columns per set) take two sets when
-// 2 nd BN <= 512 columns (the drain of one set overlaps the MMAs into the other) and one set
-// otherwise (5 digits with BN = 64).
-constexpr int kDigitBN[4] = {16, 32, 48, 64};
+// Tile widths along N the kernel supports: 16, 32, 48, 64, 80 (the epilogue splits BN >= 32 into
+// two column halves, read from TMEM in chunks of 8 columns). The TMEM accumulators (nd levels x BN
+// columns per set) take two sets when 2 nd BN <= 512 columns (the drain of one set overlaps the
+// MMAs into the other) and one set otherwise (5 digits with BN = 64 or 80, 4 digits with 80).
+// Wider tiles stream fewer operand bytes per multiply-add: a K atom of a tile brings 128 + BN
+// rows of digits into shared memory for 128 x BN outputs.
+constexpr int kDigitBN[5] = {16, 32, 48, 64, 80};
 inline bool digit_bn_ok(int BN, int nd) {
-    return (BN == 16 || BN == 32 || BN == 48 || BN == 64) && nd * BN <= 512;
+    return (BN == 16 || BN == 32 || BN == 48 || BN == 64 || BN == 80) && nd * BN <= 512;
 }
 inline int digit_nbuf(int BN, int nd) { return 2 * nd * BN <= 512 ? 2 : 1; }
 
 struct DigitGemmArgs {
     int nd;            // digits per element (4 or 5): nd (nd + 1) / 2 plane products per K atom
     int M;             // valid rows of A (rows of the output)
-    int BN;            // tile width along N: 16, 32 or 64; B is stored in tiles of BN rows
+    int BN;            // tile width along N (kDigitBN); B is stored in tiles of BN rows
     int tiles_n;       // N tiles
     int Nvalid;        // output columns written (<= tiles_n * BN)
     int katoms;        // K atoms (16 each) per split-K chunk; the last chunk may be shorter

@@ -46,7 +46,14 @@ def _bound(nd, katoms):
     (257, 100, 48, 12, 12, 4),   # 4 digits, BN 48, ragged last tile (100 = 2 x 48 + 4)
     (300, 64, 32, 70, 70, 4),    # 4 digits, K = 1120: five parts of 14
     (256, 48, 48, 41, 41, 5),    # 5 digits, K = 656: three parts (14 + 14 + 13), odd count
+    (300, 208, 80, 38, 38, 5),   # 5 digits, BN 80 (40-column halves), one TMEM set, ragged last tile
+    (257, 100, 80, 24, 9, 4),    # 4 digits, BN 80, split-K (9, 9, 6), ragged last tile (100 = 80 + 20)
+    (130, 1000, 80, 64, 64, 5),  # 5 digits, BN 80, 13 N tiles (the last 40 of 80), four scale parts
+    (257, 100, 80, 24, 24, 4),   # 4 digits, BN 80, three scale parts of 8 atoms
 ])
 def test_digit_gemm_exact(M, N, bn, katoms, chunk, nd):
+    """The int64 output (single CTAs, round-robin and dynamic tiles) within the last levels' rounding
+    of the exact V; with one K chunk and an even N, the scaled double-float output too, and with K in
+    whole scale parts the per-part FP64 output (the self-test reports 2^62 if either is off)."""
     import paper_2512_13550_gb300 as nof
     assert 0 <= nof.selftest_digit_gemm(M, N, bn, katoms, chunk, seed=M * 7 + N + bn, nd=nd) <= _bound(nd, katoms)
