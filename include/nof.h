@@ -346,7 +346,7 @@ int nof_profile_read(nof_ctx* ctx, double* ms, int* launches, const char** name)
 
 /* Self-test of the exact BF16 digit-plane tensor-core GEMM (no paper counterpart): random
  * digit planes (M x K and N x K, K = 16 katoms, nd = 4 or 5 digits) multiplied on tcgen05 with
- * N tiles of `bn` columns (16, 32, 48, 64 or 80) and K chunks of
+ * N tiles of `bn` columns (16, 32, 48, 64, 80 or 96) and K chunks of
  * `chunk_atoms` atoms (integer atomics when chunk_atoms < katoms; the last chunk may be
  * shorter), and by a SIMT integer reference; *max_abs_diff (host) receives the largest
  * difference of the exact fixed-point results (0 when correct). The same product then runs twice

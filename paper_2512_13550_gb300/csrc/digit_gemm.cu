@@ -197,11 +197,13 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
 // MMA and epilogue warps through a small queue in shared memory. A CTA that starts late (its SM still busy with another stream's blocks) then
 // takes fewer tiles instead of holding up the whole launch.
 constexpr int kEpiWarps = 8;  // two per TMEM lane group, each owning half of the columns
-constexpr int kMaxCols = 40;  // columns of one epilogue warp: BN / 2 for BN >= 32, BN for BN 16
+// columns of one epilogue warp (BN / 2 for BN >= 32, BN for BN 16), a template parameter MAXC of the
+// kernel: 40 for BN <= 80, 48 for BN 96 (whose 48 running sums leave a few registers to spill)
+constexpr int kMaxColsOf(int BN) { return BN > 80 ? 48 : 40; }
 constexpr int kTileQ = 4;     // tile-index queue slots (dynamic tiles)
 
 
-template <int ND>
+template <int ND, int kMaxCols>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
 k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, DigitGemmArgs g) {
     // 32-byte swizzling repeats every 256 bytes: every operand block starts on a 256-byte boundary
@@ -647,8 +649,10 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
         int dev = 0;
         NOF_CUDA(cudaGetDevice(&dev));
         NOF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<4, 40>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<5, 40>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<4, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<5, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
     }
     const long long ntiles = (long long)g.tiles_n * g.tiles_m * g.kchunks;
     if (ntiles > 0x7fffffffLL) {
@@ -660,8 +664,15 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
 }
 
 int digit_gemm_run(const DigitGemmPlan& p, cudaStream_t st) {
-    if (p.g.nd == 5) k_digit_gemm<5><<<p.grid, 64 + 32 * kEpiWarps, p.smem, st>>>(p.A, p.B, p.g);
-    else k_digit_gemm<4><<<p.grid, 64 + 32 * kEpiWarps, p.smem, st>>>(p.A, p.B, p.g);
+    const dim3 blk(64 + 32 * kEpiWarps);
+    const bool wide = kMaxColsOf(p.g.BN) == 48;
+    if (p.g.nd == 5) {
+        if (wide) k_digit_gemm<5, 48><<<p.grid, blk, p.smem, st>>>(p.A, p.B, p.g);
+        else k_digit_gemm<5, 40><<<p.grid, blk, p.smem, st>>>(p.A, p.B, p.g);
+    } else {
+        if (wide) k_digit_gemm<4, 48><<<p.grid, blk, p.smem, st>>>(p.A, p.B, p.g);
+        else k_digit_gemm<4, 40><<<p.grid, blk, p.smem, st>>>(p.A, p.B, p.g);
+    }
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }

@@ -4,15 +4,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-// Tile widths along N the kernel supports: 16, 32, 48, 64, 80 (the epilogue splits BN >= 32 into
-// two column halves, read from TMEM in chunks of 8 columns). The TMEM accumulators (nd levels x BN
-// columns per set) take two sets when 2 nd BN <= 512 columns (the drain of one set overlaps the
-// MMAs into the other) and one set otherwise (5 digits with BN = 64 or 80, 4 digits with 80).
+// Tile widths along N the kernel supports: 16, 32, 48, 64, 80, 96 (the epilogue splits BN >= 32
+// into two column halves, read from TMEM in chunks of 8 columns). The TMEM accumulators (nd levels
+// x BN columns per set) take two sets when 2 nd BN <= 512 columns (the drain of one set overlaps
+// the MMAs into the other) and one set otherwise (5 digits with BN >= 64, 4 digits with BN >= 80).
 // Wider tiles stream fewer operand bytes per multiply-add: a K atom of a tile brings 128 + BN
 // rows of digits into shared memory for 128 x BN outputs.
-constexpr int kDigitBN[5] = {16, 32, 48, 64, 80};
+constexpr int kDigitBN[6] = {16, 32, 48, 64, 80, 96};
 inline bool digit_bn_ok(int BN, int nd) {
-    return (BN == 16 || BN == 32 || BN == 48 || BN == 64 || BN == 80) && nd * BN <= 512;
+    return (BN == 16 || BN == 32 || BN == 48 || BN == 64 || BN == 80 || BN == 96) && nd * BN <= 512;
 }
 inline int digit_nbuf(int BN, int nd) { return 2 * nd * BN <= 512 ? 2 : 1; }
 

@@ -502,9 +502,9 @@ int fast_prepare(nof_ctx* c) {
     NOF_LAUNCH_CHECK();
 
     // ---- autotuned plans ----------------------------------------------------------------
-    int bns[5];
+    int bns[6];
     const int nbn = bn_candidates(ap, nd, bns);
-    DigitGemmPlan cand[20];
+    DigitGemmPlan cand[24];
     int best = 0;
     // every GEMM takes its tiles dynamically (a CTA that starts late, behind the side stream's
     // blocks, takes fewer tiles)
@@ -536,7 +536,7 @@ int fast_prepare(nof_ctx* c) {
         // (summed afterwards in a fixed order, so results do not depend on scheduling)
         const long long na = (long long)n * a;
         const long long max_chunks = ((long long)1 << 31) / 8 / na;  // at most 2 GiB of partials
-        int k = 0, bnk[20], chk[20];  // at most 5 widths x 4 chunks
+        int k = 0, bnk[24], chk[24];  // at most 6 widths x 4 chunks
         for (int i = 0; i < nbn; ++i) {
             // per tile width, the four longest chunks (8 * 2^i atoms, or all of K) that still give
             // half a wave of tiles (longer chunks mean fewer partials and less per-tile overhead)

@@ -50,6 +50,9 @@ def _bound(nd, katoms):
     (257, 100, 80, 24, 9, 4),    # 4 digits, BN 80, split-K (9, 9, 6), ragged last tile (100 = 80 + 20)
     (130, 1000, 80, 64, 64, 5),  # 5 digits, BN 80, 13 N tiles (the last 40 of 80), four scale parts
     (257, 100, 80, 24, 24, 4),   # 4 digits, BN 80, three scale parts of 8 atoms
+    (300, 208, 96, 38, 38, 5),   # 5 digits, BN 96 (48-column halves), last tile 16 of 96 columns
+    (130, 1000, 96, 64, 64, 5),  # 5 digits, BN 96, 11 N tiles, four scale parts
+    (257, 100, 96, 24, 9, 4),    # 4 digits, BN 96, split-K (9, 9, 6)
 ])
 def test_digit_gemm_exact(M, N, bn, katoms, chunk, nd):
     """The int64 output (single CTAs, round-robin and dynamic tiles) within the last levels' rounding

@@ -51,5 +51,5 @@ def test_h200_energy_gradients(h200, precision):
     assert np.max(np.abs(gg.cpu().numpy() - ref["g_gamma"])) < GATE
     if precision == 1:
         bn1, bn2, bn3, chunk = ctx.tuned_tiles()
-        assert {bn1, bn2, bn3} <= {16, 32, 48, 64, 80} and chunk >= 8
+        assert {bn1, bn2, bn3} <= {16, 32, 48, 64, 80, 96} and chunk >= 8
     ctx.close()
