@@ -38,6 +38,7 @@ struct FastState {
     uint16_t* Td3; int* epT;    // [4][8 nkp][n][16] (K = (P, r) padded to nkp parts), scale per (part, mu)
     float2* bdf;                // [X ap][ap] b^P_{p q} as double-floats
     float2* Ddf;                // [X][a] D^P_p = sum_r A_pr d^P_r
+    float2* dg;                 // [X][a] d^P_p = b^P_pp, contiguous (read by the J/K partials)
     uint16_t* Wd3; int* epW;    // rows p (tiles of bn3), K = (P, r); scale per (part, p)
     float2 *Adf, *Bcdf;         // [a][a]
     double *Jpart, *Kpart;      // [nchunkJK][a a]
@@ -267,11 +268,22 @@ __device__ __forceinline__ float2 b_val(const float2* bdf, int ap, int P, int p,
     return bdf[((long long)P * ap + p) * ap + q];
 }
 
+// d^P_p = b^P_pp for P < X, p < a into a contiguous [X][a] array (one thread per element)
+__global__ void __launch_bounds__(256) k_diag(const float2* __restrict__ bdf, int X, int a, int ap,
+                                              float2* __restrict__ dg) {
+    const long long i = blockIdx.x * 256LL + threadIdx.x;
+    if (i >= (long long)X * a) return;
+    const int P = (int)(i / a), p = (int)(i - (long long)P * a);
+    dg[i] = b_val(bdf, ap, P, p, p);
+}
+
 // Partial sums over one chunk of aux indices: J_pq += d_p d_q, K_pq += (b_pq)^2 (double-float),
-// with d^P_p = b^P_pp read from b (and stored contiguously in d); grid (ceil(a*a/256), nchunk);
-// partials [chunk][a*a] as FP64.
-__global__ void __launch_bounds__(256) k_JK_partial(const float2* bdf, int X, int a, int ap, int nchunk,
-                                                    double* Jpart, double* Kpart) {
+// with d^P read from the contiguous diagonals (a warp's q are consecutive: every read is
+// coalesced or a broadcast); grid (ceil(a*a/256), nchunk); partials [chunk][a*a] as FP64. The
+// sums run over P in order; the loads of four consecutive P are issued together.
+__global__ void __launch_bounds__(256) k_JK_partial(const float2* __restrict__ bdf, const float2* __restrict__ dg,
+                                                    int X, int a, int ap, int nchunk, double* Jpart,
+                                                    double* Kpart) {
     const int idx = blockIdx.x * 256 + threadIdx.x;
     const int aa = a * a;
     if (idx >= aa) return;
@@ -279,10 +291,12 @@ __global__ void __launch_bounds__(256) k_JK_partial(const float2* bdf, int X, in
     const int len = (X + nchunk - 1) / nchunk;
     const int P0 = blockIdx.y * len, P1 = min(X, P0 + len);
     float2 jacc = make_float2(0.f, 0.f), kacc = make_float2(0.f, 0.f);
+#pragma unroll 4
     for (int P = P0; P < P1; ++P) {
-        float2 b = b_val(bdf, ap, P, p, q);
+        const float2 b = b_val(bdf, ap, P, p, q);
+        const float2 dp = dg[(long long)P * a + p], dq = dg[(long long)P * a + q];
         kacc = df_add(kacc, df_mul(b, b));
-        jacc = df_add(jacc, df_mul(b_val(bdf, ap, P, p, p), b_val(bdf, ap, P, q, q)));
+        jacc = df_add(jacc, df_mul(dp, dq));
     }
     Jpart[(long long)blockIdx.y * aa + idx] = df_to_double(jacc);
     Kpart[(long long)blockIdx.y * aa + idx] = df_to_double(kacc);
@@ -425,7 +439,7 @@ int fast_release(nof_ctx* c) {
     FastState* f = c->fast;
     if (!f) return NOF_OK;
     ffree(f->Bd); ffree(f->eB); ffree(f->Cd1); ffree(f->Cd2); ffree(f->eC); ffree(f->Tdf); ffree(f->colT);
-    ffree(f->Td2); ffree(f->e2); ffree(f->Td3); ffree(f->epT); ffree(f->bdf); ffree(f->Ddf);
+    ffree(f->Td2); ffree(f->e2); ffree(f->Td3); ffree(f->epT); ffree(f->bdf); ffree(f->Ddf); ffree(f->dg);
     ffree(f->Wd3); ffree(f->epW); ffree(f->Adf); ffree(f->Bcdf); ffree(f->Jpart); ffree(f->Lpart);
     ffree(f->Kpart); ffree(f->tctr);
     delete f;
@@ -478,7 +492,7 @@ int fast_prepare(nof_ctx* c) {
     NOF_TRY(falloc(&f->Td2, nTd2)); NOF_TRY(falloc(&f->e2, rows2));
     NOF_TRY(falloc(&f->Td3, nTd3)); NOF_TRY(falloc(&f->epT, (size_t)nkp * n));
     NOF_TRY(falloc(&f->bdf, rows2 * ap));
-    NOF_TRY(falloc(&f->Ddf, (size_t)X * a));
+    NOF_TRY(falloc(&f->Ddf, (size_t)X * a)); NOF_TRY(falloc(&f->dg, (size_t)X * a));
     NOF_TRY(falloc(&f->Wd3, nWd3)); NOF_TRY(falloc(&f->epW, (size_t)nkp * a));
     NOF_TRY(falloc(&f->Adf, (size_t)a * a)); NOF_TRY(falloc(&f->Bcdf, (size_t)a * a));
     NOF_TRY(falloc(&f->Jpart, (size_t)f->nchunkJK * a * a)); NOF_TRY(falloc(&f->Kpart, (size_t)f->nchunkJK * a * a));
@@ -636,8 +650,10 @@ int b_chain(nof_ctx* c, const double* C, cudaEvent_t t_written) {
 int jk_from_b(nof_ctx* c, cudaStream_t s) {
     FastState* f = c->fast;
     const int a = f->a, nchunk = f->nchunkJK;
-    k_JK_partial<<<dim3(nblk((long long)a * a), nchunk), 256, 0, s>>>(f->bdf, f->X, a, f->ap, nchunk, f->Jpart,
-                                                                     f->Kpart);
+    k_diag<<<nblk((long long)f->X * a), 256, 0, s>>>(f->bdf, f->X, a, f->ap, f->dg);
+    NOF_LAUNCH_CHECK();
+    k_JK_partial<<<dim3(nblk((long long)a * a), nchunk), 256, 0, s>>>(f->bdf, f->dg, f->X, a, f->ap, nchunk,
+                                                                     f->Jpart, f->Kpart);
     NOF_LAUNCH_CHECK();
     k_reduce_parts<<<dim3(nblk((long long)a * a * 32), 2), 256, 0, s>>>(f->Jpart, c->J, f->Kpart, c->K, nchunk,
                                                                        a * a, f->colT, (long long)f->X * f->ap);
