@@ -130,6 +130,18 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// x 2^e for a double-float x, as (x 2^{e1}) 2^{e2} with e1 = floor(e / 2), e2 = e - e1: once e is
+// clamped to [-252, 252] both factors are normal powers of two. The intermediate lies between x
+// and the result, so every normal result is exact, the same as with ldexpf (only subnormal
+// results can round twice); beyond the clamp every nonzero result is 0 or infinite either way.
+// No branch and no library call per element.
+__device__ __forceinline__ float2 scale_df(float2 x, int e) {
+    e = min(max(e, -252), 252);
+    const int e1 = e >> 1, e2 = e - e1;
+    const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
+    return make_float2((x.x * s1) * s2, (x.y * s1) * s2);
+}
+
 // 2^{e} sum_l S_l 256^{ND-1-l} as a double-float, for level sums S_l that are exact integers
 // below 2^24 held in FP32: each scaled level is exact, and error-free two-sums collect the total
 // (no integer conversions).
@@ -146,16 +158,27 @@ __device__ __forceinline__ float2 levels_to_df(const float* S, int e) {
         h = h2;
     }
     const float hi = h + err;
-    const float lo = err - (hi - h);
-    // x 2^e as (x 2^{e1}) 2^{e2} with e1 = floor(e / 2), e2 = e - e1: once e is clamped to
-    // [-252, 252] both factors are normal powers of two. The intermediate lies between x and the
-    // result, so every normal result is exact, the same as with ldexpf (only subnormal results
-    // can round twice); beyond the clamp every nonzero result is 0 or infinite either way.
-    // No branch and no library call per element.
-    e = min(max(e, -252), 252);
-    const int e1 = e >> 1, e2 = e - e1;
-    const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
-    return make_float2((hi * s1) * s2, (lo * s1) * s2);
+    return scale_df(make_float2(hi, err - (hi - h)), e);
+}
+
+// The int64 V (|V| < 2^63) as a double-float times 2^e: V = a 2^42 + b 2^21 + c with |a| < 2^21
+// and 0 <= b, c < 2^21, each exact in FP32 (32-bit conversions; 64-bit ones run at the FP64 rate
+// here), collected by error-free two-sums (relative error near 2^-48).
+__device__ __forceinline__ float2 int_to_df(long long V, int e) {
+    const long long a = V >> 42;
+    const long long r = V - (a << 42);
+    const float c1 = (float)(int)(r >> 21) * 2097152.0f, c2 = (float)(int)(r & 2097151);
+    float h = (float)(int)a * 4398046511104.0f;
+    float err = 0.f;
+    float h2 = h + c1, bb = h2 - h;
+    err += (h - (h2 - bb)) + (c1 - bb);
+    h = h2;
+    h2 = h + c2;
+    bb = h2 - h;
+    err += (h - (h2 - bb)) + (c2 - bb);
+    h = h2;
+    const float hi = h + err;
+    return scale_df(make_float2(hi, err - (hi - h)), e);
 }
 
 // a double-float in the bits of one 64-bit register (hi in the low word, lo in the high word)
@@ -203,7 +226,9 @@ constexpr int kMaxColsOf(int BN) { return BN > 80 ? 48 : 40; }
 constexpr int kTileQ = 4;     // tile-index queue slots (dynamic tiles)
 
 
-template <int ND, int kMaxCols>
+// kPS: per-part scales (the Lagrangian contraction), a separate instantiation so that each output
+// mode's epilogue gets the registers to itself
+template <int ND, int kMaxCols, bool kPS>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
 k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, DigitGemmArgs g) {
     // 32-byte swizzling repeats every 256 bytes: every operand block starts on a 256-byte boundary
@@ -410,8 +435,10 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
             const int rbase = tm * kBM + q * 32;
             const int row = rbase + lane;  // this lane's output row
             const int col0 = tn * BN + cbeg;  // global column of this warp's column 0
-            const bool partsc = g.epA != nullptr;
-            const bool ints = !g.outf && !partsc;  // exact int64 sums
+            constexpr bool partsc = kPS;
+            // exact int64 sums over the parts (the int64 output, and the scaled output when V fits:
+            // one conversion to a scaled double-float per tile instead of one per part)
+            const bool ints = !partsc && (!g.outf || g.isum);
             constexpr int kOff = 8 * (ND + 1);  // value = 2^{e_row + e_col - 8 (ND + 1)} V
             const int er = (g.outf && row < g.M) ? g.erow[row] - kOff : 0;
             // running sums of this lane's row over the parts, in registers: the int64 V, or the bits
@@ -474,6 +501,13 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
             }
             if (!ok) break;
             const int ncol = min(cw, g.Nvalid - col0);  // valid columns of this warp (warp-uniform)
+            if (ints && g.outf) {  // the int64 sums as scaled double-floats, in place
+#pragma unroll
+                for (int c = 0; c < kMaxCols; ++c) {
+                    if (c >= ncol) break;
+                    acc[c] = pack_df(int_to_df(acc[c], er + g.ecol[col0 + c]));
+                }
+            }
             // each lane writes its own row: 16-byte stores of column pairs (double-floats) or one
             // element at a time (int64, FP64 partials, atomics)
             if (ncol > 0 && row < g.M) {
@@ -565,6 +599,29 @@ size_t smem_bytes(int BN, int stages, int nd) {
 
 }  // namespace
 
+namespace {
+template <bool PS>
+int set_smem_limits() {
+    NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<4, 40, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<5, 40, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<4, 48, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<5, 48, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    return NOF_OK;
+}
+template <bool PS>
+void launch_digit_gemm(const DigitGemmPlan& p, cudaStream_t st) {
+    const dim3 blk(64 + 32 * kEpiWarps);
+    const bool wide = kMaxColsOf(p.g.BN) == 48;
+    if (p.g.nd == 5) {
+        if (wide) k_digit_gemm<5, 48, PS><<<p.grid, blk, p.smem, st>>>(p.A, p.B, p.g);
+        else k_digit_gemm<5, 40, PS><<<p.grid, blk, p.smem, st>>>(p.A, p.B, p.g);
+    } else {
+        if (wide) k_digit_gemm<4, 48, PS><<<p.grid, blk, p.smem, st>>>(p.A, p.B, p.g);
+        else k_digit_gemm<4, 40, PS><<<p.grid, blk, p.smem, st>>>(p.A, p.B, p.g);
+    }
+}
+}  // namespace
+
 int digit_gemm_max_stages(int BN, int nd) {
     int s = 2;
     while (s < 8 && smem_bytes(BN, s + 1, nd) <= kSmemLimit) ++s;
@@ -587,7 +644,8 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
     }
     // the exact int64 result of one output element: per K element |V| <= 65536 256^{nd-1} (1 +
     // 2^-8 + 1.25 2^-16 + ...) < 1.004 * 2^16 * 256^{nd-1}; keep the K sum below 2^63
-    if (o.out && (double)katoms_total * 16.0 * 1.004 * 65536.0 * std::pow(256.0, nd - 1) > 9.0e18) {
+    const bool v_fits = (double)katoms_total * 16.0 * 1.004 * 65536.0 * std::pow(256.0, nd - 1) <= 9.0e18;
+    if (o.out && !v_fits) {
         nof_set_error("digit_gemm: K too long for an exact int64 sum");
         return NOF_EINVAL;
     }
@@ -622,6 +680,8 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
     g.tmem_cols = cols;
     g.out = o.out;
     g.outf = o.outf;
+    // (with one part per tile a double-float sum is cheaper than a conversion at the end)
+    g.isum = (o.outf && v_fits && g.katoms > g.apart) ? 1 : 0;
     g.outd = o.outd;
     g.chunk_stride = o.chunk_stride;
     g.ldo = o.ldo;
@@ -649,10 +709,8 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
         int dev = 0;
         NOF_CUDA(cudaGetDevice(&dev));
         NOF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<4, 40>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<5, 40>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<4, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
-        NOF_CUDA(cudaFuncSetAttribute(k_digit_gemm<5, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+        NOF_TRY(set_smem_limits<false>());
+        NOF_TRY(set_smem_limits<true>());
     }
     const long long ntiles = (long long)g.tiles_n * g.tiles_m * g.kchunks;
     if (ntiles > 0x7fffffffLL) {
@@ -664,15 +722,8 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
 }
 
 int digit_gemm_run(const DigitGemmPlan& p, cudaStream_t st) {
-    const dim3 blk(64 + 32 * kEpiWarps);
-    const bool wide = kMaxColsOf(p.g.BN) == 48;
-    if (p.g.nd == 5) {
-        if (wide) k_digit_gemm<5, 48><<<p.grid, blk, p.smem, st>>>(p.A, p.B, p.g);
-        else k_digit_gemm<5, 40><<<p.grid, blk, p.smem, st>>>(p.A, p.B, p.g);
-    } else {
-        if (wide) k_digit_gemm<4, 48><<<p.grid, blk, p.smem, st>>>(p.A, p.B, p.g);
-        else k_digit_gemm<4, 40><<<p.grid, blk, p.smem, st>>>(p.A, p.B, p.g);
-    }
+    if (p.g.epA) launch_digit_gemm<true>(p, st);
+    else launch_digit_gemm<false>(p, st);
     NOF_LAUNCH_CHECK();
     return NOF_OK;
 }

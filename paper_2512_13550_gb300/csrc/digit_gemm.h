@@ -33,6 +33,7 @@ struct DigitGemmArgs {
     // scaled output: when outf != nullptr the result 2^{erow[m] + ecol[n] - 40} V is stored as a
     // double-float (float2: hi, lo) at outf[m * ldo + n] instead of the int64 V
     float2* outf;
+    int isum;          // scaled output summed over the parts as int64 V (set when |V| < 2^63 is certain)
     const int* erow;
     const int* ecol;
     // per-part scales: when epA != nullptr the value of part gp (atoms [gp apart, (gp+1) apart)
