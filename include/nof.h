@@ -364,8 +364,9 @@ int nof_selftest_digit_gemm(int M, int N, int bn, int nd, int katoms, int chunk_
  * measurement only): M x N output, N tiles of bn, nd digits, K = 16 katoms in chunks of
  * chunk_atoms. mode 0: exact int64 output (split-K atomics when chunk_atoms < katoms);
  * 1: scaled double-float output (one chunk); 2: per-part scales with an FP64 partial per K chunk
- * (chunk_atoms a multiple of digit_scale_part_atoms: 16 atoms with 5 digits, 8 with 4). Flags added to `mode`: 4 = each launch timed alone after a
- * 256 MiB write (L2 flushed, operands from HBM); 8 = tiles taken dynamically from a
+ * (chunk_atoms a multiple of digit_scale_part_atoms: 20 atoms with 5 digits, 8 with 4). Flags
+ * added to `mode`: 4 = each launch timed alone after a 256 MiB write (L2 flushed, operands from
+ * HBM); 8 = tiles taken dynamically from a
  * fetch-and-add counter instead of round-robin. One warm-up, then the mean of `reps` launches
  * timed with CUDA events on the default stream into *us_per_launch (host). Allocates and frees
  * its own buffers (the flush buffer is kept for the life of the process). */

@@ -124,9 +124,10 @@ __host__ __device__ inline int digit_top(int nd) { return nd == 5 ? 128 : 256; }
 // (4 digits) receives at most 2 256 128: 256 elements, 16 atoms.
 inline int digit_part_atoms_max(int nd) { return nd == 5 ? 20 : 16; }
 // K atoms of one part of the per-part scales (the Lagrangian contraction, whose K runs over every
-// aux index): longer parts mean fewer accumulator drains, shorter ones finer scales; 4 digits,
-// which have less precision to spare, take the finer scales.
-inline int digit_scale_part_atoms(int nd) { return nd == 5 ? 16 : 8; }
+// aux index): longer parts mean fewer accumulator drains (each part is drained and scaled on its
+// own), shorter ones finer scales; 5 digits take the longest exact part, 4 digits, which have
+// less precision to spare, the finer scales.
+inline int digit_scale_part_atoms(int nd) { return nd == 5 ? 20 : 8; }
 
 // A launch plan (pointers and shapes fixed at set-up).
 struct DigitGemmPlan {

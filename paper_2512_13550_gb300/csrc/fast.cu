@@ -665,8 +665,8 @@ int jk_from_b(nof_ctx* c, cudaStream_t s) {
 int t3_digits(nof_ctx* c, cudaStream_t s) {
     FastState* f = c->fast;
     const dim3 grid(f->nkp, (f->n + 7) / 8);
-    if (f->patoms == 16)
-        k_T3_digits<16><<<grid, 256, 0, s>>>(f->Tdf, f->X, f->n, f->ap, f->nkp, f->nd, f->Td3, f->epT);
+    if (f->patoms == 20)
+        k_T3_digits<20><<<grid, 320, 0, s>>>(f->Tdf, f->X, f->n, f->ap, f->nkp, f->nd, f->Td3, f->epT);
     else
         k_T3_digits<8><<<grid, 128, 0, s>>>(f->Tdf, f->X, f->n, f->ap, f->nkp, f->nd, f->Td3, f->epT);
     NOF_LAUNCH_CHECK();
@@ -682,8 +682,8 @@ int w_digits(nof_ctx* c) {
     k_D_df<<<dim3((a + 15) / 16, (X + 15) / 16), 256, 0, st>>>(f->Adf, f->bdf, X, a, ap, f->Ddf);
     NOF_LAUNCH_CHECK();
     const dim3 grid(f->nkp, (a + 7) / 8);
-    if (f->patoms == 16)
-        k_W_digits<16><<<grid, 256, 0, st>>>(f->bdf, f->Bcdf, f->Ddf, X, a, ap, f->nkp, f->nd, f->bn3, f->Wd3, f->epW);
+    if (f->patoms == 20)
+        k_W_digits<20><<<grid, 320, 0, st>>>(f->bdf, f->Bcdf, f->Ddf, X, a, ap, f->nkp, f->nd, f->bn3, f->Wd3, f->epW);
     else
         k_W_digits<8><<<grid, 128, 0, st>>>(f->bdf, f->Bcdf, f->Ddf, X, a, ap, f->nkp, f->nd, f->bn3, f->Wd3, f->epW);
     NOF_LAUNCH_CHECK();

@@ -48,10 +48,10 @@ def _bound(nd, katoms):
     (256, 48, 48, 41, 41, 5),    # 5 digits, K = 656: three parts (14 + 14 + 13), odd count
     (300, 208, 80, 38, 38, 5),   # 5 digits, BN 80 (40-column halves), one TMEM set, ragged last tile
     (257, 100, 80, 24, 9, 4),    # 4 digits, BN 80, split-K (9, 9, 6), ragged last tile (100 = 80 + 20)
-    (130, 1000, 80, 64, 64, 5),  # 5 digits, BN 80, 13 N tiles (the last 40 of 80), four scale parts
+    (130, 1000, 80, 60, 60, 5),  # 5 digits, BN 80, 13 N tiles (the last 40 of 80), three scale parts
     (257, 100, 80, 24, 24, 4),   # 4 digits, BN 80, three scale parts of 8 atoms
     (300, 208, 96, 38, 38, 5),   # 5 digits, BN 96 (48-column halves), last tile 16 of 96 columns
-    (130, 1000, 96, 64, 64, 5),  # 5 digits, BN 96, 11 N tiles, four scale parts
+    (130, 1000, 96, 80, 80, 5),  # 5 digits, BN 96, 11 N tiles, four scale parts
     (257, 100, 96, 24, 9, 4),    # 4 digits, BN 96, split-K (9, 9, 6)
 ])
 def test_digit_gemm_exact(M, N, bn, katoms, chunk, nd):
