@@ -545,22 +545,25 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                 }
             }
             // column maxima of |value| per group of rows (GEMM1: per aux function; atomics without a
-            // return value: nothing waits). When the warp's valid rows lie in one group, a
-            // transposing butterfly over 32 columns at a time (steps 16, 8, 4, 2, 1: each lane keeps
-            // half of its columns and takes the partner's maxima of them) leaves lane c with column
-            // c's maximum, and one atomic per lane follows: 31 shuffles and one atomic instruction
-            // per 32 columns.
-            const bool one_group = rbase / g.group_rows == (min(rbase + 31, g.M - 1)) / g.group_rows;
-            if (!partsc && g.outf && g.colmax && ncol > 0 && rbase < g.M && one_group) {
-                const int grp = rbase / g.group_rows;
+            // return value: nothing waits). When the warp's valid rows lie in at most four groups,
+            // then for each group a transposing butterfly over 32 columns at a time (steps 16, 8,
+            // 4, 2, 1: each lane keeps half of its columns and takes the partner's maxima of them;
+            // rows of the other group count as 0) leaves lane c with column c's maximum, and one
+            // atomic per lane follows: 31 shuffles and one atomic instruction per 32 columns.
+            const int g_first = rbase / g.group_rows, g_last = min(rbase + 31, g.M - 1) / g.group_rows;
+            const bool few_groups = g_last - g_first <= 3;
+            for (int grp = g_first; !partsc && g.outf && g.colmax && ncol > 0 && rbase < g.M && few_groups &&
+                                    grp <= g_last;
+                 ++grp) {
+                const bool mine = row < g.M && row / g.group_rows == grp;
 #pragma unroll
                 for (int cb = 0; cb < kMaxCols; cb += 32) {
                     if (cb >= ncol) break;
                     float v[32];
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
-                        v[i] = (cb + i < kMaxCols && cb + i < ncol && row < g.M) ? fabsf(unpack_df(acc[cb + i < kMaxCols ? cb + i : 0]).x)
-                                                                                  : 0.f;
+                        v[i] = (cb + i < kMaxCols && cb + i < ncol && mine) ? fabsf(unpack_df(acc[cb + i < kMaxCols ? cb + i : 0]).x)
+                                                                             : 0.f;
 #pragma unroll
                     for (int sft = 16; sft >= 1; sft >>= 1) {
                         const bool up = (lane & sft) != 0;
@@ -575,10 +578,10 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                         atomicMax(g.colmax + (long long)grp * g.Nvalid + col0 + cb + lane, __float_as_uint(v[0]));
                 }
             }
-            // otherwise a segmented reduction over the lanes: groups are runs of consecutive rows, so
-            // after steps 1, 2, 4, 8, 16 that only take a lane's value from a lane of the same group,
-            // the first lane of each run holds the run's maximum
-            if (!partsc && g.outf && g.colmax && ncol > 0 && rbase < g.M && !one_group) {
+            // otherwise (groups of fewer than 11 rows) a segmented reduction over the lanes: groups are
+            // runs of consecutive rows, so after steps 1, 2, 4, 8, 16 that only take a lane's value
+            // from a lane of the same group, the first lane of each run holds the run's maximum
+            if (!partsc && g.outf && g.colmax && ncol > 0 && rbase < g.M && !few_groups) {
                 const int grp = row / g.group_rows;
                 unsigned same = 0;
 #pragma unroll
