@@ -551,9 +551,13 @@ int fast_prepare(nof_ctx* c) {
         const long long na = (long long)n * a;
         const long long max_chunks = ((long long)1 << 31) / 8 / na;  // at most 2 GiB of partials
         int k = 0, bnk[24], chk[24];  // at most 6 widths x 4 chunks
+        int dev = 0, sms = 0;
+        NOF_CUDA(cudaGetDevice(&dev));
+        NOF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         for (int i = 0; i < nbn; ++i) {
-            // per tile width, the four longest chunks (8 * 2^i atoms, or all of K) that still give
-            // half a wave of tiles (longer chunks mean fewer partials and less per-tile overhead)
+            // per tile width, the three longest chunks (patoms 2^i atoms, or all of K) that still give
+            // half a wave of tiles (longer chunks mean fewer partials and less per-tile overhead),
+            // and the chunk whose tiles best fill whole waves of the SMs
             const long long tmn = (long long)((n + 127) / 128) * ((a + bns[i] - 1) / bns[i]);
             int all[24], na2 = 0;
             for (long long ch = patoms; na2 < 24; ch *= 2) {
@@ -561,13 +565,34 @@ int fast_prepare(nof_ctx* c) {
                 if (ch >= kat3) break;
             }
             int nch = 0;
-            for (int j = na2 - 1; j >= 0 && nch < 4; --j) {
+            for (int j = na2 - 1; j >= 0 && nch < 3; --j) {
                 const long long kch = (kat3 + all[j] - 1) / all[j];
                 if (kch > max_chunks) break;
                 if (tmn * kch < 76 && j > 0) continue;
                 chk[k] = all[j];
                 bnk[k++] = bns[i];
                 ++nch;
+            }
+            // balance: a wave of sms tiles takes about one chunk's time, so the efficiency of c
+            // chunks of ch atoms is tmn kat3 / (sms waves ch); the best, then the fewest chunks
+            long long bch = 0;
+            double beff = 0.0;
+            for (long long c = 1; c <= max_chunks && c <= 64; ++c) {  // at most 64 partials
+                const long long ch = ((kat3 + c - 1) / c + patoms - 1) / patoms * patoms;
+                const long long kch = (kat3 + ch - 1) / ch;
+                if (kch != c || tmn * kch < 76) continue;
+                const long long waves = (tmn * kch + sms - 1) / sms;
+                const double eff = (double)tmn * kat3 / ((double)sms * waves * ch);
+                if (eff > beff + 0.005) {
+                    beff = eff;
+                    bch = ch;
+                }
+            }
+            bool have = bch == 0;
+            for (int j = k - nch; j < k; ++j) have = have || chk[j] == bch;
+            if (!have) {
+                chk[k] = (int)bch;
+                bnk[k++] = bns[i];
             }
         }
         if (k == 0) {
