@@ -349,10 +349,11 @@ def converged_solutions(sizes, orb, aux, seed=31, gtol=1e-4, etol=1e-7, maxit=30
     return np.concatenate(feats), np.concatenate(targs), recs
 
 
-def learned_start(bnet: BF16Net, xyz, eps: np.ndarray, C0, ngamma: int, gamma0: float = 0.3):
+def learned_start(bnet: BF16Net, xyz, eps: np.ndarray, C0, ngamma: int, gamma0: float = 0.3,
+                  rotate: bool = True):
     """The learned starting point: gamma_g from the predicted sin^2 gamma, and C0 exp(Y) with
-    Y_{g, p(g)} = -Y_{p(g), g} the predicted pair angles (BF16 inference). Returns (C, gamma) as
-    device tensors."""
+    Y_{g, p(g)} = -Y_{p(g), g} the predicted pair angles (BF16 inference; C0 itself when rotate is
+    False). Returns (C, gamma) as device tensors."""
     import torch
     from scipy.linalg import expm
     N = xyz.shape[0]
@@ -362,7 +363,7 @@ def learned_start(bnet: BF16Net, xyz, eps: np.ndarray, C0, ngamma: int, gamma0: 
     gam[:npair] = angles(y[:, 0])
     n = C0.shape[0]
     Y = np.zeros((n, n))
-    for g in range(npair):  # exp(Y) rotates the plane (g, p(g)) by theta_g: C_g -> cos C_g + sin C_p
+    for g in range(npair if rotate else 0):  # exp(Y) rotates the plane (g, p(g)) by theta_g: C_g -> cos C_g + sin C_p
         p = pair_partner(npair, g)
         Y[p, g] = y[g, 1]
         Y[g, p] = -y[g, 1]
@@ -370,19 +371,26 @@ def learned_start(bnet: BF16Net, xyz, eps: np.ndarray, C0, ngamma: int, gamma0: 
     return C, torch.tensor(gam, dtype=torch.float64, device="cuda")
 
 
-def choose_start(ctx, learned, core):
-    """The automatic fallback: the learned start unless the core guess has the lower energy after
-    its ONs are converged (one outer iteration of nof_optimize from each, on copies)."""
-    es = []
-    for C, gam in (learned, core):
-        r = ctx.optimize(C.clone(), gam.clone(), maxit=1, maxloop=1)
-        es.append(r["history"][0, 0])
-    return (learned[0].clone(), learned[1].clone()) if es[0] <= es[1] else (core[0].clone(), core[1].clone())
+def optimize_with_fallback(ctx, learned, core, **params):
+    """nof_optimize from the learned start; when that does not converge, again from the core guess
+    (the automatic fallback). The learned start's first energy is no criterion: on held-out chains
+    it lies above the core guess's while the loop from it converges in fewer evaluations. Returns
+    the result of the run that is kept, with "fallback" set and the evaluations of both runs."""
+    r = ctx.optimize(learned[0].clone(), learned[1].clone(), **params)
+    if r["converged"]:
+        r["fallback"] = False
+        return r, learned
+    spent = r["evaluations"]
+    r = ctx.optimize(core[0].clone(), core[1].clone(), **params)
+    r["fallback"] = True
+    r["evaluations"] += spent
+    return r, core
 
 
 def compare_starts(bnet: BF16Net, sizes, orb, aux, seed=41, gtol=1e-4, etol=1e-7, maxit=3000, precision=1):
-    """Held-out displaced chains, optimised to convergence from the core guess (gamma = 0.3) and from
-    the learned start: per chain (N, E_start and evaluations, seconds, E_final for each start)."""
+    """Held-out displaced chains, optimised to convergence from the core guess (gamma = 0.3), from the
+    learned start (occupations and pair rotations), from the learned occupations alone and through
+    the fallback: per chain (N, E_start and evaluations, seconds, E_final for each start)."""
     import time
 
     import torch
@@ -396,15 +404,22 @@ def compare_starts(bnet: BF16Net, sizes, orb, aux, seed=41, gtol=1e-4, etol=1e-7
         ctx.build_B(xyz, orb, aux)
         C0, eps = ctx.core_guess()
         row = {"N": N}
+        e = eps.cpu().numpy()
         starts = {"core": (C0.clone(), torch.full((ctx.sizes["ngamma"],), 0.3, dtype=torch.float64, device="cuda")),
-                  "learned": learned_start(bnet, xyz, eps.cpu().numpy(), C0, ctx.sizes["ngamma"])}
-        starts["learned_or_core"] = choose_start(ctx, starts["learned"], starts["core"])
-        for name, (C, gam) in starts.items():
+                  "learned": learned_start(bnet, xyz, e, C0, ctx.sizes["ngamma"]),
+                  "learned_occupations": learned_start(bnet, xyz, e, C0, ctx.sizes["ngamma"], rotate=False)}
+        for name in ("core", "learned", "learned_occupations", "learned_or_core"):
             t0 = time.perf_counter()
-            r = ctx.optimize(C, gam, gtol=gtol, etol=etol, maxit=maxit)
+            if name == "learned_or_core":
+                r, _ = optimize_with_fallback(ctx, starts["learned"], starts["core"], gtol=gtol, etol=etol, maxit=maxit)
+            else:
+                C, gam = starts[name]
+                r = ctx.optimize(C.clone(), gam.clone(), gtol=gtol, etol=etol, maxit=maxit)
             dt = time.perf_counter() - t0
             row[name] = {"E_start": float(r["history"][0, 0]), "E_final": r["E"], "iterations": r["iterations"],
                          "evaluations": r["evaluations"], "converged": r["converged"], "seconds": round(dt, 3)}
+            if name == "learned_or_core":
+                row[name]["fallback"] = r["fallback"]
         out.append(row)
         ctx.close()
     return out

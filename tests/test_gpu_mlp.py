@@ -85,22 +85,26 @@ def test_bf16_inference_matches_oracle_forward():
     assert np.max(np.abs(Y32 - ref)) < 1e-5 * scale
 
 
-def test_learned_start_from_converged_solutions():
-    """Trained on converged solutions of displaced chains (occupations and pair rotation angles from
-    nof_optimize), the BF16 network proposes starts on held-out chains; every start converges, the
-    start with the automatic fallback is never above the core guess's first energy, and the
-    evaluations each start needed are reported."""
+@pytest.mark.slow
+def test_learned_start_from_converged_solutions_saves_evaluations():
+    """Trained on 300 converged solutions of displaced H6-H40 chains (occupations and pair rotation
+    angles from nof_optimize), the BF16 network's start converges on held-out H24, H40 and H64 to
+    the core guess's minimum or a lower one, in fewer evaluations in total; the start with the
+    automatic fallback converges too. The rows (E_start, E_final, iterations, evaluations per start)
+    are printed."""
     from paper_2512_13550_gb300 import learned
     orb, aux = inputs.basis_3s_10aux()
-    X, T, recs = learned.converged_solutions(inputs.batch_sizes(24, seed=21, lo=6, hi=20), orb, aux, seed=31)
+    X, T, recs = learned.converged_solutions(inputs.batch_sizes(300, seed=21, lo=6, hi=40), orb, aux, seed=31)
     assert all(r[3] for r in recs)
     net = learned.MLP(learned.NFEAT, 256, learned.NOUT, seed=0)
-    hist = learned.train(net, X, T, iters=800, lr=1e-3, wd=0.3)
+    hist = learned.train(net, X, T, iters=1500, lr=1e-3, wd=0.3)
     assert hist[-1] < 0.5 * hist[0]
-    rows = learned.compare_starts(learned.BF16Net(net), [12, 16, 20], orb, aux)
+    rows = learned.compare_starts(learned.BF16Net(net), [24, 40, 64], orb, aux)
     for r in rows:
         print(r)
-        assert r["core"]["converged"] and r["learned"]["converged"] and r["learned_or_core"]["converged"]
-        assert r["learned_or_core"]["E_start"] <= r["core"]["E_start"] + 1e-9
-    print("evaluations, core / learned / with fallback:",
-          [(r["core"]["evaluations"], r["learned"]["evaluations"], r["learned_or_core"]["evaluations"]) for r in rows])
+        for name in ("core", "learned", "learned_occupations", "learned_or_core"):
+            assert r[name]["converged"], (r["N"], name)
+        assert r["learned"]["E_final"] <= r["core"]["E_final"] + 1e-6
+    ev = {name: sum(r[name]["evaluations"] for r in rows) for name in ("core", "learned", "learned_occupations")}
+    print("evaluations to ||g|| < 1e-4 over H24, H40, H64:", ev)
+    assert ev["learned"] < ev["core"]
