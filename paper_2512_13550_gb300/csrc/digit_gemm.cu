@@ -223,6 +223,8 @@ constexpr int kEpiWarps = 8;  // two per TMEM lane group, each owning half of th
 // columns of one epilogue warp (BN / 2 for BN >= 32, BN for BN 16), a template parameter MAXC of the
 // kernel: 40 for BN <= 80, 48 for BN 96 (whose 48 running sums leave a few registers to spill)
 constexpr int kMaxColsOf(int BN) { return BN > 80 ? 48 : 40; }
+// the staging tile of one epilogue warp: 32 rows of its columns, an odd pitch in 8-byte words
+__host__ __device__ constexpr int stage_pitch(int BN) { return (BN >= 32 ? BN / 2 : 16) + 1; }
 constexpr int kTileQ = 4;     // tile-index queue slots (dynamic tiles)
 
 
@@ -243,6 +245,8 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
     uint64_t* bars = (uint64_t*)(sB + S * b_stage_bytes);
     uint32_t* tmem_slot = (uint32_t*)(bars + 2 * S + 4 + 2 * kTileQ);
     volatile int* tq_id = (volatile int*)(tmem_slot + 4);  // queued tile indices (dynamic tiles)
+    // staging tiles of the epilogue warps (g.staged), 16-byte aligned after the queue
+    float2* stage_out = (float2*)(((uintptr_t)(tq_id + kTileQ) + 15) & ~(uintptr_t)15);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[S]),
                    tfull0 = smem_u32(&bars[2 * S]), tempty0 = smem_u32(&bars[2 * S + 2]),
@@ -508,9 +512,37 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                     acc[c] = pack_df(int_to_df(acc[c], er + g.ecol[col0 + c]));
                 }
             }
-            // each lane writes its own row: 16-byte stores of column pairs (double-floats) or one
-            // element at a time (int64, FP64 partials, atomics)
-            if (ncol > 0 && row < g.M) {
+            if (!partsc && g.staged && ncol > 0) {
+                // single-part tiles: the warp's rows go through its staging tile, and consecutive
+                // lanes store along a row (cw / 2 lanes of 16-byte column pairs per row, 32 / that
+                // many rows per pass)
+                const int SP = stage_pitch(BN);
+                float2* st = stage_out + (warp - 2) * 32 * SP;
+#pragma unroll
+                for (int c = 0; c < kMaxCols; ++c) {
+                    if (c >= ncol) break;
+                    st[lane * SP + c] = unpack_df(acc[c]);
+                }
+                __syncwarp();
+                const int hp = (cw + 1) / 2;
+                const int rpp = 32 / hp, lr = lane / hp, cc = 2 * (lane - lr * hp);
+                for (int rr = lr; lr < rpp && rr < 32; rr += rpp) {
+                    const int grow = rbase + rr;
+                    if (grow >= g.M || cc >= ncol) continue;
+                    float2* dst = g.outf + (long long)grow * g.ldo + col0 + cc;  // ldo, col0, cc even
+                    const float2 x0 = st[rr * SP + cc];
+                    if (cc + 1 < ncol) {
+                        const float2 x1 = st[rr * SP + cc + 1];
+                        *reinterpret_cast<float4*>(dst) = make_float4(x0.x, x0.y, x1.x, x1.y);
+                    } else {
+                        *dst = x0;
+                    }
+                }
+                __syncwarp();
+            }
+            // otherwise each lane writes its own row: 16-byte stores of column pairs (double-floats)
+            // or one element at a time (int64, FP64 partials, atomics)
+            if (ncol > 0 && row < g.M && !(!partsc && g.staged)) {
                 if (g.out) {
                     long long* dst = g.out + (long long)row * g.ldo + col0;
 #pragma unroll
@@ -625,9 +657,9 @@ constexpr size_t kSmemLimit = 227 * 1024;
 
 // the ring of stages, the barriers, the TMEM address slot and the tile queue (the epilogue keeps its
 // sums in registers and writes from them: no staging tile)
-size_t smem_bytes(int BN, int stages, int nd) {
+size_t smem_bytes(int BN, int stages, int nd, bool staged = false) {
     return (size_t)stages * nd * kStageAtoms * 32 * (kBM + BN) + 8 * (2 * stages + 4 + 2 * kTileQ) + 16 +
-           4 * kTileQ + 16 + 256;
+           4 * kTileQ + 16 + 256 + (staged ? (size_t)kEpiWarps * 32 * stage_pitch(BN) * sizeof(float2) + 16 : 0);
 }
 
 }  // namespace
@@ -655,9 +687,9 @@ void launch_digit_gemm(const DigitGemmPlan& p, cudaStream_t st) {
 }
 }  // namespace
 
-int digit_gemm_max_stages(int BN, int nd) {
+int digit_gemm_max_stages(int BN, int nd, bool staged) {
     int s = 2;
-    while (s < 8 && smem_bytes(BN, s + 1, nd) <= kSmemLimit) ++s;
+    while (s < 8 && smem_bytes(BN, s + 1, nd, staged) <= kSmemLimit) ++s;
     return s;
 }
 
@@ -682,8 +714,13 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
         nof_set_error("digit_gemm: K too long for an exact int64 sum");
         return NOF_EINVAL;
     }
-    if (stages == 0) stages = digit_gemm_max_stages(BN, nd);
-    if (stages < 2 || smem_bytes(BN, stages, nd) > kSmemLimit) {
+    // single-part tiles of the scaled output write through a staging tile when it leaves a ring of
+    // at least 3 stages: their stores, not their one drain, dominate the epilogue
+    const int katoms_chunk = chunk_atoms < katoms_total ? chunk_atoms : katoms_total;
+    const bool staged = o.outf && katoms_chunk <= digit_part_atoms_max(nd) &&
+                        smem_bytes(BN, 3, nd, true) <= kSmemLimit && (stages == 0 || smem_bytes(BN, stages, nd, true) <= kSmemLimit);
+    if (stages == 0) stages = digit_gemm_max_stages(BN, nd, staged);
+    if (stages < 2 || smem_bytes(BN, stages, nd, staged) > kSmemLimit) {
         nof_set_error("digit_gemm: shared memory plan too large");
         return NOF_EINVAL;
     }
@@ -736,7 +773,8 @@ int digit_gemm_plan(DigitGemmPlan* p, const uint16_t* A, const uint16_t* B, int 
         nof_set_error("digit_gemm: split-K needs an atomic or per-chunk output");
         return NOF_EINVAL;
     }
-    p->smem = smem_bytes(BN, stages, nd);
+    p->smem = smem_bytes(BN, stages, nd, staged);
+    g.staged = staged ? 1 : 0;
     static int sms = 0;
     if (!sms) {
         int dev = 0;

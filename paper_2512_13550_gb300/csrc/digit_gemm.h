@@ -34,6 +34,8 @@ struct DigitGemmArgs {
     // double-float (float2: hi, lo) at outf[m * ldo + n] instead of the int64 V
     float2* outf;
     int isum;          // scaled output summed over the parts as int64 V (set when |V| < 2^63 is certain)
+    int staged;        // scaled output of single-part tiles written through a shared-memory tile (rows
+                       // stored with consecutive lanes along a row) instead of lane by lane
     const int* erow;
     const int* ecol;
     // per-part scales: when epA != nullptr the value of part gp (atoms [gp apart, (gp+1) apart)
@@ -144,7 +146,7 @@ int digit_gemm_plan(DigitGemmPlan* plan, const uint16_t* A, const uint16_t* B, i
                     int nd, int katoms_total, int chunk_atoms, int stages, const DigitGemmOut& out,
                     int* status);
 int digit_gemm_run(const DigitGemmPlan& plan, cudaStream_t st);
-int digit_gemm_max_stages(int BN, int nd);
+int digit_gemm_max_stages(int BN, int nd, bool staged = false);
 
 // Autotuner: times every candidate (one warm-up launch, then the best of three timed with CUDA
 // events on `st`; with `cold`, each timed launch follows an L2 flush, as for a GEMM whose operands
