@@ -210,15 +210,16 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
 // shared-memory slots that carries over from one tile to the next; warp 1 lane 0 issues the
 // digit-product MMAs (6 per K atom with 4 digits, 9 with 5: pairs of products share one MMA of
 // width 2 BN) of a part into one of g.nbuf TMEM accumulator sets (nd levels x BN columns); the
-// epilogue warps drain each finished part into running sums held in registers (int64 sums, or
-// double-float sums of the scaled values: each lane owns one row and up to 32 columns), hand the
-// set back, and after the last part of a tile write their rows from those registers. With two sets
-// the drain of one part overlaps the MMAs of the next; with no staging tile in shared memory the
-// ring holds one or two more stages.
+// epilogue warps drain each finished part into running sums held in registers (exact int64 sums,
+// or double-float sums of per-part-scaled values: each lane owns one row and up to 48 columns),
+// hand the set back, and after the last part of a tile write their rows (the int64 sums of the
+// scaled output converted once; single-part tiles of the scaled output through a small staging
+// tile, so that consecutive lanes store along a row). With two sets the drain of one part overlaps
+// the MMAs of the next; with one (tiles wider than 48 columns with 5 digits) the MMAs wait for it.
 // Tiles go to CTAs round-robin, or, with a tile counter, dynamically: after its first tile
 // (blockIdx.x) the producer takes each next tile by a fetch-and-add and hands every index to the
-// MMA and epilogue warps through a small queue in shared memory. A CTA that starts late (its SM still busy with another stream's blocks) then
-// takes fewer tiles instead of holding up the whole launch.
+// MMA and epilogue warps through a small queue in shared memory. A CTA that starts late (its SM
+// still busy with another stream's blocks) then takes fewer tiles instead of holding up the launch.
 constexpr int kEpiWarps = 8;  // two per TMEM lane group, each owning half of the columns
 // columns of one epilogue warp (BN / 2 for BN >= 32, BN for BN 16), a template parameter MAXC of the
 // kernel: 40 for BN <= 80, 48 for BN 96 (whose 48 running sums leave a few registers to spill)
@@ -655,8 +656,8 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
 
 constexpr size_t kSmemLimit = 227 * 1024;
 
-// the ring of stages, the barriers, the TMEM address slot and the tile queue (the epilogue keeps its
-// sums in registers and writes from them: no staging tile)
+// the ring of stages, the barriers, the TMEM address slot, the tile queue and, for staged stores,
+// the epilogue warps' staging tiles
 size_t smem_bytes(int BN, int stages, int nd, bool staged = false) {
     return (size_t)stages * nd * kStageAtoms * 32 * (kBM + BN) + 8 * (2 * stages + 4 + 2 * kTileQ) + 16 +
            4 * kTileQ + 16 + 256 + (staged ? (size_t)kEpiWarps * 32 * stage_pitch(BN) * sizeof(float2) + 16 : 0);
