@@ -302,6 +302,44 @@ __global__ void __launch_bounds__(256) k_JK_partial(const float2* __restrict__ b
     Kpart[(long long)blockIdx.y * aa + idx] = df_to_double(kacc);
 }
 
+// The same for a multiple of 4: each thread takes four consecutive q of one p, so that every
+// load of b and of d is 32 bytes (two 16-byte loads) and a warp keeps four times the bytes in
+// flight; the sums over P run in the same order as in k_JK_partial.
+__global__ void __launch_bounds__(256) k_JK_partial4(const float2* __restrict__ bdf, const float2* __restrict__ dg,
+                                                     int X, int a, int ap, int nchunk, double* Jpart,
+                                                     double* Kpart) {
+    const int idx = (blockIdx.x * 256 + threadIdx.x) * 4;
+    const int aa = a * a;
+    if (idx >= aa) return;
+    const int p = idx / a, q = idx - p * a;
+    const int len = (X + nchunk - 1) / nchunk;
+    const int P0 = blockIdx.y * len, P1 = min(X, P0 + len);
+    float2 jacc[4], kacc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) jacc[i] = kacc[i] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int P = P0; P < P1; ++P) {
+        const float4* bq = reinterpret_cast<const float4*>(bdf + ((long long)P * ap + p) * ap + q);
+        const float4* dq = reinterpret_cast<const float4*>(dg + (long long)P * a + q);
+        const float4 b01 = bq[0], b23 = bq[1], d01 = dq[0], d23 = dq[1];
+        const float2 dp = dg[(long long)P * a + p];
+        const float2 b[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w), make_float2(b23.x, b23.y),
+                             make_float2(b23.z, b23.w)};
+        const float2 d[4] = {make_float2(d01.x, d01.y), make_float2(d01.z, d01.w), make_float2(d23.x, d23.y),
+                             make_float2(d23.z, d23.w)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            kacc[i] = df_add(kacc[i], df_mul(b[i], b[i]));
+            jacc[i] = df_add(jacc[i], df_mul(dp, d[i]));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        Jpart[(long long)blockIdx.y * aa + idx + i] = df_to_double(jacc[i]);
+        Kpart[(long long)blockIdx.y * aa + idx + i] = df_to_double(kacc[i]);
+    }
+}
+
 // out[i] = sum_b part[b][i], one warp per output, fixed order (lane-strided then a fixed tree);
 // blockIdx.y selects one of two (part, out) pairs.
 __global__ void k_reduce_parts(const double* part0, double* out0, const double* part1, double* out1, int nparts,
@@ -677,8 +715,12 @@ int jk_from_b(nof_ctx* c, cudaStream_t s) {
     const int a = f->a, nchunk = f->nchunkJK;
     k_diag<<<nblk((long long)f->X * a), 256, 0, s>>>(f->bdf, f->X, a, f->ap, f->dg);
     NOF_LAUNCH_CHECK();
-    k_JK_partial<<<dim3(nblk((long long)a * a), nchunk), 256, 0, s>>>(f->bdf, f->dg, f->X, a, f->ap, nchunk,
-                                                                     f->Jpart, f->Kpart);
+    if (a % 4 == 0)
+        k_JK_partial4<<<dim3(nblk((long long)a * a / 4), nchunk), 256, 0, s>>>(f->bdf, f->dg, f->X, a, f->ap, nchunk,
+                                                                            f->Jpart, f->Kpart);
+    else
+        k_JK_partial<<<dim3(nblk((long long)a * a), nchunk), 256, 0, s>>>(f->bdf, f->dg, f->X, a, f->ap, nchunk,
+                                                                         f->Jpart, f->Kpart);
     NOF_LAUNCH_CHECK();
     k_reduce_parts<<<dim3(nblk((long long)a * a * 32), 2), 256, 0, s>>>(f->Jpart, c->J, f->Kpart, c->K, nchunk,
                                                                        a * a, f->colT, (long long)f->X * f->ap);
