@@ -242,12 +242,17 @@ __global__ void __launch_bounds__(16 * PA) k_T3_digits(const float2* Tdf, int X,
     for (int j = 0; j < 8; ++j) v[j] = make_float2(0.f, 0.f);
     if (mu < n && K < (long long)X * ap) {
         const int P = (int)(K / ap), r0 = (int)(K - (long long)P * ap);
-        const float2* src = Tdf + ((long long)P * n + mu) * ap + r0;
+        // 8 consecutive elements from a multiple of 8 in a row of ap (a multiple of 16): four
+        // 16-byte loads
+        const float4* src = reinterpret_cast<const float4*>(Tdf + ((long long)P * n + mu) * ap + r0);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            v[j] = src[j];
-            m = fmaxf(m, fabsf(v[j].x));
+        for (int j = 0; j < 4; ++j) {
+            const float4 x = src[j];
+            v[2 * j] = make_float2(x.x, x.y);
+            v[2 * j + 1] = make_float2(x.z, x.w);
         }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) m = fmaxf(m, fabsf(v[j].x));
     }
     mx[g][i] = m;
     __syncthreads();
@@ -406,11 +411,26 @@ __global__ void __launch_bounds__(16 * PA) k_W_digits(const float2* bdf, const f
     for (int j = 0; j < 8; ++j) v[j] = make_float2(0.f, 0.f);
     if (p < a && K < (long long)X * ap) {
         const int P = (int)(K / ap), r0 = (int)(K - (long long)P * ap);
+        if ((a & 1) == 0 && r0 + 8 <= a) {
+            // all 8 inside the a x a block: b's row and B's row as four 16-byte loads each (r0 a
+            // multiple of 8, ap a multiple of 16, p a + r0 even), then the same arithmetic as w_val
+            const float4* bs = reinterpret_cast<const float4*>(bdf + ((long long)P * ap + p) * ap + r0);
+            const float4* cs = reinterpret_cast<const float4*>(Bcdf + (long long)p * a + r0);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            v[j] = w_val(bdf, Bcdf, D, a, ap, P, p, r0 + j);
-            m = fmaxf(m, fabsf(v[j].x));
+            for (int j = 0; j < 4; ++j) {
+                const float4 bx = bs[j], cx = cs[j];
+                v[2 * j] = df_neg(df_mul(make_float2(cx.x, cx.y), make_float2(bx.x, bx.y)));
+                v[2 * j + 1] = df_neg(df_mul(make_float2(cx.z, cx.w), make_float2(bx.z, bx.w)));
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (r0 + j == p) v[j] = df_add(v[j], D[(long long)P * a + p]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = w_val(bdf, Bcdf, D, a, ap, P, p, r0 + j);
         }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) m = fmaxf(m, fabsf(v[j].x));
     }
     mx[g][i] = m;
     __syncthreads();
