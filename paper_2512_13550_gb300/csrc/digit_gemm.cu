@@ -467,8 +467,9 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                 for (int c0 = 0; c0 < kMaxCols; c0 += 8) {  // constant indices keep acc in registers
                     if (c0 >= cw) break;  // cw is a multiple of 8
                     // 8 columns of every level at a time: the register budget of a 10-warp CTA (about
-                    // 170 per thread: three warps share a sub-partition's 16K registers) holds the 32
-                    // running sums and ND x 8 loaded values without spilling
+                    // 170 per thread: three warps share a sub-partition's 16K registers) holds up to
+                    // 40 running sums and ND x 8 loaded values without spilling (48 sums, for BN
+                    // 96, spill a few words outside this loop)
                     float v[ND][8];
                     const uint32_t col = (uint32_t)(cbeg + c0);
 #pragma unroll
@@ -543,7 +544,7 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
             }
             // otherwise each lane writes its own row: 16-byte stores of column pairs (double-floats)
             // or one element at a time (int64, FP64 partials, atomics)
-            if (ncol > 0 && row < g.M && !(!partsc && g.staged)) {
+            if (ncol > 0 && row < g.M && (partsc || !g.staged)) {
                 if (g.out) {
                     long long* dst = g.out + (long long)row * g.ldo + col0;
 #pragma unroll
