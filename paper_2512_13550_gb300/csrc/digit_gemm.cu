@@ -468,8 +468,8 @@ k_digit_gemm(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, Dig
                     if (c0 >= cw) break;  // cw is a multiple of 8
                     // 8 columns of every level at a time: the register budget of a 10-warp CTA (about
                     // 170 per thread: three warps share a sub-partition's 16K registers) holds up to
-                    // 40 running sums and ND x 8 loaded values without spilling (48 sums, for BN
-                    // 96, spill a few words outside this loop)
+                    // 40 running sums and ND x 8 loaded values without spilling (with 48 sums, for
+                    // BN 96, ptxas spills 8 to 20 bytes per thread)
                     float v[ND][8];
                     const uint32_t col = (uint32_t)(cbeg + c0);
 #pragma unroll
