@@ -538,7 +538,8 @@ int fast_prepare(nof_ctx* c) {
                     nTd2 = digit_elems(128, rows2, katK, nd), nTd3 = digit_elems(128, n, kat3, nd),
                     nWd3 = digit_elems(16, npad, kat3, nd);
     {   // J/K chunks: enough blocks for a few waves, never more than one chunk per 8 aux indices
-        const int per = (int)nblk((long long)a * a);
+        // (blocks per chunk as launched: a thread takes four columns when a is a multiple of 4)
+        const int per = (int)nblk((long long)a * a / (a % 4 == 0 ? 4 : 1));
         int nc = (4 * 152 + per - 1) / per;
         const int cap = (X + 7) / 8;
         f->nchunkJK = nc < 1 ? 1 : (nc > cap ? cap : nc);
