@@ -48,3 +48,36 @@ def test_pair_partner_is_an_involution_onto_the_weak_orbitals():
         ps = [learned.pair_partner(npair, g) for g in range(npair)]
         assert sorted(ps) == list(range(npair, 2 * npair))
         assert all(learned.pair_partner(npair, p) == g for g, p in enumerate(ps))
+
+
+class _FakeContext:
+    """Stands in for a Context: optimize() answers from a table keyed by the start's first element."""
+
+    def __init__(self, answers):
+        self.answers = answers
+        self.calls = []
+
+    def optimize(self, C, gamma, **params):
+        key = float(C[0])
+        self.calls.append((key, params))
+        return dict(self.answers[key])
+
+
+def test_fallback_runs_the_core_guess_only_when_the_learned_start_does_not_converge():
+    """optimize_with_fallback keeps a converged learned run as it is; after a learned run that does
+    not converge it runs the core guess and reports the evaluations of both runs."""
+    torch = pytest.importorskip("torch")
+    learned_start = (torch.tensor([1.0]), torch.tensor([0.1]))
+    core_start = (torch.tensor([2.0]), torch.tensor([0.3]))
+    ctx = _FakeContext({1.0: {"converged": True, "evaluations": 40, "E": -1.0},
+                        2.0: {"converged": True, "evaluations": 70, "E": -1.0}})
+    r, used = learned.optimize_with_fallback(ctx, learned_start, core_start, gtol=1e-4)
+    assert used is learned_start and not r["fallback"] and r["evaluations"] == 40
+    assert [c[0] for c in ctx.calls] == [1.0] and ctx.calls[0][1] == {"gtol": 1e-4}
+
+    ctx = _FakeContext({1.0: {"converged": False, "evaluations": 300, "E": -0.5},
+                        2.0: {"converged": True, "evaluations": 70, "E": -1.0}})
+    r, used = learned.optimize_with_fallback(ctx, learned_start, core_start)
+    assert used is core_start and r["fallback"] and r["converged"]
+    assert r["evaluations"] == 370 and r["E"] == -1.0
+    assert [c[0] for c in ctx.calls] == [1.0, 2.0]
